@@ -1,0 +1,176 @@
+"""CPU oracle for the Wolff single-cluster update (Komura & Okabe, section 2).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+benchmark's timed CPU-baseline leg may import this package.  It shares no code
+with the CUDA library: the arithmetic lives in ``wolff_oracle.c`` (Philox,
+bond threshold, breadth-first cluster with the ic/in list, flip, observables by
+definition, exact enumeration) and in ``kaufman.py`` (the exact partition
+function of the periodic square lattice).  This module only marshals arrays.
+
+Every function here is pinned by a CPU test against something other than
+itself: Philox against an independent library implementation, the cluster
+against a connected-component routine, the observables against closed forms,
+the chain against exact enumeration and the exact finite-lattice solution.
+"""
+import ctypes
+
+import numpy as np
+
+from . import build as _build
+
+RECORD_DTYPE = np.dtype([("C", "<u4"), ("levels", "<u4"),
+                         ("E", "<i8"), ("M", "<i8")])
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(_build.build())
+    u32, u64, i64, i32 = (ctypes.c_uint32, ctypes.c_uint64,
+                          ctypes.c_int64, ctypes.c_int)
+    p = ctypes.c_void_p
+    lib.orc_philox4x32_10.argtypes = [u32, u32, p, p]
+    lib.orc_philox4x32_10.restype = None
+    lib.orc_bond_threshold.argtypes = [ctypes.c_double, ctypes.c_double]
+    lib.orc_bond_threshold.restype = u64
+    lib.orc_init.argtypes = [i32, u32, u64, p]
+    lib.orc_init.restype = None
+    lib.orc_energy_bond.argtypes = [i32, u32, p]
+    lib.orc_energy_bond.restype = i64
+    lib.orc_magnetisation.argtypes = [i32, u32, p]
+    lib.orc_magnetisation.restype = i64
+    lib.orc_seed_site.argtypes = [u64, u64, u32]
+    lib.orc_seed_site.restype = u32
+    lib.orc_cluster.argtypes = [i32, u32, u64, u64, u64, p, p, p, p]
+    lib.orc_cluster.restype = u32
+    lib.orc_run.argtypes = [i32, u32, u64, u64, u64, u64, p, p]
+    lib.orc_run.restype = i32
+    lib.orc_enumerate.argtypes = [i32, u32, p]
+    lib.orc_enumerate.restype = i32
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def philox4x32_10(key, ctr):
+    """Philox4x32-10 of one 2x32-bit key and 4x32-bit counter -> 4 words."""
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32))
+    out = np.zeros(4, dtype=np.uint32)
+    _load().orc_philox4x32_10(int(key[0]) & 0xFFFFFFFF,
+                              int(key[1]) & 0xFFFFFFFF, _ptr(c), _ptr(out))
+    return out
+
+
+def bond_threshold(J, T):
+    """floor(p * 2^32), p = 1 - exp(-2J/T)  (section 2, step (ii))."""
+    return int(_load().orc_bond_threshold(float(J), float(T)))
+
+
+def n_sites(dim, L):
+    return int(L) ** int(dim)
+
+
+def init_lattice(dim, L, seed):
+    """Random +-1 start drawn from Philox (tag 2); int8, site i = x + L*y (+L^2 z)."""
+    s = np.zeros(n_sites(dim, L), dtype=np.int8)
+    _load().orc_init(dim, L, seed, _ptr(s))
+    return s
+
+
+def energy_bond(dim, L, s):
+    """E_bond = sum over sites and axes of s_i s_{nb(i,d)}; energy = -J E_bond."""
+    s = np.ascontiguousarray(s, dtype=np.int8)
+    return int(_load().orc_energy_bond(dim, L, _ptr(s)))
+
+
+def magnetisation(dim, L, s):
+    s = np.ascontiguousarray(s, dtype=np.int8)
+    return int(_load().orc_magnetisation(dim, L, _ptr(s)))
+
+
+def seed_site(seed, t, N):
+    return int(_load().orc_seed_site(seed, t, N))
+
+
+def cluster(dim, L, thr, seed, t, s):
+    """Cluster of update t on s (s unchanged).
+
+    Returns (member bool array, list of sites in the order added, levels)."""
+    s = np.ascontiguousarray(s, dtype=np.int8)
+    n = n_sites(dim, L)
+    member = np.zeros(n, dtype=np.uint8)
+    lst = np.zeros(n, dtype=np.uint32)
+    levels = np.zeros(1, dtype=np.uint32)
+    c = _load().orc_cluster(dim, L, thr, seed, t, _ptr(s), _ptr(member),
+                            _ptr(lst), _ptr(levels))
+    return member.astype(bool), lst[:c].copy(), int(levels[0])
+
+
+def run(dim, L, thr, seed, t0, n, s, records=True):
+    """Updates t0..t0+n-1 applied to s (int8, modified in place).
+
+    Returns a structured array of RECORD_DTYPE (|C|, levels, E_bond, M after
+    each update), or None when records is False."""
+    if s.dtype != np.int8 or not s.flags.c_contiguous:
+        raise ValueError("s must be a contiguous int8 array")
+    rec = np.zeros(int(n), dtype=RECORD_DTYPE) if records else None
+    rc = _load().orc_run(dim, L, thr, seed, t0, n, _ptr(s),
+                         _ptr(rec) if rec is not None else None)
+    if rc != 0:
+        raise MemoryError("oracle could not allocate its scratch arrays")
+    return rec
+
+
+def density_of_states(dim, L):
+    """g(E_bond, M) by enumerating all 2^N states (N <= 32).
+
+    Returns (g, E values, M values) with g[e_index, m_index] counts."""
+    n = n_sites(dim, L)
+    width = 2 * n + 1
+    hist = np.zeros((2 * dim * n + 1) * width, dtype=np.uint64)
+    if _load().orc_enumerate(dim, L, _ptr(hist)) != 0:
+        raise ValueError("enumeration needs N <= 32")
+    g = hist.reshape(2 * dim * n + 1, width)
+    E = np.arange(-dim * n, dim * n + 1)
+    M = np.arange(-n, n + 1)
+    return g, E, M
+
+
+def exact_moments(dim, L, J, T, g=None):
+    """Boltzmann averages from the enumerated density of states.
+
+    Returns a dict with <E_bond>, <E_bond^2>, <M^2>, <|M|>, <M^4> and the
+    normalised joint distribution P(E_bond, M)."""
+    if g is None:
+        g, E, M = density_of_states(dim, L)
+    else:
+        n = n_sites(dim, L)
+        E = np.arange(-dim * n, dim * n + 1)
+        M = np.arange(-n, n + 1)
+    K = float(J) / float(T)
+    gf = g.astype(np.float64)
+    occupied = gf > 0
+    logw = np.full(gf.shape, -np.inf)
+    logw[occupied] = np.log(gf[occupied]) + K * E[:, None].repeat(
+        gf.shape[1], 1)[occupied]
+    logw -= logw[occupied].max()
+    w = np.exp(logw)
+    P = w / w.sum()
+    pe = P.sum(axis=1)
+    pm = P.sum(axis=0)
+    Ef = E.astype(np.float64)
+    Mf = M.astype(np.float64)
+    return {
+        "E": float((pe * Ef).sum()),
+        "E2": float((pe * Ef ** 2).sum()),
+        "M2": float((pm * Mf ** 2).sum()),
+        "absM": float((pm * np.abs(Mf)).sum()),
+        "M4": float((pm * Mf ** 4).sum()),
+        "P": P, "E_values": E, "M_values": M,
+    }

@@ -1,0 +1,288 @@
+/*
+ * wolff_oracle.c -- plain, slow, single-threaded CPU oracle for the Wolff
+ * single-cluster update of the Ising model (Komura & Okabe, "GPU-based
+ * single-cluster algorithm for the simulation of the Ising model").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or
+ * call this file: only the tests, the smoke check and the benchmark's timed
+ * CPU-baseline leg use it.  It shares no code, header, table or constant
+ * generator with the CUDA library; the two meet only through their outputs.
+ *
+ * What it computes (section 2 of the paper):
+ *   H = -J sum_<ij> S_i S_j on the L^D periodic square (D=2) or simple-cubic
+ *   (D=3) lattice.  One update: (i) pick a random site i0; (ii)-(iv) grow the
+ *   cluster: every member looks at each nearest neighbour j and adds it when
+ *   S_j is parallel to the seed spin and a bond test with probability
+ *   p = 1 - exp(-2J/T) succeeds; members are kept in a FIFO list with the
+ *   counters ic (members) and in (members already checked), looping while
+ *   in < ic; then every member is flipped.
+ *
+ * Readings where the paper is silent (each one is also listed in the design
+ * notes of the repository):
+ *   - Randomness.  The paper's linear congruential generator is replaced by the
+ *     counter-based Philox4x32-10 of Salmon, Moraes, Dror and Shaw (SC'11),
+ *     key = (seed_lo, seed_hi).  Bond (o,d) -- the bond from site o to its
+ *     forward neighbour in direction d -- uses lane d of
+ *     Philox(ctr = (o, t_lo, t_hi, 0)).  The seed site of update t is
+ *     floor(x * N / 2^32) with x = lane 0 of Philox(ctr = (0, t_lo, t_hi, 1)).
+ *     The initial spin of site i is -1 when the top bit of lane 0 of
+ *     Philox(ctr = (i, 0, 0, 2)) is set, else +1.
+ *   - Bond test.  thr = floor(p * 2^32) with p = 1 - exp(-2J/T) evaluated in
+ *     IEEE double with the C library's exp; a bond is active when r < thr, so
+ *     thr = 2^32 (p = 1) always accepts and thr = 0 never does.
+ *   - Small L.  At L = 2 the forward and backward neighbours along an axis are
+ *     the same site but the bonds (i,d) and (nb(i,d),d) stay distinct, so the
+ *     energy counts D*N directed-forward bonds at every L.
+ *   - The cluster is the connected component of the seed in the graph of
+ *     active bonds whose both ends carry the seed's spin; the paper leaves the
+ *     timing of the flip open, and this file flips the members after growth.
+ *   - Measurement ("+ measurement" column of Tables 1-2): the bond sum
+ *     E_bond = sum_{i,d} s_i s_{nb(i,d)} and M = sum_i s_i, recounted from
+ *     their definitions after every update (physical energy = -J * E_bond).
+ *
+ * Build: gcc -O2 -std=c99 -shared -fPIC (see oracle/build.py).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- Philox4x32-10 (Salmon et al., SC'11, section 3.3 and table 2) ------- */
+
+#define ORC_PHILOX_M0 0xD2511F53u
+#define ORC_PHILOX_M1 0xCD9E8D57u
+#define ORC_PHILOX_W0 0x9E3779B9u
+#define ORC_PHILOX_W1 0xBB67AE85u
+
+/* One Philox4x32 round: the two multiplications act on words 0 and 2; the
+ * high halves are mixed with words 1 and 3 and the round key.  */
+static void orc_philox_round(uint32_t c[4], uint32_t k0, uint32_t k1)
+{
+    uint64_t p0 = (uint64_t)ORC_PHILOX_M0 * (uint64_t)c[0];
+    uint64_t p1 = (uint64_t)ORC_PHILOX_M1 * (uint64_t)c[2];
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c[1] ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c[3] ^ k1;
+    uint32_t n3 = lo0;
+    c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+}
+
+/* Ten rounds; the key is bumped by the Weyl constants between rounds. */
+void orc_philox4x32_10(uint32_t k0, uint32_t k1, const uint32_t ctr[4],
+                       uint32_t out[4])
+{
+    uint32_t c[4] = { ctr[0], ctr[1], ctr[2], ctr[3] };
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += ORC_PHILOX_W0; k1 += ORC_PHILOX_W1; }
+        orc_philox_round(c, k0, k1);
+    }
+    out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
+}
+
+/* Counter tags: the fourth counter word separates the three uses. */
+enum { ORC_TAG_BOND = 0, ORC_TAG_SEED = 1, ORC_TAG_INIT = 2 };
+
+static void orc_draw(uint64_t seed, uint32_t c0, uint64_t t, uint32_t tag,
+                     uint32_t out[4])
+{
+    uint32_t ctr[4] = { c0, (uint32_t)t, (uint32_t)(t >> 32), tag };
+    orc_philox4x32_10((uint32_t)seed, (uint32_t)(seed >> 32), ctr, out);
+}
+
+/* ---- bond probability (section 2, step (ii)) ------------------------------ */
+
+/* thr = floor(p * 2^32), p = 1 - exp(-2J/T).  Returns 0 for J <= 0 or
+ * T = +inf, and 2^32 when p rounds to 1. */
+uint64_t orc_bond_threshold(double J, double T)
+{
+    double p = 1.0 - exp(-2.0 * J / T);
+    if (!(p > 0.0)) return 0;
+    if (p >= 1.0) return (uint64_t)1 << 32;
+    return (uint64_t)floor(ldexp(p, 32));
+}
+
+/* ---- lattice geometry ---------------------------------------------------- */
+
+/* site i = x + L*y (+ L*L*z).  Neighbour of i one step along axis d with
+ * sign +1 or -1, periodic. */
+static uint32_t orc_neighbour(int dim, uint32_t L, uint32_t i, int d, int sign)
+{
+    uint32_t stride = 1;
+    for (int k = 0; k < d; ++k) stride *= L;
+    uint32_t coord = (i / stride) % L;
+    uint32_t moved = sign > 0 ? (coord + 1) % L : (coord + L - 1) % L;
+    (void)dim;
+    return i + (moved - coord) * stride;   /* unsigned wrap is exact here */
+}
+
+static uint32_t orc_sites(int dim, uint32_t L)
+{
+    uint32_t n = 1;
+    for (int k = 0; k < dim; ++k) n *= L;
+    return n;
+}
+
+/* ---- initial configuration ----------------------------------------------- */
+
+void orc_init(int dim, uint32_t L, uint64_t seed, int8_t *s)
+{
+    uint32_t n = orc_sites(dim, L);
+    for (uint32_t i = 0; i < n; ++i) {
+        uint32_t r[4];
+        orc_draw(seed, i, 0, ORC_TAG_INIT, r);
+        s[i] = (r[0] >> 31) ? (int8_t)-1 : (int8_t)1;
+    }
+}
+
+/* ---- observables by definition (section 2, the Hamiltonian) -------------- */
+
+int64_t orc_energy_bond(int dim, uint32_t L, const int8_t *s)
+{
+    uint32_t n = orc_sites(dim, L);
+    int64_t e = 0;
+    for (uint32_t i = 0; i < n; ++i)
+        for (int d = 0; d < dim; ++d)
+            e += (int64_t)s[i] * (int64_t)s[orc_neighbour(dim, L, i, d, +1)];
+    return e;
+}
+
+int64_t orc_magnetisation(int dim, uint32_t L, const int8_t *s)
+{
+    uint32_t n = orc_sites(dim, L);
+    int64_t m = 0;
+    for (uint32_t i = 0; i < n; ++i) m += s[i];
+    return m;
+}
+
+/* ---- seed site (section 2, step (i)) ------------------------------------- */
+
+uint32_t orc_seed_site(uint64_t seed, uint64_t t, uint32_t n)
+{
+    uint32_t r[4];
+    orc_draw(seed, 0, t, ORC_TAG_SEED, r);
+    return (uint32_t)(((uint64_t)r[0] * (uint64_t)n) >> 32);
+}
+
+/* Random number of bond (o,d) in update t. */
+static uint32_t orc_bond_random(uint64_t seed, uint64_t t, uint32_t o, int d)
+{
+    uint32_t r[4];
+    orc_draw(seed, o, t, ORC_TAG_BOND, r);
+    return r[d];
+}
+
+/* ---- one cluster (section 2, steps (i)-(iv), ic/in list) ------------------
+ *
+ * Grows the cluster of update t on configuration s without changing s.
+ * member[] must be all zero on entry; on return member[i] = 1 exactly for the
+ * cluster's sites and list[0..ic) holds them in the order they were added
+ * (breadth-first).  *levels receives the number of breadth-first generations
+ * (1 for a lone seed).  Returns ic = |C|. */
+uint32_t orc_cluster(int dim, uint32_t L, uint64_t thr, uint64_t seed,
+                     uint64_t t, const int8_t *s, uint8_t *member,
+                     uint32_t *list, uint32_t *levels)
+{
+    uint32_t n = orc_sites(dim, L);
+    uint32_t i0 = orc_seed_site(seed, t, n);
+    int8_t sigma0 = s[i0];
+    uint32_t ic = 0, in = 0;
+    list[ic++] = i0;
+    member[i0] = 1;
+    uint32_t generation_end = ic, generations = 1;
+    while (in < ic) {
+        if (in == generation_end) {          /* next breadth-first generation */
+            generation_end = ic;
+            ++generations;
+        }
+        uint32_t i = list[in++];
+        for (int d = 0; d < dim; ++d) {
+            for (int sign = +1; sign >= -1; sign -= 2) {
+                uint32_t j = orc_neighbour(dim, L, i, d, sign);
+                uint32_t owner = sign > 0 ? i : j;   /* bond (owner, d) */
+                if (member[j] || s[j] != sigma0) continue;
+                if ((uint64_t)orc_bond_random(seed, t, owner, d) < thr) {
+                    member[j] = 1;
+                    list[ic++] = j;
+                }
+            }
+        }
+    }
+    if (levels) *levels = generations;
+    return ic;
+}
+
+/* ---- the update loop ----------------------------------------------------- */
+
+typedef struct {
+    uint32_t C;        /* |C_t| */
+    uint32_t levels;   /* breadth-first generations of the cluster */
+    int64_t  E_bond;   /* bond sum after the flip */
+    int64_t  M;        /* magnetisation after the flip */
+} orc_record;
+
+/* Runs updates t0 .. t0+n-1 on s in place and writes one record per update
+ * (rec may be NULL).  Returns 0, or -1 when scratch memory is unavailable. */
+int orc_run(int dim, uint32_t L, uint64_t thr, uint64_t seed, uint64_t t0,
+            uint64_t n, int8_t *s, orc_record *rec)
+{
+    uint32_t sites = orc_sites(dim, L);
+    uint8_t *member = (uint8_t *)calloc(sites, 1);
+    uint32_t *list = (uint32_t *)malloc((size_t)sites * sizeof(uint32_t));
+    if (!member || !list) { free(member); free(list); return -1; }
+    for (uint64_t u = 0; u < n; ++u) {
+        uint64_t t = t0 + u;
+        uint32_t levels = 0;
+        uint32_t c = orc_cluster(dim, L, thr, seed, t, s, member, list, &levels);
+        for (uint32_t k = 0; k < c; ++k) {   /* step (iii): flip the members */
+            s[list[k]] = (int8_t)-s[list[k]];
+            member[list[k]] = 0;
+        }
+        if (rec) {
+            rec[u].C = c;
+            rec[u].levels = levels;
+            rec[u].E_bond = orc_energy_bond(dim, L, s);
+            rec[u].M = orc_magnetisation(dim, L, s);
+        }
+    }
+    free(member);
+    free(list);
+    return 0;
+}
+
+/* ---- exact enumeration of all 2^N states --------------------------------
+ *
+ * Fills hist[(E_bond + D*N) * (2N+1) + (M + N)] with the number of
+ * configurations having that bond sum and magnetisation (the density of
+ * states g(E_bond, M)).  The states are visited in binary-reflected Gray-code
+ * order, so each step flips one spin and E_bond, M change by the local terms.
+ * hist must hold (2*D*N+1)*(2N+1) zeroed entries.  N <= 32. */
+int orc_enumerate(int dim, uint32_t L, uint64_t *hist)
+{
+    uint32_t n = orc_sites(dim, L);
+    if (n > 32) return -1;
+    int8_t *s = (int8_t *)malloc(n);
+    if (!s) return -1;
+    for (uint32_t i = 0; i < n; ++i) s[i] = 1;
+    int64_t e = orc_energy_bond(dim, L, s);
+    int64_t m = n;
+    int64_t width = 2 * (int64_t)n + 1, eoff = (int64_t)dim * n;
+    hist[(e + eoff) * width + (m + n)] += 1;
+    uint64_t total = (uint64_t)1 << n;
+    for (uint64_t k = 1; k < total; ++k) {
+        uint32_t i = (uint32_t)__builtin_ctzll(k);   /* Gray-code bit to flip */
+        int64_t local = 0;
+        for (int d = 0; d < dim; ++d) {
+            local += s[orc_neighbour(dim, L, i, d, +1)];
+            local += s[orc_neighbour(dim, L, i, d, -1)];
+        }
+        /* flipping s_i changes every bond touching i from s_i s_j to -s_i s_j */
+        e -= 2 * (int64_t)s[i] * local;
+        m -= 2 * (int64_t)s[i];
+        s[i] = (int8_t)-s[i];
+        hist[(e + eoff) * width + (m + n)] += 1;
+    }
+    free(s);
+    return 0;
+}

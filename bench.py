@@ -1,0 +1,324 @@
+"""Benchmark: flipped spins per second of the Wolff single-cluster update.
+
+Default workload (N=1): 2D square lattice L = 4096 (16.8M spins), periodic,
+J = 1, T = T_c = 2/ln(1+sqrt 2), int8 spins, Philox random start from seed 2,
+equilibrated for 2000 updates (untimed), then K timed steps of U updates each,
+one lattice per launch (the plain form), records written every update (the
+"+ measurement" form of the paper's Tables 1-2).  --workload 3d runs the
+simple-cubic L = 256 lattice at T = 4.5115, seed 3.
+
+value = sum of cluster sizes over the timed updates / device time of the
+timed steps (CUDA events on the lattice's stream, an L2 flush of 256 MB
+between steps, outside the events).  With torchrun (N > 1) every rank runs its
+own independent lattice (seed + rank): replicas only, no collective on the
+data path; value = all ranks' flips / the slowest rank's time.
+
+--impl reference times the CPU oracle (single-threaded C) on the host cores on
+a bounded sample of the same workload.
+"""
+import argparse
+import ctypes
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "flipped spins/s at Tc (2D L=4096, 3D L=256); batched/served vs plain, p50/p99"
+UNIT = "flipped spins/s"
+# algorithmic bytes per flipped spin of the int8 layout: frontier write+read
+# (8 B), the 2D neighbour spin reads (4 B in 2D, 6 B in 3D), the claim's
+# read-modify-write (2 B), and the energy/unmark pass (list re-read 4 B,
+# neighbour re-read 2D B, mark write 1 B)
+ALGO_BYTES_PER_FLIP = {2: 23.0, 3: 27.0}
+
+WORKLOADS = {
+    "2d": dict(dim=2, L=4096, T=2.0 / math.log(1.0 + math.sqrt(2.0)), seed=2, equil=2000),
+    "3d": dict(dim=3, L=256, T=4.5115, seed=3, equil=2000),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS))
+    ap.add_argument("--updates-per-step", type=int, default=100)
+    ap.add_argument("--equil", type=int, default=None)
+    ap.add_argument("--schedule", default="persistent", choices=["persistent", "graph"])
+    ap.add_argument("--blocks", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="bound of the oracle sample timed beside the GPU")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in out.strip().splitlines():
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    """CPU oracle on the host cores, bounded sample of the same workload."""
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    wl = WORKLOADS[args.workload]
+    dim, L, T, seed = wl["dim"], wl["L"], wl["T"], wl["seed"]
+    thr = oracle.bond_threshold(1.0, T)
+    s = oracle.init_lattice(dim, L, seed)
+    equil = 300 if args.equil is None else args.equil
+    oracle.run(dim, L, thr, seed, 0, equil, s, records=False)
+    t = equil
+    per_step = 4
+    times, flips = [], []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        rec = oracle.run(dim, L, thr, seed, t, per_step, s)
+        dt = time.perf_counter() - t0
+        t += per_step
+        if k >= args.warmup:
+            times.append(dt)
+            flips.append(int(rec["C"].astype(np.int64).sum()))
+    value = sum(flips) / sum(times)
+    ms = 1000.0 * sum(times) / len(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
+        "data": "synthetic",
+        "config": {"workload": "%dD L=%d T=%.6g seed %d, oracle equilibrated %d updates, "
+                               "steps of %d recorded updates" % (dim, L, T, seed, equil, per_step),
+                   "dim": dim, "L": L, "T": T, "seed": seed},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d steps x %d updates after %d untimed updates"
+                                   % (args.steps, per_step, equil)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(dim, L, T, seed, spins, t, seconds):
+    """The oracle (single-threaded C) from the GPU's equilibrated lattice, a
+    few updates at a time until `seconds` of CPU work have run."""
+    import numpy as np
+
+    import oracle
+    thr = oracle.bond_threshold(1.0, T)
+    s = np.array(spins, dtype=np.int8, copy=True)
+    flips, spent, n = 0, 0.0, 0
+    while spent < seconds and n < 1000:
+        t0 = time.perf_counter()
+        rec = oracle.run(dim, L, thr, seed, t + n, 1, s)
+        spent += time.perf_counter() - t0
+        flips += int(rec["C"][0])
+        n += 1
+    return {"value": flips / spent, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d updates from the GPU's equilibrated lattice (t=%d), %.1f s of one core"
+                      % (n, t, spent)}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import paper_1110_0899_gb300 as w
+
+    wl = WORKLOADS[args.workload]
+    dim, L, T = wl["dim"], wl["L"], wl["T"]
+    seed = wl["seed"] + rank
+    equil = wl["equil"] if args.equil is None else args.equil
+    U = args.updates_per_step
+    sched = {"persistent": w.SCHED_PERSISTENT, "graph": w.SCHED_GRAPH}[args.schedule]
+
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        lat = w.WolffLattice(dim, L, T, seed=seed, stream=stream)
+        lat.set_schedule(sched, args.blocks, args.threads)
+        info = lat.info()
+        rec_buf = lat.record_buffer(U)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        # equilibration (untimed)
+        done = 0
+        while done < equil:
+            k = min(1000, equil - done)
+            lat.step(k, records=False)
+            done += k
+        torch.cuda.synchronize()
+        snap, t_snap = lat.get_state()
+        # warm-up steps
+        for _ in range(args.warmup):
+            w.wolff_step(lat.handle, U, rec_buf)
+        torch.cuda.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        recs = []
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            starts[k].record(stream)
+            w.wolff_step(lat.handle, U, rec_buf)
+            ends[k].record(stream)
+            recs.append(rec_buf[: U * w.RECORD_BYTES].clone())
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        if world > 1:
+            torch.distributed.barrier()
+        step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        records = np.concatenate([r.cpu().numpy().view(w.RECORD_DTYPE) for r in recs])
+        flips = int(records["C"].astype(np.int64).sum())
+        total_ms = float(sum(step_ms))
+        levels = records["levels"].astype(np.int64)
+        if world > 1:
+            import torch.distributed as dist
+            tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ff = torch.tensor([flips], device="cuda", dtype=torch.float64)
+            dist.all_reduce(ff, op=dist.ReduceOp.SUM)
+            total_ms_all, flips_all = float(tt.item()), float(ff.item())
+        else:
+            total_ms_all, flips_all = total_ms, float(flips)
+        value = flips_all / (total_ms_all / 1000.0)
+
+        # end to end through the host-buffer entry point: upload the
+        # equilibrated lattice, run U recorded updates, read the records back
+        e2e = None
+        if not args.no_e2e:
+            e2e_flips, e2e_s = 0, 0.0
+            for k in range(max(3, min(args.steps, 10))):
+                t0 = time.perf_counter()
+                r, _ = lat.run_host(U, spins_in=snap, t_in=t_snap, records=True, spins_out=False)
+                e2e_s += time.perf_counter() - t0
+                e2e_flips += int(r["C"].astype(np.int64).sum())
+            e2e = {"value": e2e_flips / e2e_s, "unit": UNIT,
+                   "h2d_bytes_per_step": int(lat.N), "d2h_bytes_per_step": int(U * w.RECORD_BYTES)}
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    peaks, peak_kind = measured_peaks()
+    per_launch_flips = flips / args.steps
+    avg_launch_s = total_ms / args.steps / 1000.0
+    achieved = ALGO_BYTES_PER_FLIP[dim] * per_launch_flips / avg_launch_s / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "peak_kind": peak_kind, "kernel": "k_persistent<%d>" % dim if
+            args.schedule == "persistent" else "k_graph_level<%d>" % dim}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(dim, L, T, seed, snap, t_snap, args.cpu_seconds)
+    launches = args.steps if args.schedule == "persistent" else int(
+        args.steps + (levels + 3).sum())
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
+        "data": "synthetic",
+        "config": {"workload": "%dD L=%d T=%.6g J=1 seed %d, %d equilibration + %d x %d "
+                               "recorded updates, one lattice per launch"
+                               % (dim, L, T, seed, equil, args.steps, U),
+                   "dim": dim, "L": L, "T": T, "seed": seed, "updates_per_step": U,
+                   "schedule": args.schedule, "grid_blocks": info["grid_blocks"],
+                   "block_threads": info["block_threads"],
+                   "l2": "256 MB buffer written between timed steps",
+                   "parallelism": "replicas x%d" % world},
+        "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
+        "clocks": clk,
+        "detail": {"mean_cluster": flips / len(records), "mean_levels": float(levels.mean()),
+                   "max_levels": int(levels.max()), "ms_per_update": total_ms / len(records),
+                   "p50_update_ms": None},
+    }
+    print(json.dumps(line), flush=True)
+    lat.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

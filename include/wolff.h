@@ -1,0 +1,191 @@
+/*
+ * wolff.h -- C ABI of the GB300 Wolff single-cluster library.
+ *
+ * The operation (Komura & Okabe, "GPU-based single-cluster algorithm for the
+ * simulation of the Ising model", section 2 and section 4):
+ *   H = -J sum_<ij> S_i S_j on the periodic L^D lattice, D = 2 (square) or
+ *   D = 3 (simple cubic), site i = x + L*y (+ L*L*z).  One single-cluster
+ *   update t: pick a random seed site (step (i)); grow the cluster by parallel
+ *   expansion of the newly added ("wave-front") spins, each testing its
+ *   parallel neighbours with bond probability p = 1 - exp(-2J/T)
+ *   (steps (ii)-(iv) and (iii')); flip the finished cluster.
+ *
+ * Randomness is counter based (Philox4x32-10, Salmon et al. SC'11) with
+ * key = (seed mod 2^32, seed >> 32):
+ *   bond (o,d) of update t  -> lane d of Philox(ctr = (o, t_lo, t_hi, 0)),
+ *   seed site of update t   -> floor(lane0(Philox((0, t_lo, t_hi, 1))) * N / 2^32),
+ *   initial spin of site i  -> -1 if bit 31 of lane0(Philox((i, 0, 0, 2))) else +1.
+ * A bond is active when its random word is below thr = floor(p * 2^32), p
+ * evaluated on the host in IEEE double (the device never evaluates exp).  The
+ * cluster is therefore the connected component of the seed in the graph of
+ * active bonds joining spins parallel to the seed, whatever order the GPU
+ * explores it in, and every result is reproducible bit for bit.
+ *
+ * Observables: E_bond = sum_{i,d} s_i s_{nb(i,d)} over the D*N forward bonds
+ * (physical energy = -J * E_bond) and M = sum_i s_i, both exact integers.
+ *
+ * Conventions for every entry point:
+ *   - Returns a wolff_status; nothing is thrown across the ABI.
+ *   - Pointers named d_* are device pointers on the context's device, h_* are
+ *     host pointers.  The caller owns every buffer it passes and must keep it
+ *     alive until the work using it has completed on the context's stream.
+ *   - Device work is enqueued on the stream given to ising_init (NULL = the
+ *     legacy default stream) and is asynchronous unless stated otherwise.
+ *     Errors detected on the device (a bounded wait that ran out, an invalid
+ *     state word) are latched in the context and reported by the next call
+ *     that synchronises (measure, measure_full, wolff_get_state, ...).
+ *   - A context is not thread safe; use one context per host thread.
+ */
+#ifndef WOLFF_H
+#define WOLFF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WOLFF_OK = 0,
+    WOLFF_EINVAL = 1,         /* bad argument (size, pointer, parameter) */
+    WOLFF_ENOMEM = 2,         /* workspace too small or allocation failed */
+    WOLFF_ECUDA = 3,          /* a CUDA runtime call failed */
+    WOLFF_ETIMEOUT = 4,       /* a device-side bounded wait gave up */
+    WOLFF_EUNSUPPORTED = 5    /* valid request this build cannot serve */
+} wolff_status;
+
+/* Spin layouts.  INT8: one byte per site (bit 0 = current spin, bit 1 = spin
+ * at the start of the running update; +1 is stored as 1). */
+enum { WOLFF_LAYOUT_INT8 = 0 };
+
+/* How one update's levels are synchronised (section 3 of the paper replaced):
+ *   PERSISTENT  one cooperative launch per wolff_step; all updates and levels
+ *               run inside it, separated by a bounded grid-wide barrier;
+ *   GRAPH       a CUDA graph: one kernel node per level inside a conditional
+ *               WHILE node, nested inside a WHILE node over updates;
+ *   AUTO        the library's choice (see wolff_set_schedule). */
+enum {
+    WOLFF_SCHED_AUTO = 0,
+    WOLFF_SCHED_PERSISTENT = 1,
+    WOLFF_SCHED_GRAPH = 2
+};
+
+/* One record per update, written after the update's flip
+ * (section 5, the "+ measurement" column of Tables 1-2). */
+typedef struct {
+    uint32_t C;        /* cluster size |C_t| */
+    uint32_t levels;   /* breadth-first generations grown (1 = lone seed) */
+    int64_t  E_bond;   /* bond sum after the flip */
+    int64_t  M;        /* magnetisation after the flip */
+} wolff_record;
+
+/* Static facts about a context. */
+typedef struct {
+    int      dim, L;
+    uint32_t N;            /* L^dim */
+    uint64_t thr;          /* bond threshold floor(p 2^32), 0 .. 2^32 */
+    uint64_t seed;
+    uint64_t t;            /* index of the next update (host mirror) */
+    int      schedule;     /* schedule wolff_step will use */
+    int      grid_blocks;  /* CTAs of the growth kernels */
+    int      block_threads;
+    int      sm_count;
+    size_t   workspace_bytes;
+} wolff_info;
+
+typedef struct wolff_ctx wolff_ctx;
+
+/* Bytes of device workspace a context of this shape needs (0 if the shape is
+ * invalid).  The workspace holds the spin array, the cluster list (the ic/in
+ * list of section 2, one 32-bit entry per site) and a small control block. */
+size_t wolff_workspace_bytes(int dim, int L, int layout);
+
+/* Creates a context on the current device and initialises the lattice from
+ * Philox (update counter t = 0), then computes E_bond and M by a full pass.
+ *   dim         2 or 3;  L >= 2, with dim*L^dim < 2^32 and L <= 1024 in 3D,
+ *               L <= 32767 in 2D;
+ *   J, T        coupling and temperature, J >= 0, T > 0 (T may be +inf);
+ *   seed        Philox key;  layout  WOLFF_LAYOUT_INT8;
+ *   d_workspace device buffer of at least wolff_workspace_bytes(), 256-byte
+ *               aligned, owned by the caller, not to be used by anyone else
+ *               while the context lives; NULL makes the library cudaMalloc
+ *               (and later free) its own;
+ *   stream      cudaStream_t to enqueue on (NULL = default stream).
+ * On success *out receives the context.  EINVAL for a bad shape/parameter or
+ * a misaligned/small workspace, ENOMEM if the library's allocation fails. */
+wolff_status ising_init(wolff_ctx **out, int dim, int L, double J, double T,
+                        uint64_t seed, int layout, void *d_workspace,
+                        size_t workspace_bytes, void *stream);
+
+/* Enqueues n_updates single-cluster updates (t .. t+n-1), each: seed site,
+ * level-synchronous growth with atomic claims and warp-aggregated appends to
+ * the cluster list, boundary-bond energy change, unmark, record.  d_records
+ * (nullable) receives n_updates wolff_record entries.  n_updates = 0 is a
+ * no-op.  Asynchronous. */
+wolff_status wolff_step(wolff_ctx *ctx, uint64_t n_updates, void *d_records);
+
+/* Same as wolff_step but through host memory: if h_spins_in is non-NULL the
+ * lattice (int8 +-1, N entries) is first uploaded and t set to t_in; the
+ * records (n_updates entries, nullable) and the final lattice (nullable) are
+ * copied back.  Synchronises the stream. */
+wolff_status wolff_run_host(wolff_ctx *ctx, const int8_t *h_spins_in,
+                            uint64_t t_in, uint64_t n_updates,
+                            wolff_record *h_records, int8_t *h_spins_out);
+
+/* Reads the incrementally tracked E_bond, M and the size of the last cluster
+ * (0 before the first update).  Synchronises the stream; reports latched
+ * device errors.  Any output pointer may be NULL. */
+wolff_status measure(wolff_ctx *ctx, int64_t *E_bond, int64_t *M,
+                     uint64_t *last_C);
+
+/* Recomputes E_bond and M by a full pass over the lattice (the verification
+ * path).  Synchronises. */
+wolff_status measure_full(wolff_ctx *ctx, int64_t *E_bond, int64_t *M);
+
+/* Checkpoint: copies the lattice out as int8 +-1 (N entries, h_spins) and the
+ * next update index.  Synchronises. */
+wolff_status wolff_get_state(wolff_ctx *ctx, int8_t *h_spins, uint64_t *t);
+
+/* Restore: uploads an int8 +-1 lattice and sets the next update index; E_bond
+ * and M are recomputed.  EINVAL (latched, reported here) if an entry is not
+ * +-1.  Synchronises. */
+wolff_status wolff_set_state(wolff_ctx *ctx, const int8_t *h_spins, uint64_t t);
+
+/* Chooses the schedule and the CTA shape of the growth kernels (0 = keep /
+ * library default).  The persistent schedule caps grid_blocks at what can be
+ * co-resident.  Results do not depend on the choice. */
+wolff_status wolff_set_schedule(wolff_ctx *ctx, int schedule, int grid_blocks,
+                                int block_threads);
+
+wolff_status wolff_get_info(wolff_ctx *ctx, wolff_info *info);
+
+/* Host-side Philox threshold the library uses for (J, T). */
+uint64_t wolff_bond_threshold(double J, double T);
+
+/* Fills d_out[4k .. 4k+3] with Philox4x32-10(key, d_ctr[4k .. 4k+3]) for k <
+ * n on the device (test hook for the generator).  Asynchronous on stream. */
+wolff_status wolff_philox(uint32_t key0, uint32_t key1, const uint32_t *d_ctr,
+                          uint32_t *d_out, uint64_t n, void *stream);
+
+/* Failure-detection self test: runs the library's bounded device-side wait
+ * on a private control block where nothing can release it, with a limit of
+ * wait_ns nanoseconds (<= 10 s).  *observed receives the status the device
+ * latched: WOLFF_ETIMEOUT when the limit works.  The context's own state is
+ * not touched and stays usable.  Synchronises. */
+wolff_status wolff_selftest_wait_timeout(wolff_ctx *ctx, uint64_t wait_ns, int *observed);
+
+/* Releases the context (and the workspace if the library allocated it).
+ * Synchronises the stream first. */
+wolff_status ising_free(wolff_ctx *ctx);
+
+/* Last error message of the context (never NULL; "" if none). */
+const char *wolff_last_error(wolff_ctx *ctx);
+
+const char *wolff_status_string(wolff_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WOLFF_H */

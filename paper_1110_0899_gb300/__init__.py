@@ -1,0 +1,273 @@
+"""GB300 Wolff single-cluster library: Python binding of ``include/wolff.h``.
+
+Argument marshalling only.  Every step of an update runs in the CUDA kernels
+of ``_build/libwolff.so``; PyTorch provides device memory and the stream.  The
+library must be built first (``python -m paper_1110_0899_gb300.build`` or
+``__graft_entry__.build()``); importing the binding without it raises.
+
+Names follow the C ABI: ``ising_init``, ``wolff_step``, ``measure``,
+``measure_full``, ``wolff_get_state``, ``wolff_set_state``, ``wolff_run_host``,
+``ising_free``; :class:`WolffLattice` wraps a context for convenience.
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from . import build as _build
+
+WOLFF_OK, WOLFF_EINVAL, WOLFF_ENOMEM, WOLFF_ECUDA, WOLFF_ETIMEOUT, WOLFF_EUNSUPPORTED = range(6)
+STATUS_NAMES = {0: "WOLFF_OK", 1: "WOLFF_EINVAL", 2: "WOLFF_ENOMEM", 3: "WOLFF_ECUDA",
+                4: "WOLFF_ETIMEOUT", 5: "WOLFF_EUNSUPPORTED"}
+LAYOUT_INT8 = 0
+SCHED_AUTO, SCHED_PERSISTENT, SCHED_GRAPH = 0, 1, 2
+
+RECORD_DTYPE = np.dtype([("C", "<u4"), ("levels", "<u4"), ("E", "<i8"), ("M", "<i8")])
+RECORD_BYTES = RECORD_DTYPE.itemsize  # 24
+
+TC_2D = 2.0 / math.log(1.0 + math.sqrt(2.0))   # Onsager: T_c/J = 2.2691...
+TC_3D = 4.5115                                  # simple cubic, J = 1
+
+
+class WolffError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__("%s%s" % (STATUS_NAMES.get(status, str(status)),
+                                   (": " + msg) if msg else ""))
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("L", ctypes.c_int), ("N", ctypes.c_uint32),
+                ("thr", ctypes.c_uint64), ("seed", ctypes.c_uint64), ("t", ctypes.c_uint64),
+                ("schedule", ctypes.c_int), ("grid_blocks", ctypes.c_int),
+                ("block_threads", ctypes.c_int), ("sm_count", ctypes.c_int),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load_library():
+    """Loads ``libwolff.so``; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError("libwolff.so is not built (%s); run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    v, i, u32, u64, i64, d, sz = (ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32,
+                                  ctypes.c_uint64, ctypes.c_int64, ctypes.c_double,
+                                  ctypes.c_size_t)
+    P = ctypes.POINTER
+    sigs = {
+        "wolff_workspace_bytes": (sz, [i, i, i]),
+        "ising_init": (i, [P(v), i, i, d, d, u64, i, v, sz, v]),
+        "wolff_step": (i, [v, u64, v]),
+        "wolff_run_host": (i, [v, v, u64, u64, v, v]),
+        "measure": (i, [v, P(i64), P(i64), P(u64)]),
+        "measure_full": (i, [v, P(i64), P(i64)]),
+        "wolff_get_state": (i, [v, v, P(u64)]),
+        "wolff_set_state": (i, [v, v, u64]),
+        "wolff_set_schedule": (i, [v, i, i, i]),
+        "wolff_get_info": (i, [v, P(_Info)]),
+        "wolff_bond_threshold": (u64, [d, d]),
+        "wolff_philox": (i, [u32, u32, v, v, u64, v]),
+        "wolff_selftest_wait_timeout": (i, [v, u64, P(i)]),
+        "ising_free": (i, [v]),
+        "wolff_last_error": (ctypes.c_char_p, [v]),
+        "wolff_status_string": (ctypes.c_char_p, [i]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status, ctx=None):
+    if status != WOLFF_OK:
+        msg = ""
+        if ctx is not None:
+            msg = load_library().wolff_last_error(ctx).decode(errors="replace")
+        raise WolffError(status, msg)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# ---- functions with the C names ---------------------------------------------
+
+def wolff_workspace_bytes(dim, L, layout=LAYOUT_INT8):
+    return int(load_library().wolff_workspace_bytes(dim, L, layout))
+
+
+def wolff_bond_threshold(J, T):
+    return int(load_library().wolff_bond_threshold(float(J), float(T)))
+
+
+def ising_init(dim, L, J, T, seed, layout=LAYOUT_INT8, workspace=None, stream=None):
+    """Creates a context; returns (handle, workspace tensor).  The workspace is
+    a torch uint8 CUDA tensor that must outlive the handle."""
+    torch = _torch()
+    lib = load_library()
+    nbytes = lib.wolff_workspace_bytes(dim, L, layout)
+    if nbytes == 0:
+        raise WolffError(WOLFF_EINVAL, "invalid lattice shape dim=%r L=%r" % (dim, L))
+    if workspace is None:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    handle = ctypes.c_void_p()
+    st = lib.ising_init(ctypes.byref(handle), int(dim), int(L), float(J), float(T),
+                        int(seed) & 0xFFFFFFFFFFFFFFFF, int(layout),
+                        ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                        _stream_handle(stream))
+    _check(st)
+    return handle, workspace
+
+
+def wolff_step(handle, n_updates, d_records=None):
+    """Enqueues n_updates updates; d_records: torch uint8 CUDA tensor of
+    n_updates * 24 bytes (or None)."""
+    ptr = ctypes.c_void_p(d_records.data_ptr()) if d_records is not None else None
+    _check(load_library().wolff_step(handle, int(n_updates), ptr), handle)
+
+
+def measure(handle):
+    E, M, C = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_uint64()
+    _check(load_library().measure(handle, ctypes.byref(E), ctypes.byref(M), ctypes.byref(C)),
+           handle)
+    return E.value, M.value, C.value
+
+
+def measure_full(handle):
+    E, M = ctypes.c_int64(), ctypes.c_int64()
+    _check(load_library().measure_full(handle, ctypes.byref(E), ctypes.byref(M)), handle)
+    return E.value, M.value
+
+
+def wolff_get_state(handle, N):
+    s = np.empty(N, dtype=np.int8)
+    t = ctypes.c_uint64()
+    _check(load_library().wolff_get_state(handle, ctypes.c_void_p(s.ctypes.data),
+                                          ctypes.byref(t)), handle)
+    return s, t.value
+
+
+def wolff_set_state(handle, spins, t):
+    s = np.ascontiguousarray(spins, dtype=np.int8)
+    _check(load_library().wolff_set_state(handle, ctypes.c_void_p(s.ctypes.data), int(t)),
+           handle)
+
+
+def wolff_run_host(handle, N, n_updates, spins_in=None, t_in=0, records=True, spins_out=True):
+    """Host-buffer path: optional upload, n updates, records and lattice back."""
+    sin = None if spins_in is None else np.ascontiguousarray(spins_in, dtype=np.int8)
+    rec = np.zeros(int(n_updates), dtype=RECORD_DTYPE) if records else None
+    sout = np.empty(N, dtype=np.int8) if spins_out else None
+    ptr = lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+    _check(load_library().wolff_run_host(handle, ptr(sin), int(t_in), int(n_updates), ptr(rec),
+                                         ptr(sout)), handle)
+    return rec, sout
+
+
+def ising_free(handle):
+    _check(load_library().ising_free(handle))
+
+
+def wolff_philox(key0, key1, d_ctr, d_out, n, stream=None):
+    _check(load_library().wolff_philox(key0 & 0xFFFFFFFF, key1 & 0xFFFFFFFF,
+                                       ctypes.c_void_p(d_ctr.data_ptr()),
+                                       ctypes.c_void_p(d_out.data_ptr()), int(n),
+                                       _stream_handle(stream)))
+
+
+def records_to_numpy(d_records, n):
+    """Device record buffer -> numpy structured array (synchronises)."""
+    host = d_records[: n * RECORD_BYTES].cpu().numpy()
+    return host.view(RECORD_DTYPE).copy()
+
+
+class WolffLattice:
+    """One Ising lattice and its Wolff chain on the current CUDA device."""
+
+    def __init__(self, dim, L, T, J=1.0, seed=0, layout=LAYOUT_INT8, schedule=None,
+                 grid_blocks=0, block_threads=0, stream=None):
+        self.dim, self.L, self.J, self.T, self.seed = int(dim), int(L), float(J), float(T), int(seed)
+        self.N = self.L ** self.dim
+        self.handle, self.workspace = ising_init(dim, L, J, T, seed, layout, stream=stream)
+        self._records = None
+        if schedule is not None or grid_blocks or block_threads:
+            self.set_schedule(schedule or SCHED_AUTO, grid_blocks, block_threads)
+
+    def set_schedule(self, schedule=SCHED_AUTO, grid_blocks=0, block_threads=0):
+        _check(load_library().wolff_set_schedule(self.handle, int(schedule), int(grid_blocks),
+                                                 int(block_threads)), self.handle)
+
+    def info(self):
+        inf = _Info()
+        _check(load_library().wolff_get_info(self.handle, ctypes.byref(inf)), self.handle)
+        return {k: getattr(inf, k) for k, _ in _Info._fields_}
+
+    def record_buffer(self, n):
+        torch = _torch()
+        need = int(n) * RECORD_BYTES
+        if self._records is None or self._records.numel() < need:
+            self._records = torch.empty(max(need, RECORD_BYTES), dtype=torch.uint8, device="cuda")
+        return self._records
+
+    def step(self, n, records=True):
+        """Runs n updates; returns the records as a numpy array (synchronising)
+        when records is True, the device buffer when records == "device", else None."""
+        buf = self.record_buffer(n) if records else None
+        wolff_step(self.handle, n, buf)
+        if records == "device":
+            return buf
+        if records:
+            return records_to_numpy(buf, n)
+        return None
+
+    def measure(self):
+        return measure(self.handle)
+
+    def measure_full(self):
+        return measure_full(self.handle)
+
+    def get_state(self):
+        return wolff_get_state(self.handle, self.N)
+
+    def set_state(self, spins, t):
+        wolff_set_state(self.handle, spins, t)
+
+    def run_host(self, n, spins_in=None, t_in=0, records=True, spins_out=True):
+        return wolff_run_host(self.handle, self.N, n, spins_in, t_in, records, spins_out)
+
+    def selftest_wait_timeout(self, wait_ns):
+        obs = ctypes.c_int()
+        _check(load_library().wolff_selftest_wait_timeout(self.handle, int(wait_ns),
+                                                          ctypes.byref(obs)), self.handle)
+        return obs.value
+
+    def close(self):
+        if self.handle is not None:
+            ising_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,425 @@
+// wolff_capi.cu -- the C ABI declared in include/wolff.h.
+//
+// Host logic only: argument validation, the workspace layout, the bond
+// threshold (computed here with the C library's exp so that the device never
+// evaluates it), the choice of schedule and launch shape, checkpoint
+// conversion and error latching.  All arithmetic of the update runs in the
+// kernels of wolff_kernels.cu.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "wolff.h"
+#include "wolff_internal.h"
+
+using namespace wolff;
+
+namespace wolff {
+cudaError_t launch_selftest_wait(DevCtl *scratch, unsigned long long wait_ns, cudaStream_t s);
+}
+
+struct wolff_ctx {
+    int dim = 0, L = 0;
+    uint32_t N = 0;
+    double J = 0, T = 0;
+    uint64_t seed = 0, thr = 0;
+    int layout = 0;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool own_ws = false;
+    DevCtl *ctl = nullptr;
+    DevCtl *scratch_ctl = nullptr;
+    uint8_t *spins = nullptr;
+    uint32_t *list = nullptr;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int sm_count = 0;
+    int schedule = WOLFF_SCHED_PERSISTENT;
+    int blocks = 0, threads = 256;
+    int graph_blocks = 0, graph_threads = 0;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    uint64_t t_host = 0;
+    void *rec_stage = nullptr;
+    size_t rec_stage_bytes = 0;
+    unsigned long long wait_ns = 2000000000ull;
+    std::string err;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+bool shape_ok(int dim, int L) {
+    if (dim == 2) return L >= 2 && L <= 32767;
+    if (dim == 3) return L >= 2 && L <= 1024;
+    return false;
+}
+
+uint32_t sites(int dim, int L) {
+    uint64_t n = 1;
+    for (int d = 0; d < dim; ++d) n *= (uint64_t)L;
+    return (uint32_t)n;
+}
+
+wolff_status fail(wolff_ctx *c, wolff_status s, const char *msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+wolff_status cuda_fail(wolff_ctx *c, cudaError_t e, const char *where) {
+    if (c) {
+        c->err = std::string(where) + ": " + cudaGetErrorString(e);
+    }
+    return WOLFF_ECUDA;
+}
+
+StepParams make_params(const wolff_ctx *c) {
+    StepParams p;
+    p.spins = c->spins;
+    p.list = c->list;
+    p.ctl = c->ctl;
+    p.records = nullptr;
+    p.g.L = (uint32_t)c->L;
+    p.g.N = c->N;
+    p.g.LL = (uint32_t)c->L * (uint32_t)c->L;
+    p.key0 = (uint32_t)c->seed;
+    p.key1 = (uint32_t)(c->seed >> 32);
+    p.thr = c->thr;
+    p.t0 = c->t_host;
+    p.n = 0;
+    p.wait_ns = c->wait_ns;
+    return p;
+}
+
+// Synchronises and turns a latched device status into the return value.
+wolff_status sync_and_check(wolff_ctx *c, DevCtl *host_copy) {
+    DevCtl tmp;
+    DevCtl *dst = host_copy ? host_copy : &tmp;
+    cudaError_t e = cudaMemcpyAsync(dst, c->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "synchronise");
+    if (dst->status != 0) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "device reported %s (detail %u)",
+                 wolff_status_string((wolff_status)dst->status), dst->err_detail);
+        c->err = buf;
+        return (wolff_status)dst->status;
+    }
+    return WOLFF_OK;
+}
+
+int default_blocks(const wolff_ctx *c) {
+    int b = (int)(c->N / 2048u);
+    if (b < 1) b = 1;
+    if (b > c->sm_count) b = c->sm_count;
+    return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *wolff_status_string(wolff_status s) {
+    switch (s) {
+        case WOLFF_OK: return "WOLFF_OK";
+        case WOLFF_EINVAL: return "WOLFF_EINVAL";
+        case WOLFF_ENOMEM: return "WOLFF_ENOMEM";
+        case WOLFF_ECUDA: return "WOLFF_ECUDA";
+        case WOLFF_ETIMEOUT: return "WOLFF_ETIMEOUT";
+        case WOLFF_EUNSUPPORTED: return "WOLFF_EUNSUPPORTED";
+    }
+    return "WOLFF_UNKNOWN";
+}
+
+uint64_t wolff_bond_threshold(double J, double T) {
+    const double p = 1.0 - exp(-2.0 * J / T);
+    if (!(p > 0.0)) return 0;
+    if (p >= 1.0) return 1ull << 32;
+    return (uint64_t)floor(ldexp(p, 32));
+}
+
+size_t wolff_workspace_bytes(int dim, int L, int layout) {
+    if (layout != WOLFF_LAYOUT_INT8 || !shape_ok(dim, L)) return 0;
+    const size_t n = sites(dim, L);
+    return 2 * sizeof(DevCtl) + round_up(n, kAlign) + round_up(n * sizeof(uint32_t), kAlign);
+}
+
+wolff_status ising_init(wolff_ctx **out, int dim, int L, double J, double T, uint64_t seed,
+                        int layout, void *d_workspace, size_t workspace_bytes, void *stream) {
+    if (!out) return WOLFF_EINVAL;
+    *out = nullptr;
+    if (!shape_ok(dim, L) || layout != WOLFF_LAYOUT_INT8) return WOLFF_EINVAL;
+    if (!(J >= 0.0) || !(T > 0.0)) return WOLFF_EINVAL;
+    const size_t need = wolff_workspace_bytes(dim, L, layout);
+    if (d_workspace) {
+        if (workspace_bytes < need) return WOLFF_ENOMEM;
+        if (reinterpret_cast<uintptr_t>(d_workspace) % kAlign) return WOLFF_EINVAL;
+    }
+    wolff_ctx *c = new (std::nothrow) wolff_ctx;
+    if (!c) return WOLFF_ENOMEM;
+    c->dim = dim;
+    c->L = L;
+    c->N = sites(dim, L);
+    c->J = J;
+    c->T = T;
+    c->seed = seed;
+    c->thr = wolff_bond_threshold(J, T);
+    c->layout = layout;
+    c->stream = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return WOLFF_ECUDA;
+    }
+    if (d_workspace) {
+        c->ws = d_workspace;
+        c->ws_bytes = workspace_bytes;
+    } else {
+        if (cudaMalloc(&c->ws, need) != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return WOLFF_ENOMEM;
+        }
+        c->own_ws = true;
+        c->ws_bytes = need;
+    }
+    char *base = static_cast<char *>(c->ws);
+    c->ctl = reinterpret_cast<DevCtl *>(base);
+    c->scratch_ctl = reinterpret_cast<DevCtl *>(base + sizeof(DevCtl));
+    c->spins = reinterpret_cast<uint8_t *>(base + 2 * sizeof(DevCtl));
+    c->list = reinterpret_cast<uint32_t *>(base + 2 * sizeof(DevCtl) + round_up(c->N, kAlign));
+    c->blocks = default_blocks(c);
+    c->threads = 256;
+
+    const StepParams p = make_params(c);
+    e = cudaMemsetAsync(c->ws, 0, 2 * sizeof(DevCtl) + round_up(c->N, kAlign), c->stream);
+    if (e == cudaSuccess) e = launch_reset_ctl(c->ctl, 0, c->stream);
+    if (e == cudaSuccess) e = launch_init(c->spins, p.g, p.key0, p.key1, c->stream);
+    if (e == cudaSuccess) e = launch_measure_full(dim, c->spins, p.g, c->ctl, 1, c->stream);
+    if (e != cudaSuccess) {
+        cuda_fail(c, e, "ising_init");
+        ising_free(c);
+        return WOLFF_ECUDA;
+    }
+    wolff_status s = sync_and_check(c, nullptr);
+    if (s != WOLFF_OK) {
+        ising_free(c);
+        return s;
+    }
+    *out = c;
+    return WOLFF_OK;
+}
+
+wolff_status wolff_set_schedule(wolff_ctx *c, int schedule, int grid_blocks, int block_threads) {
+    if (!c) return WOLFF_EINVAL;
+    if (schedule < WOLFF_SCHED_AUTO || schedule > WOLFF_SCHED_GRAPH)
+        return fail(c, WOLFF_EINVAL, "unknown schedule");
+    if (block_threads != 0 && (block_threads < 32 || block_threads > 1024 || block_threads % 32))
+        return fail(c, WOLFF_EINVAL, "block_threads must be a multiple of 32 in [32, 1024]");
+    if (grid_blocks < 0) return fail(c, WOLFF_EINVAL, "grid_blocks must be >= 0");
+    c->schedule = schedule == WOLFF_SCHED_AUTO ? WOLFF_SCHED_PERSISTENT : schedule;
+    if (block_threads) c->threads = block_threads;
+    c->blocks = grid_blocks ? grid_blocks : default_blocks(c);
+    if (c->gexec && (c->graph_blocks != c->blocks || c->graph_threads != c->threads)) {
+        cudaGraphExecDestroy(c->gexec);
+        cudaGraphDestroy(c->graph);
+        c->gexec = nullptr;
+        c->graph = nullptr;
+    }
+    return WOLFF_OK;
+}
+
+wolff_status wolff_step(wolff_ctx *c, uint64_t n_updates, void *d_records) {
+    if (!c) return WOLFF_EINVAL;
+    if (n_updates == 0) return WOLFF_OK;
+    StepParams p = make_params(c);
+    p.records = reinterpret_cast<wolff_record *>(d_records);
+    p.n = n_updates;
+    cudaError_t e;
+    if (c->schedule == WOLFF_SCHED_GRAPH) {
+        if (!c->gexec) {
+            e = build_update_graph(c->dim, p, c->blocks, c->threads, &c->gexec, &c->graph);
+            if (e != cudaSuccess) return cuda_fail(c, e, "build_update_graph");
+            c->graph_blocks = c->blocks;
+            c->graph_threads = c->threads;
+        }
+        e = launch_graph_call(c->ctl, n_updates, p.records, c->stream);
+        if (e == cudaSuccess) e = cudaGraphLaunch(c->gexec, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    } else {
+        int err = 0;
+        const int per_sm = persistent_max_blocks_per_sm(c->dim, c->threads, &err);
+        if (err) return cuda_fail(c, (cudaError_t)err, "occupancy");
+        int blocks = c->blocks;
+        if (blocks > per_sm * c->sm_count) blocks = per_sm * c->sm_count;
+        if (blocks < 1) return fail(c, WOLFF_EUNSUPPORTED, "persistent kernel cannot be resident");
+        void *args[] = {&p};
+        e = cudaLaunchCooperativeKernel(persistent_kernel(c->dim), dim3(blocks), dim3(c->threads),
+                                        args, 0, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cooperative launch");
+    }
+    c->t_host += n_updates;
+    return WOLFF_OK;
+}
+
+wolff_status measure(wolff_ctx *c, int64_t *E_bond, int64_t *M, uint64_t *last_C) {
+    if (!c) return WOLFF_EINVAL;
+    DevCtl h;
+    wolff_status s = sync_and_check(c, &h);
+    if (s != WOLFF_OK) return s;
+    if (E_bond) *E_bond = h.E;
+    if (M) *M = h.M;
+    if (last_C) *last_C = h.last_C;
+    return WOLFF_OK;
+}
+
+wolff_status measure_full(wolff_ctx *c, int64_t *E_bond, int64_t *M) {
+    if (!c) return WOLFF_EINVAL;
+    const StepParams p = make_params(c);
+    cudaError_t e = launch_measure_full(c->dim, c->spins, p.g, c->ctl, 0, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "measure_full");
+    DevCtl h;
+    wolff_status s = sync_and_check(c, &h);
+    if (s != WOLFF_OK) return s;
+    if (E_bond) *E_bond = h.full_E;
+    if (M) *M = h.full_M;
+    return WOLFF_OK;
+}
+
+wolff_status wolff_get_state(wolff_ctx *c, int8_t *h_spins, uint64_t *t) {
+    if (!c) return WOLFF_EINVAL;
+    if (h_spins) {
+        int8_t *scratch = reinterpret_cast<int8_t *>(c->list);
+        cudaError_t e = launch_to_pm1(scratch, c->spins, c->N, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_spins, scratch, c->N, cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "get_state");
+    }
+    DevCtl h;
+    wolff_status s = sync_and_check(c, &h);
+    if (s != WOLFF_OK) return s;
+    if (t) *t = h.t;
+    return WOLFF_OK;
+}
+
+wolff_status wolff_set_state(wolff_ctx *c, const int8_t *h_spins, uint64_t t) {
+    if (!c || !h_spins) return WOLFF_EINVAL;
+    int8_t *scratch = reinterpret_cast<int8_t *>(c->list);
+    const StepParams p = make_params(c);
+    cudaError_t e = cudaMemcpyAsync(scratch, h_spins, c->N, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_reset_ctl(c->ctl, t, c->stream);
+    if (e == cudaSuccess) e = launch_from_pm1(c->spins, scratch, c->N, c->ctl, c->stream);
+    if (e == cudaSuccess) e = launch_measure_full(c->dim, c->spins, p.g, c->ctl, 1, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set_state");
+    c->t_host = t;
+    return sync_and_check(c, nullptr);
+}
+
+wolff_status wolff_run_host(wolff_ctx *c, const int8_t *h_spins_in, uint64_t t_in,
+                            uint64_t n_updates, wolff_record *h_records, int8_t *h_spins_out) {
+    if (!c) return WOLFF_EINVAL;
+    wolff_status s;
+    if (h_spins_in) {
+        s = wolff_set_state(c, h_spins_in, t_in);
+        if (s != WOLFF_OK) return s;
+    }
+    wolff_record *d_rec = nullptr;
+    if (h_records && n_updates) {
+        // device staging for the records, kept by the context and grown on
+        // demand so that repeated calls do not allocate
+        const size_t bytes = n_updates * sizeof(wolff_record);
+        if (bytes > c->rec_stage_bytes) {
+            cudaStreamSynchronize(c->stream);
+            if (c->rec_stage) cudaFree(c->rec_stage);
+            c->rec_stage = nullptr;
+            c->rec_stage_bytes = 0;
+            if (cudaMalloc(&c->rec_stage, bytes) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(c, WOLFF_ENOMEM, "record staging buffer");
+            }
+            c->rec_stage_bytes = bytes;
+        }
+        d_rec = reinterpret_cast<wolff_record *>(c->rec_stage);
+    }
+    s = wolff_step(c, n_updates, d_rec);
+    if (s == WOLFF_OK && d_rec) {
+        cudaError_t e = cudaMemcpyAsync(h_records, d_rec, n_updates * sizeof(wolff_record),
+                                        cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) s = cuda_fail(c, e, "records copy");
+    }
+    if (s == WOLFF_OK && h_spins_out) {
+        s = wolff_get_state(c, h_spins_out, nullptr);
+    } else if (s == WOLFF_OK) {
+        s = sync_and_check(c, nullptr);
+    }
+    return s;
+}
+
+wolff_status wolff_get_info(wolff_ctx *c, wolff_info *info) {
+    if (!c || !info) return WOLFF_EINVAL;
+    info->dim = c->dim;
+    info->L = c->L;
+    info->N = c->N;
+    info->thr = c->thr;
+    info->seed = c->seed;
+    info->t = c->t_host;
+    info->schedule = c->schedule;
+    info->grid_blocks = c->blocks;
+    info->block_threads = c->threads;
+    info->sm_count = c->sm_count;
+    info->workspace_bytes = c->ws_bytes;
+    return WOLFF_OK;
+}
+
+wolff_status wolff_philox(uint32_t key0, uint32_t key1, const uint32_t *d_ctr, uint32_t *d_out,
+                          uint64_t n, void *stream) {
+    if (n && (!d_ctr || !d_out)) return WOLFF_EINVAL;
+    cudaError_t e = launch_philox(key0, key1, d_ctr, d_out, n, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? WOLFF_OK : WOLFF_ECUDA;
+}
+
+wolff_status ising_free(wolff_ctx *c) {
+    if (!c) return WOLFF_OK;
+    cudaStreamSynchronize(c->stream);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    if (c->own_ws && c->ws) cudaFree(c->ws);
+    if (c->rec_stage) cudaFree(c->rec_stage);
+    delete c;
+    return WOLFF_OK;
+}
+
+const char *wolff_last_error(wolff_ctx *c) {
+    if (!c) return "";
+    return c->err.c_str();
+}
+
+// Test hook for the failure-detection path: runs the library's bounded
+// grid barrier on a private control block with two expected CTAs but only one
+// launched, so the wait can only end by its time limit.  Writes the status
+// the device latched (WOLFF_ETIMEOUT when the limit works) to *observed and
+// leaves the context's own state untouched.
+wolff_status wolff_selftest_wait_timeout(wolff_ctx *c, uint64_t wait_ns, int *observed) {
+    if (!c || !observed) return WOLFF_EINVAL;
+    if (wait_ns > 10000000000ull) return fail(c, WOLFF_EINVAL, "wait_ns above 10 s");
+    cudaError_t e = cudaMemsetAsync(c->scratch_ctl, 0, sizeof(DevCtl), c->stream);
+    if (e == cudaSuccess) e = launch_selftest_wait(c->scratch_ctl, wait_ns, c->stream);
+    DevCtl h;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&h, c->scratch_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "selftest");
+    *observed = (int)h.status;
+    return WOLFF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,312 @@
+// wolff_device.cuh -- device building blocks of the Wolff growth kernels.
+//
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), lattice coordinate
+// packing, the idempotent atomic claim, warp-aggregated appends and the
+// bounded grid-wide barrier that replaces the paper's quasi-block
+// synchronisation (section 3).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "wolff_internal.h"
+
+namespace wolff {
+
+constexpr unsigned kFullMask = 0xffffffffu;
+
+// ---- Philox4x32-10 --------------------------------------------------------
+// Round: multiply words 0 and 2 by the two round multipliers; the new words
+// are (hi(M1*c2) ^ c1 ^ k0, lo(M1*c2), hi(M0*c0) ^ c3 ^ k1, lo(M0*c0)); the
+// key advances by the Weyl increments between rounds.
+struct Philox4 {
+    uint32_t v[4];
+};
+
+__device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1,
+                                                 uint32_t c2, uint32_t c3,
+                                                 uint32_t k0, uint32_t k1) {
+    const uint32_t kMul0 = 0xD2511F53u, kMul1 = 0xCD9E8D57u;
+    const uint32_t kWeyl0 = 0x9E3779B9u, kWeyl1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(kMul0, c0);
+        const uint32_t lo0 = kMul0 * c0;
+        const uint32_t hi1 = __umulhi(kMul1, c2);
+        const uint32_t lo1 = kMul1 * c2;
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+        k0 += kWeyl0;
+        k1 += kWeyl1;
+    }
+    Philox4 out;
+    out.v[0] = c0; out.v[1] = c1; out.v[2] = c2; out.v[3] = c3;
+    return out;
+}
+
+// ---- lattice coordinates ---------------------------------------------------
+template <int DIM> struct Pack;
+template <> struct Pack<2> {
+    __host__ __device__ static constexpr int shift(int d) { return 16 * d; }
+    static constexpr uint32_t kMask = 0xffffu;
+};
+template <> struct Pack<3> {
+    __host__ __device__ static constexpr int shift(int d) { return 10 * d; }
+    static constexpr uint32_t kMask = 0x3ffu;
+};
+
+template <int DIM>
+__device__ __forceinline__ void unpack(uint32_t p, uint32_t c[DIM]) {
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) c[d] = (p >> Pack<DIM>::shift(d)) & Pack<DIM>::kMask;
+}
+
+template <int DIM>
+__device__ __forceinline__ uint32_t pack(const uint32_t c[DIM]) {
+    uint32_t p = 0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) p |= c[d] << Pack<DIM>::shift(d);
+    return p;
+}
+
+template <int DIM>
+__device__ __forceinline__ uint32_t site_index(const Geometry &g, const uint32_t c[DIM]) {
+    uint32_t i = c[0] + g.L * c[1];
+    if (DIM == 3) i += g.LL * c[2];
+    return i;
+}
+
+template <int DIM>
+__device__ __forceinline__ uint32_t axis_stride(const Geometry &g, int d) {
+    return d == 0 ? 1u : (d == 1 ? g.L : g.LL);
+}
+
+// Neighbours of a site: slot 2d = forward along axis d, slot 2d+1 = backward.
+// Both the linear index and the packed coordinates are produced; unsigned
+// wrap-around makes the +-(L-1) periodic jumps exact.
+template <int DIM>
+struct Neighbours {
+    uint32_t idx[2 * DIM];
+    uint32_t packed[2 * DIM];
+};
+
+template <int DIM>
+__device__ __forceinline__ void neighbours(const Geometry &g, uint32_t p,
+                                           uint32_t *self_idx,
+                                           Neighbours<DIM> &nb) {
+    uint32_t c[DIM];
+    unpack<DIM>(p, c);
+    const uint32_t i = site_index<DIM>(g, c);
+    *self_idx = i;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        const uint32_t cf = (c[d] + 1 == g.L) ? 0u : c[d] + 1;
+        const uint32_t cb = (c[d] == 0) ? g.L - 1 : c[d] - 1;
+        const uint32_t st = axis_stride<DIM>(g, d);
+        nb.idx[2 * d] = i + (cf - c[d]) * st;
+        nb.idx[2 * d + 1] = i + (cb - c[d]) * st;
+        nb.packed[2 * d] = p + ((cf - c[d]) << Pack<DIM>::shift(d));
+        nb.packed[2 * d + 1] = p + ((cb - c[d]) << Pack<DIM>::shift(d));
+    }
+}
+
+// ---- claim -----------------------------------------------------------------
+// Flips bit 0 of the site's byte from the seed spin to its opposite with one
+// atomic on the containing 32-bit word: AND-clear when the seed spin is +1,
+// OR-set when it is -1.  The operation is idempotent, so exactly one caller
+// sees the old bit equal to the seed spin and wins the site.
+__device__ __forceinline__ bool claim_site(uint8_t *spins, uint32_t j, uint32_t sig0bit) {
+    unsigned int *w = reinterpret_cast<unsigned int *>(spins) + (j >> 2);
+    const unsigned int bit = 1u << ((j & 3u) * 8u);
+    if (sig0bit) {
+        const unsigned int old = atomicAnd(w, ~bit);
+        return (old & bit) != 0u;
+    }
+    const unsigned int old = atomicOr(w, bit);
+    return (old & bit) == 0u;
+}
+
+// ---- small PTX helpers -----------------------------------------------------
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned int *p, unsigned int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned int ld_volatile_u32(const unsigned int *p) {
+    return *reinterpret_cast<const volatile unsigned int *>(p);
+}
+
+__device__ __forceinline__ void raise_status(DevCtl *ctl, unsigned int code,
+                                             unsigned int detail) {
+    if (atomicCAS(&ctl->status, 0u, code) == 0u) ctl->err_detail = detail;
+}
+
+// ---- bounded grid-wide barrier ----------------------------------------------
+// Sense by generation counter: every CTA adds one arrival; the last arrival
+// resets the count and publishes generation g+1 with a release store; the
+// others poll the generation with acquire loads.  The poll gives up after
+// wait_ns nanoseconds (globaltimer) or 2^28 polls, or when another CTA has
+// already raised an error, records WOLFF_ETIMEOUT, and the barrier returns false so that every
+// CTA leaves the kernel.  `gen` is the CTA's private copy of the generation.
+__device__ __forceinline__ bool grid_barrier(DevCtl *ctl, unsigned int nblocks,
+                                             unsigned int &gen,
+                                             unsigned long long wait_ns,
+                                             unsigned int where) {
+    __shared__ unsigned int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int ok = 1;
+        const unsigned int my = gen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&ctl->bar_count, 1u);
+        if (arrived == nblocks - 1) {
+            ctl->bar_count = 0;
+            st_release_u32(&ctl->bar_gen, my + 1);
+        } else {
+            const unsigned long long start = global_ns();
+            unsigned int polls = 0;
+            while (ld_acquire_u32(&ctl->bar_gen) == my) {
+                if ((++polls & 63u) == 0u) {
+                    if (ld_volatile_u32(&ctl->status) != 0u) { ok = 0; break; }
+                    if (global_ns() - start > wait_ns || polls > (1u << 28)) {
+                        raise_status(ctl, WOLFF_ETIMEOUT, where);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        __threadfence();
+        gen = my + 1;
+        if (ld_volatile_u32(&ctl->status) != 0u) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0u;
+}
+
+// ---- warp-aggregated append -------------------------------------------------
+// Each lane contributes `mine` entries; one atomicAdd per warp reserves the
+// warp's range in the cluster list.  Returns the lane's first slot.  All 32
+// lanes must call it.
+__device__ __forceinline__ uint32_t warp_reserve(unsigned int *counter, uint32_t mine) {
+    const int lane = threadIdx.x & 31;
+    uint32_t incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFullMask, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const uint32_t total = __shfl_sync(kFullMask, incl, 31);
+    uint32_t base = 0;
+    if (total != 0u) {
+        if (lane == 31) base = atomicAdd(counter, total);
+        base = __shfl_sync(kFullMask, base, 31);
+    }
+    return base + incl - mine;
+}
+
+// ---- block reduction of a 64-bit sum ---------------------------------------
+__device__ __forceinline__ long long block_sum(long long v) {
+    __shared__ long long s_part[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFullMask, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) s_part[warp] = v;
+    __syncthreads();
+    long long total = 0;
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        total = lane < nw ? s_part[lane] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) total += __shfl_down_sync(kFullMask, total, o);
+    }
+    return total;   // valid in thread 0
+}
+
+// ---- the expansion of one wave-front site (step (iii') of section 4) -------
+// Loads the 2*DIM neighbour bytes (L2, bypassing L1 because other CTAs write
+// them), draws the site's own forward bonds with one Philox call and each
+// backward bond from its owner's call only when that neighbour is still
+// parallel to the seed spin, and claims every neighbour whose bond is active.
+// Returns the mask of neighbour slots won; nb receives their coordinates.
+template <int DIM>
+__device__ __forceinline__ uint32_t expand_site(const StepParams &p, uint32_t packed,
+                                                uint32_t sig0bit, uint32_t tlo,
+                                                uint32_t thi, Neighbours<DIM> &nb) {
+    uint32_t i;
+    neighbours<DIM>(p.g, packed, &i, nb);
+    uint8_t v[2 * DIM];
+#pragma unroll
+    for (int s = 0; s < 2 * DIM; ++s) v[s] = __ldcg(p.spins + nb.idx[s]);
+    const Philox4 fwd = philox4x32_10(i, tlo, thi, kTagBond, p.key0, p.key1);
+    uint32_t won = 0;
+#pragma unroll
+    for (int s = 0; s < 2 * DIM; ++s) {
+        const int d = s >> 1;
+        if ((uint32_t)(v[s] & 1u) != sig0bit) continue;
+        uint32_t r;
+        if ((s & 1) == 0) {
+            r = fwd.v[d];
+        } else {
+            r = philox4x32_10(nb.idx[s], tlo, thi, kTagBond, p.key0, p.key1).v[d];
+        }
+        if ((unsigned long long)r < p.thr && claim_site(p.spins, nb.idx[s], sig0bit))
+            won |= 1u << s;
+    }
+    return won;
+}
+
+// Boundary term of one member: for every neighbour outside the cluster,
+// +1 if it is anti-parallel to the seed spin (the bond gains energy when the
+// member flips) and -1 if it is parallel; members have differing bits.
+template <int DIM>
+__device__ __forceinline__ int boundary_term(const StepParams &p, uint32_t packed,
+                                             uint32_t sig0bit, uint32_t *self_idx) {
+    Neighbours<DIM> nb;
+    neighbours<DIM>(p.g, packed, self_idx, nb);
+    int acc = 0;
+#pragma unroll
+    for (int s = 0; s < 2 * DIM; ++s) {
+        const uint32_t v = __ldcg(p.spins + nb.idx[s]);
+        const uint32_t cur = v & 1u, orig = (v >> 1) & 1u;
+        if (cur == orig) acc += (orig == sig0bit) ? -1 : 1;
+    }
+    return acc;
+}
+
+// Seed site of update t: floor(x * N / 2^32), x = lane 0 of the seed draw.
+__device__ __forceinline__ uint32_t seed_site(const StepParams &p, unsigned long long t) {
+    const Philox4 r = philox4x32_10(0u, (uint32_t)t, (uint32_t)(t >> 32), kTagSeed,
+                                    p.key0, p.key1);
+    return (uint32_t)(((unsigned long long)r.v[0] * p.g.N) >> 32);
+}
+
+template <int DIM>
+__device__ __forceinline__ uint32_t pack_index(const Geometry &g, uint32_t i) {
+    uint32_t c[DIM];
+    c[0] = i % g.L;
+    if (DIM == 2) {
+        c[1] = i / g.L;
+    } else {
+        c[1] = (i / g.L) % g.L;
+        c[DIM - 1] = i / g.LL;
+    }
+    return pack<DIM>(c);
+}
+
+}  // namespace wolff

@@ -1,0 +1,101 @@
+// wolff_internal.h -- structures shared by the library's host and device code.
+//
+// Device memory of one context (the caller's workspace), 256-byte aligned
+// pieces:
+//   [DevCtl, 256 B][spins: N bytes, padded to 256][list: N x u32]
+// spins: one byte per site, bit 0 = current spin, bit 1 = spin at the start
+//   of the running update (+1 stored as 1).  Between updates the two bits are
+//   equal, so a byte is 0x00 (-1) or 0x03 (+1).  Claiming a site flips bit 0
+//   only; a cluster member is a site whose two bits differ.
+// list: the cluster list of section 2 (ic = members, in = checked); entries
+//   are packed lattice coordinates (2D: x | y << 16, 3D: x | y << 10 | z << 20)
+//   so that no division is needed to find neighbours.  Level k's frontier is a
+//   contiguous range of it.
+#pragma once
+
+#include <stdint.h>
+
+#include "wolff.h"
+
+namespace wolff {
+
+constexpr uint32_t kTagBond = 0;
+constexpr uint32_t kTagSeed = 1;
+constexpr uint32_t kTagInit = 2;
+
+// Control block living at the start of the workspace.  Plain fields are only
+// touched by one thread at a time; counters marked (atomic) are shared.
+struct alignas(256) DevCtl {
+    // chain state
+    unsigned long long t;          // next update index
+    long long E;                   // bond sum
+    long long M;                   // magnetisation
+    unsigned long long total_C;    // sum of cluster sizes so far
+    unsigned int last_C;
+    unsigned int last_levels;
+    unsigned int status;           // 0 or a wolff_status (atomic, first wins)
+    unsigned int err_detail;       // where a bounded wait gave up, etc.
+    // growth scratch
+    unsigned int cnt[4];           // level append counters (atomic)
+    long long dE;                  // boundary-bond sum of this update (atomic)
+    unsigned int bar_count;        // grid barrier arrivals (atomic)
+    unsigned int bar_gen;          // grid barrier generation
+    // graph schedule state
+    unsigned int lo, hi;           // current frontier = list[lo, hi)
+    unsigned int levels;
+    unsigned int done;             // blocks finished in this kernel (atomic)
+    unsigned int sig0bit;          // seed spin (1 = +1) of the running update
+    unsigned int pad0;
+    unsigned long long t_end;      // graph loop stops when t == t_end
+    unsigned long long rec_t0;     // t of records[0] for this call
+    wolff_record *records;         // destination of this call's records
+    // full recount
+    long long full_E;
+    long long full_M;
+};
+static_assert(sizeof(DevCtl) == 256, "control block must stay 256 bytes");
+
+struct Geometry {
+    uint32_t L;
+    uint32_t N;
+    uint32_t LL;         // L*L
+};
+
+struct StepParams {
+    uint8_t *spins;
+    uint32_t *list;
+    DevCtl *ctl;
+    wolff_record *records;      // nullable
+    Geometry g;
+    uint32_t key0, key1;
+    unsigned long long thr;     // 0 .. 2^32
+    unsigned long long t0;      // first update of this launch
+    unsigned long long n;       // updates in this launch
+    unsigned long long wait_ns; // bound of every device-side wait
+};
+
+// Launch helpers implemented in wolff_kernels.cu (C++ linkage, internal).
+cudaError_t launch_init(uint8_t *spins, Geometry g, uint32_t k0, uint32_t k1,
+                        cudaStream_t s);
+cudaError_t launch_measure_full(int dim, const uint8_t *spins, Geometry g,
+                                DevCtl *ctl, int set_chain, cudaStream_t s);
+cudaError_t launch_from_pm1(uint8_t *spins, const int8_t *src, uint32_t N,
+                            DevCtl *ctl, cudaStream_t s);
+cudaError_t launch_to_pm1(int8_t *dst, const uint8_t *spins, uint32_t N,
+                          cudaStream_t s);
+cudaError_t launch_philox(uint32_t k0, uint32_t k1, const uint32_t *ctr,
+                          uint32_t *out, unsigned long long n, cudaStream_t s);
+cudaError_t launch_reset_ctl(DevCtl *ctl, unsigned long long t, cudaStream_t s);
+
+// Persistent cooperative schedule.
+const void *persistent_kernel(int dim);
+int persistent_max_blocks_per_sm(int dim, int threads, int *err);
+
+// Graph schedule: builds the nested-WHILE graph; returns its executable.
+cudaError_t build_update_graph(int dim, const StepParams &p, int blocks,
+                               int threads, cudaGraphExec_t *exec,
+                               cudaGraph_t *graph);
+cudaError_t launch_graph_call(DevCtl *ctl, unsigned long long n,
+                              wolff_record *records, cudaStream_t s);
+
+}  // namespace wolff

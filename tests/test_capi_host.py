@@ -1,0 +1,84 @@
+"""CPU checks of the C ABI library: it loads, exports every declared entry
+point, and its host logic (bond threshold, workspace sizes, argument
+validation) agrees with the oracle and the header -- no GPU call is made."""
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1110_0899_gb300 import build
+    build.build()
+    import paper_1110_0899_gb300 as w
+    return w.load_library()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "wolff.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^[a-z_][a-z0-9_ \*]*?\b([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "while", "for", "return")))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "ising_init" in names and "wolff_step" in names and "measure" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_threshold_matches_oracle(lib):
+    import paper_1110_0899_gb300 as w
+    for J in (0.0, 0.5, 1.0, 2.0):
+        for T in (1e-3, 0.5, 1.0, w.TC_2D, 3.0, w.TC_3D, 100.0, float("inf")):
+            assert w.wolff_bond_threshold(J, T) == oracle.bond_threshold(J, T), (J, T)
+    assert w.wolff_bond_threshold(1.0, w.TC_2D) == 2**33 - math.isqrt(2**65) - 1
+
+
+def test_workspace_bytes(lib):
+    import paper_1110_0899_gb300 as w
+    n = 4096 * 4096
+    b = w.wolff_workspace_bytes(2, 4096)
+    assert b >= n + 4 * n and b <= n + 4 * n + 4096
+    assert w.wolff_workspace_bytes(3, 256) == w.wolff_workspace_bytes(2, 4096)
+    for dim, L in ((1, 10), (4, 2), (2, 1), (2, 0), (3, 1025), (2, 40000)):
+        assert w.wolff_workspace_bytes(dim, L) == 0
+    assert w.wolff_workspace_bytes(2, 16, 7) == 0
+
+
+def test_init_rejects_bad_arguments_before_touching_the_device(lib):
+    import paper_1110_0899_gb300 as w
+    h = ctypes.c_void_p()
+    bad = [(4, 16, 1.0, 2.0), (2, 1, 1.0, 2.0), (3, 2000, 1.0, 2.0),
+           (2, 16, -1.0, 2.0), (2, 16, 1.0, 0.0), (2, 16, 1.0, -1.0),
+           (2, 16, float("nan"), 2.0)]
+    for dim, L, J, T in bad:
+        st = lib.ising_init(ctypes.byref(h), dim, L, J, T, 1, 0, None, 0, None)
+        assert st == w.WOLFF_EINVAL, (dim, L, J, T)
+    assert lib.ising_init(None, 2, 16, 1.0, 2.0, 1, 0, None, 0, None) == w.WOLFF_EINVAL
+    # a caller workspace that is too small or misaligned
+    st = lib.ising_init(ctypes.byref(h), 2, 16, 1.0, 2.0, 1, 0, ctypes.c_void_p(256), 16, None)
+    assert st == w.WOLFF_ENOMEM
+    st = lib.ising_init(ctypes.byref(h), 2, 16, 1.0, 2.0, 1, 0, ctypes.c_void_p(4096 + 8),
+                        1 << 20, None)
+    assert st == w.WOLFF_EINVAL
+    assert lib.wolff_step(None, 1, None) == w.WOLFF_EINVAL
+    assert lib.measure(None, None, None, None) == w.WOLFF_EINVAL
+    assert lib.wolff_status_string(4) == b"WOLFF_ETIMEOUT"
+    assert lib.wolff_last_error(None) == b""
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    import paper_1110_0899_gb300 as w
+    monkeypatch.setattr(w._build, "LIB", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(w, "_lib", None)
+    with pytest.raises(ImportError):
+        w.load_library()

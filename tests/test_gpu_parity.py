@@ -1,0 +1,182 @@
+"""GPU path vs the CPU oracle, bit for bit (section 2's update on the GPU).
+
+Every test drives the CUDA kernels through the C ABI (the Python binding only
+marshals arguments) and compares the per-update records (|C|, levels,
+E_bond, M) and the lattice with the oracle on the same seeded inputs, for both
+schedules and for several launch shapes, since the cluster is a connected
+component and must not depend on the exploration order."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from _gpu import assert_records_equal, oracle_trajectory, require_cuda
+
+pytestmark = pytest.mark.gpu
+
+TC2 = 2.0 / math.log(1.0 + math.sqrt(2.0))
+SCHEDS = ("persistent", "graph")
+
+
+def sched_id(w, name):
+    return {"persistent": w.SCHED_PERSISTENT, "graph": w.SCHED_GRAPH}[name]
+
+
+def run_gpu(w, dim, L, T, seed, n, sched, blocks=0, threads=0):
+    lat = w.WolffLattice(dim, L, T, seed=seed)
+    lat.set_schedule(sched_id(w, sched), blocks, threads)
+    rec = lat.step(n)
+    spins, t = lat.get_state()
+    E, M, C = lat.measure()
+    Ef, Mf = lat.measure_full()
+    lat.close()
+    assert t == n
+    assert (E, M) == (Ef, Mf)
+    if n:
+        assert (E, M, C) == (rec["E"][-1], rec["M"][-1], rec["C"][-1])
+    return rec, spins
+
+
+def test_device_philox_matches_oracle():
+    torch, w = require_cuda()
+    rng = np.random.default_rng(5)
+    n = 4096
+    ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:8] = [[0, 0, 0, 0], [0, 0, 0, 1], [0, 0, 0, 2], [2**32 - 1] * 4,
+               [5, 1, 0, 0], [16777215, 11999, 0, 0], [1, 2**32 - 1, 7, 0], [3, 3, 3, 3]]
+    d_ctr = torch.from_numpy(ctr.view(np.int32)).cuda()
+    d_out = torch.empty((n, 4), dtype=torch.int32, device="cuda")
+    for key in ((0, 0), (1, 0), (0xDEADBEEF, 0x12345678), (2**32 - 1, 2**32 - 1)):
+        w.wolff_philox(key[0], key[1], d_ctr, d_out, n)
+        got = d_out.cpu().numpy().view(np.uint32)
+        for k in list(range(8)) + list(rng.integers(0, n, 64)):
+            assert np.array_equal(got[k], oracle.philox4x32_10(key, ctr[k])), (key, k)
+
+
+@pytest.mark.parametrize("sched", SCHEDS)
+def test_small_workload_2d_l16(sched):
+    """2D L=16, J=1, T=Tc, seed 1, 10^4 updates: every record and the final lattice."""
+    torch, w = require_cuda()
+    ref, s_ref = oracle_trajectory(2, 16, TC2, 1, 10_000)
+    rec, spins = run_gpu(w, 2, 16, TC2, 1, 10_000, sched)
+    assert_records_equal(rec, ref, "2D L=16 " + sched)
+    assert np.array_equal(spins, s_ref)
+
+
+@pytest.mark.parametrize("sched", SCHEDS)
+def test_3d_l8(sched):
+    torch, w = require_cuda()
+    ref, s_ref = oracle_trajectory(3, 8, 4.5115, 3, 2_000)
+    rec, spins = run_gpu(w, 3, 8, 4.5115, 3, 2_000, sched)
+    assert_records_equal(rec, ref, "3D L=8 " + sched)
+    assert np.array_equal(spins, s_ref)
+
+
+# ragged and degenerate shapes: L=2 (double bonds), odd L, non powers of two,
+# a single CTA, a one-warp CTA and many CTAs over a tiny lattice
+SHAPES = [
+    (2, 2, 1.0, 300, 1, 32), (2, 3, TC2, 300, 0, 0), (3, 2, 4.5115, 300, 3, 64),
+    (3, 3, 3.0, 300, 0, 0), (2, 37, TC2, 400, 5, 96), (2, 100, 2.0, 300, 0, 1024),
+    (3, 13, 4.5115, 300, 0, 0), (3, 17, 4.0, 200, 64, 256), (2, 64, 2.6, 400, 152, 128),
+    (2, 255, TC2, 150, 0, 0),
+]
+
+
+@pytest.mark.parametrize("sched", SCHEDS)
+@pytest.mark.parametrize("dim,L,T,n,blocks,threads", SHAPES)
+def test_ragged_shapes(sched, dim, L, T, n, blocks, threads):
+    torch, w = require_cuda()
+    seed = 1000 + L
+    ref, s_ref = oracle_trajectory(dim, L, T, seed, n)
+    rec, spins = run_gpu(w, dim, L, T, seed, n, sched, blocks, threads)
+    assert_records_equal(rec, ref, "%dD L=%d %s" % (dim, L, sched))
+    assert np.array_equal(spins, s_ref)
+
+
+@pytest.mark.parametrize("sched", SCHEDS)
+def test_degenerate_thresholds(sched):
+    torch, w = require_cuda()
+    # T = inf: thr = 0, every cluster is the seed alone
+    rec, _ = run_gpu(w, 2, 32, float("inf"), 4, 100, sched)
+    assert np.all(rec["C"] == 1) and np.all(rec["levels"] == 1)
+    ref, _ = oracle_trajectory(2, 32, float("inf"), 4, 100)
+    assert_records_equal(rec, ref, "T=inf")
+    # T -> 0: thr = 2^32, clusters are whole aligned domains
+    for dim, L in ((2, 48), (3, 10)):
+        ref, s_ref = oracle_trajectory(dim, L, 1e-3, 6, 50)
+        rec, spins = run_gpu(w, dim, L, 1e-3, 6, 50, sched)
+        assert_records_equal(rec, ref, "T=0")
+        assert np.array_equal(spins, s_ref)
+
+
+@pytest.mark.parametrize("sched", SCHEDS)
+def test_medium_lattices(sched):
+    """Lattices spanning many CTAs: 2D L=512 at Tc, 3D L=64 at 4.5115."""
+    torch, w = require_cuda()
+    for dim, L, T, n in ((2, 512, TC2, 120), (3, 64, 4.5115, 60)):
+        ref, s_ref = oracle_trajectory(dim, L, T, 7, n)
+        rec, spins = run_gpu(w, dim, L, T, 7, n, sched)
+        assert_records_equal(rec, ref, "%dD L=%d" % (dim, L))
+        assert np.array_equal(spins, s_ref)
+
+
+def test_checkpoint_resume_and_segments():
+    torch, w = require_cuda()
+    dim, L, T, seed = 2, 128, TC2, 9
+    ref, s_ref = oracle_trajectory(dim, L, T, seed, 300)
+    a = w.WolffLattice(dim, L, T, seed=seed)
+    r1 = a.step(120)
+    snap, t = a.get_state()
+    assert t == 120
+    b = w.WolffLattice(dim, L, T, seed=seed, schedule=w.SCHED_GRAPH)
+    b.set_state(snap, t)
+    r2 = b.step(180)
+    assert_records_equal(np.concatenate([r1, r2]), ref, "resume")
+    spins, t2 = b.get_state()
+    assert t2 == 300 and np.array_equal(spins, s_ref)
+    # the same context switching schedule between calls
+    c = w.WolffLattice(dim, L, T, seed=seed)
+    parts = []
+    for k, sched in enumerate([w.SCHED_PERSISTENT, w.SCHED_GRAPH] * 3):
+        c.set_schedule(sched)
+        parts.append(c.step(50))
+    assert_records_equal(np.concatenate(parts), ref, "alternating schedules")
+    for x in (a, b, c):
+        x.close()
+
+
+def test_set_state_rejects_non_spin_values():
+    torch, w = require_cuda()
+    lat = w.WolffLattice(2, 16, TC2, seed=1)
+    bad = np.ones(256, dtype=np.int8)
+    bad[17] = 0
+    with pytest.raises(w.WolffError) as ei:
+        lat.set_state(bad, 0)
+    assert ei.value.status == w.WOLFF_EINVAL
+    good = oracle.init_lattice(2, 16, 1)
+    lat.set_state(good, 0)
+    ref, _ = oracle_trajectory(2, 16, TC2, 1, 50)
+    assert_records_equal(lat.step(50), ref, "after rejected restore")
+    lat.close()
+
+
+def test_host_buffer_path():
+    torch, w = require_cuda()
+    dim, L, T, seed = 3, 20, 4.5115, 12
+    s0 = oracle.init_lattice(dim, L, seed)
+    ref, s_ref = oracle_trajectory(dim, L, T, seed, 80, t0=40, s=s0)
+    lat = w.WolffLattice(dim, L, T, seed=seed)
+    rec, spins = lat.run_host(80, spins_in=s0, t_in=40)
+    assert_records_equal(rec, ref, "run_host")
+    assert np.array_equal(spins, s_ref)
+    lat.close()
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    torch, w = require_cuda()
+    lat = w.WolffLattice(2, 16, TC2, seed=1)
+    assert lat.selftest_wait_timeout(20_000_000) == w.WOLFF_ETIMEOUT   # 20 ms limit
+    ref, _ = oracle_trajectory(2, 16, TC2, 1, 100)
+    assert_records_equal(lat.step(100), ref, "after self test")
+    lat.close()

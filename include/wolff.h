@@ -175,6 +175,38 @@ wolff_status wolff_philox(uint32_t key0, uint32_t key1, const uint32_t *d_ctr,
  * not touched and stays usable.  Synchronises. */
 wolff_status wolff_selftest_wait_timeout(wolff_ctx *ctx, uint64_t wait_ns, int *observed);
 
+/* ---- an update path that allocates nothing ------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot call cudaMalloc where they run updates: code inside a framework
+ * whose caching allocator already owns the device memory, loops that cannot
+ * afford cudaMalloc's implicit device-wide synchronisation, and programs that
+ * fix their device-memory budget when the library is loaded.
+ *
+ * wolff_step_static runs n_updates updates (t0 .. t0+n-1, the same Philox
+ * streams and results as a context with this dim, L, J, T and seed) on a
+ * caller-owned lattice, using no workspace and allocating nothing.  Its
+ * scratch (control block and cluster list) is a file-scope __device__ array
+ * of WOLFF_STATIC_MAX_SITES 32-bit entries plus 256 bytes (about 4 MiB),
+ * which every GPU that loads the library holds until the process exits.
+ *   d_spins    device int8 lattice of +-1 values (N = L^dim entries, site
+ *              i = x + L*y (+ L*L*z)), 4-byte aligned, with room for
+ *              N rounded up to a multiple of 4 bytes; updated in place.
+ *              Entries other than +-1 are read as -1;
+ *   d_records  nullable, n_updates wolff_record entries;
+ *   stream     cudaStream_t (NULL = default stream); asynchronous.
+ * Returns WOLFF_EINVAL for a bad shape/parameter, a misaligned lattice, or
+ * L^dim > WOLFF_STATIC_MAX_SITES.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one array and it keeps the last call's
+ * contents (each call clears what must start at zero), so calls whose work
+ * overlaps on the GPU -- on different streams, or from different threads --
+ * race and must be serialised by the caller. */
+#define WOLFF_STATIC_MAX_SITES (1u << 20)
+wolff_status wolff_step_static(int dim, int L, double J, double T, uint64_t seed,
+                               uint64_t t0, uint64_t n_updates, void *d_spins,
+                               void *d_records, void *stream);
+
 /* Releases the context (and the workspace if the library allocated it).
  * Synchronises the stream first. */
 wolff_status ising_free(wolff_ctx *ctx);

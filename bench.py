@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--schedule", default="persistent", choices=["persistent", "graph"])
     ap.add_argument("--blocks", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--t-up", type=int, default=None,
+                    help="leader hands wave fronts above this size to all CTAs")
+    ap.add_argument("--t-down", type=int, default=None)
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="bound of the oracle sample timed beside the GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -216,6 +219,9 @@ def main():
     with torch.cuda.stream(stream):
         lat = w.WolffLattice(dim, L, T, seed=seed, stream=stream)
         lat.set_schedule(sched, args.blocks, args.threads)
+        if args.t_up is not None:
+            lat.set_local_thresholds(args.t_up, args.t_down if args.t_down is not None
+                                     else args.t_up // 2)
         info = lat.info()
         rec_buf = lat.record_buffer(U)
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -305,6 +311,7 @@ def main():
                                % (dim, L, T, seed, equil, args.steps, U),
                    "dim": dim, "L": L, "T": T, "seed": seed, "updates_per_step": U,
                    "schedule": args.schedule, "grid_blocks": info["grid_blocks"],
+                   "t_up": args.t_up, "t_down": args.t_down,
                    "block_threads": info["block_threads"],
                    "l2": "256 MB buffer written between timed steps",
                    "parallelism": "replicas x%d" % world},

@@ -158,6 +158,13 @@ wolff_status wolff_set_state(wolff_ctx *ctx, const int8_t *h_spins, uint64_t t);
 wolff_status wolff_set_schedule(wolff_ctx *ctx, int schedule, int grid_blocks,
                                 int block_threads);
 
+/* Persistent schedule: a level whose new wave front exceeds t_up sites is
+ * expanded by all CTAs (grid barrier per level) until a level produces at
+ * most t_down sites, which CTA 0 then expands alone (__syncthreads per
+ * level).  t_up = 0 puts every level on the grid.  Requires
+ * t_down <= t_up <= 2048.  Results do not depend on the values. */
+wolff_status wolff_set_local_thresholds(wolff_ctx *ctx, uint32_t t_up, uint32_t t_down);
+
 wolff_status wolff_get_info(wolff_ctx *ctx, wolff_info *info);
 
 /* Host-side Philox threshold the library uses for (J, T). */

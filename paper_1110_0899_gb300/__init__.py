@@ -76,6 +76,8 @@ def load_library():
         "wolff_set_state": (i, [v, v, u64]),
         "wolff_set_schedule": (i, [v, i, i, i]),
         "wolff_get_info": (i, [v, P(_Info)]),
+        "wolff_set_local_thresholds": (i, [v, u32, u32]),
+        "wolff_step_static": (i, [i, i, d, d, u64, u64, u64, v, v, v]),
         "wolff_bond_threshold": (u64, [d, d]),
         "wolff_philox": (i, [u32, u32, v, v, u64, v]),
         "wolff_selftest_wait_timeout": (i, [v, u64, P(i)]),
@@ -216,6 +218,10 @@ class WolffLattice:
     def set_schedule(self, schedule=SCHED_AUTO, grid_blocks=0, block_threads=0):
         _check(load_library().wolff_set_schedule(self.handle, int(schedule), int(grid_blocks),
                                                  int(block_threads)), self.handle)
+
+    def set_local_thresholds(self, t_up, t_down):
+        _check(load_library().wolff_set_local_thresholds(self.handle, int(t_up), int(t_down)),
+               self.handle)
 
     def info(self):
         inf = _Info()

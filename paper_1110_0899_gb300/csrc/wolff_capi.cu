@@ -47,6 +47,7 @@ struct wolff_ctx {
     void *rec_stage = nullptr;
     size_t rec_stage_bytes = 0;
     unsigned long long wait_ns = 2000000000ull;
+    uint32_t t_up = 512, t_down = 256;
     std::string err;
 };
 
@@ -95,6 +96,8 @@ StepParams make_params(const wolff_ctx *c) {
     p.t0 = c->t_host;
     p.n = 0;
     p.wait_ns = c->wait_ns;
+    p.t_up = c->t_up;
+    p.t_down = c->t_down;
     return p;
 }
 
@@ -235,6 +238,15 @@ wolff_status wolff_set_schedule(wolff_ctx *c, int schedule, int grid_blocks, int
         c->gexec = nullptr;
         c->graph = nullptr;
     }
+    return WOLFF_OK;
+}
+
+wolff_status wolff_set_local_thresholds(wolff_ctx *c, uint32_t t_up, uint32_t t_down) {
+    if (!c) return WOLFF_EINVAL;
+    if (t_up > kLocalFrontierCap || t_down > t_up)
+        return fail(c, WOLFF_EINVAL, "need t_down <= t_up <= 2048");
+    c->t_up = t_up;
+    c->t_down = t_down;
     return WOLFF_OK;
 }
 

@@ -154,47 +154,76 @@ __device__ __forceinline__ void raise_status(DevCtl *ctl, unsigned int code,
     if (atomicCAS(&ctl->status, 0u, code) == 0u) ctl->err_detail = detail;
 }
 
-// ---- bounded grid-wide barrier ----------------------------------------------
-// Sense by generation counter: every CTA adds one arrival; the last arrival
-// resets the count and publishes generation g+1 with a release store; the
-// others poll the generation with acquire loads.  The poll gives up after
-// wait_ns nanoseconds (globaltimer) or 2^28 polls, or when another CTA has
-// already raised an error, records WOLFF_ETIMEOUT, and the barrier returns false so that every
-// CTA leaves the kernel.  `gen` is the CTA's private copy of the generation.
-__device__ __forceinline__ bool grid_barrier(DevCtl *ctl, unsigned int nblocks,
-                                             unsigned int &gen,
-                                             unsigned long long wait_ns,
-                                             unsigned int where) {
-    __shared__ unsigned int s_ok;
+// ---- bounded waits -----------------------------------------------------------
+// Polls *word until it differs from `seen`.  Gives up after wait_ns
+// nanoseconds (globaltimer) without progress or 2^28 polls, or as soon as
+// another CTA has raised an error.  `progress` (nullable) is a word whose
+// change counts as progress and restarts the clock (a worker waiting for the
+// next command while the leader completes updates on its own).  Returns the
+// new value, or `seen` after raising WOLFF_ETIMEOUT / seeing an error.
+__device__ __forceinline__ unsigned int bounded_wait_change(DevCtl *ctl, const unsigned int *word,
+                                                            unsigned int seen,
+                                                            const unsigned long long *progress,
+                                                            unsigned long long wait_ns,
+                                                            unsigned int where, bool *ok) {
+    unsigned long long start = global_ns();
+    unsigned long long last_progress = progress ? *(const volatile unsigned long long *)progress : 0;
+    unsigned int polls = 0;
+    *ok = true;
+    while (true) {
+        const unsigned int v = ld_acquire_u32(word);
+        if (v != seen) return v;
+        if ((++polls & 63u) == 0u) {
+            if (ld_volatile_u32(&ctl->status) != 0u) { *ok = false; return seen; }
+            const unsigned long long now = global_ns();
+            if (progress) {
+                const unsigned long long pv = *(const volatile unsigned long long *)progress;
+                if (pv != last_progress) { last_progress = pv; start = now; }
+            }
+            if (now - start > wait_ns || polls > (1u << 28)) {
+                raise_status(ctl, WOLFF_ETIMEOUT, where);
+                *ok = false;
+                return seen;
+            }
+        }
+    }
+}
+
+// ---- bounded grid-wide barrier that carries the level's append count --------
+// Generation barrier: every CTA adds one arrival; the last arrival takes the
+// append counter (atomicExch to 0, so the next level starts from zero), puts
+// it in the broadcast slot of the new generation, resets the arrival count
+// and publishes generation g+1 with a release store.  The others poll the
+// generation with acquire loads (bounded, see bounded_wait_change).  Every
+// thread of every CTA returns the broadcast count in *value.  Returns false
+// when a wait ran out or another CTA raised an error: the caller must leave.
+// `gen` is the CTA's copy of the generation (meaningful in thread 0).
+__device__ __forceinline__ bool grid_sync(DevCtl *ctl, unsigned int nblocks, unsigned int &gen,
+                                          unsigned long long wait_ns, unsigned int where,
+                                          unsigned int *counter, unsigned int *value) {
+    __shared__ unsigned int s_ok, s_val;
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned int ok = 1;
+        bool ok = true;
         const unsigned int my = gen;
         __threadfence();
         const unsigned int arrived = atomicAdd(&ctl->bar_count, 1u);
         if (arrived == nblocks - 1) {
+            const unsigned int v = counter ? atomicExch(counter, 0u) : 0u;
+            ctl->bcast[(my + 1) & 3u] = v;
             ctl->bar_count = 0;
             st_release_u32(&ctl->bar_gen, my + 1);
         } else {
-            const unsigned long long start = global_ns();
-            unsigned int polls = 0;
-            while (ld_acquire_u32(&ctl->bar_gen) == my) {
-                if ((++polls & 63u) == 0u) {
-                    if (ld_volatile_u32(&ctl->status) != 0u) { ok = 0; break; }
-                    if (global_ns() - start > wait_ns || polls > (1u << 28)) {
-                        raise_status(ctl, WOLFF_ETIMEOUT, where);
-                        ok = 0;
-                        break;
-                    }
-                }
-            }
+            bounded_wait_change(ctl, &ctl->bar_gen, my, nullptr, wait_ns, where, &ok);
         }
         __threadfence();
         gen = my + 1;
-        if (ld_volatile_u32(&ctl->status) != 0u) ok = 0;
-        s_ok = ok;
+        if (ld_volatile_u32(&ctl->status) != 0u) ok = false;
+        s_val = ld_volatile_u32(&ctl->bcast[(my + 1) & 3u]);
+        s_ok = ok ? 1u : 0u;
     }
     __syncthreads();
+    if (value) *value = s_val;
     return s_ok != 0u;
 }
 

@@ -2,7 +2,7 @@
 //
 // Device memory of one context (the caller's workspace), 256-byte aligned
 // pieces:
-//   [DevCtl, 256 B][spins: N bytes, padded to 256][list: N x u32]
+//   [DevCtl][self-test DevCtl][spins: N bytes, padded to 256][list: N x u32]
 // spins: one byte per site, bit 0 = current spin, bit 1 = spin at the start
 //   of the running update (+1 stored as 1).  Between updates the two bits are
 //   equal, so a byte is 0x00 (-1) or 0x03 (+1).  Claiming a site flips bit 0
@@ -23,10 +23,12 @@ constexpr uint32_t kTagBond = 0;
 constexpr uint32_t kTagSeed = 1;
 constexpr uint32_t kTagInit = 2;
 
-// Control block living at the start of the workspace.  Plain fields are only
-// touched by one thread at a time; counters marked (atomic) are shared.
-struct alignas(256) DevCtl {
-    // chain state
+// Control block living at the start of the workspace.  Fields are grouped
+// into 128-byte lines by who touches them: the chain state (one thread at a
+// time), the grid barrier, the leader's command word, the append counters and
+// the graph schedule's state.
+struct alignas(128) DevCtl {
+    // line 0: chain state
     unsigned long long t;          // next update index
     long long E;                   // bond sum
     long long M;                   // magnetisation
@@ -35,25 +37,32 @@ struct alignas(256) DevCtl {
     unsigned int last_levels;
     unsigned int status;           // 0 or a wolff_status (atomic, first wins)
     unsigned int err_detail;       // where a bounded wait gave up, etc.
-    // growth scratch
-    unsigned int cnt[4];           // level append counters (atomic)
-    long long dE;                  // boundary-bond sum of this update (atomic)
-    unsigned int bar_count;        // grid barrier arrivals (atomic)
-    unsigned int bar_gen;          // grid barrier generation
-    // graph schedule state
-    unsigned int lo, hi;           // current frontier = list[lo, hi)
-    unsigned int levels;
-    unsigned int done;             // blocks finished in this kernel (atomic)
-    unsigned int sig0bit;          // seed spin (1 = +1) of the running update
-    unsigned int pad0;
-    unsigned long long t_end;      // graph loop stops when t == t_end
-    unsigned long long rec_t0;     // t of records[0] for this call
-    wolff_record *records;         // destination of this call's records
-    // full recount
-    long long full_E;
+    long long full_E;              // full recount results
     long long full_M;
+    // line 1: grid barrier
+    alignas(128) unsigned int bar_count;   // arrivals (atomic)
+    unsigned int bar_gen;                  // generation
+    unsigned int bcast[4];                 // per-generation broadcast slot
+    // line 2: leader -> worker commands
+    alignas(128) unsigned int cmd_seq;
+    unsigned int cmd_kind;
+    unsigned int cmd_lo, cmd_hi, cmd_level, cmd_sig0bit;
+    unsigned long long cmd_t;
+    unsigned long long cmd_rec;            // record index of the update
+    // line 3: append counters and the boundary-bond sum
+    alignas(128) unsigned int cnt[4];      // (atomic)
+    long long dE;                          // (atomic)
+    // line 4: graph schedule state
+    alignas(128) unsigned int lo, hi;      // current frontier = list[lo, hi)
+    unsigned int levels;
+    unsigned int done;                     // CTAs finished in this kernel (atomic)
+    unsigned int sig0bit;                  // seed spin (1 = +1) of the running update
+    unsigned int pad0;
+    unsigned long long t_end;              // graph loop stops when t == t_end
+    unsigned long long rec_t0;             // t of records[0] for this call
+    wolff_record *records;                 // destination of this call's records
 };
-static_assert(sizeof(DevCtl) == 256, "control block must stay 256 bytes");
+static_assert(sizeof(DevCtl) % 256 == 0 && sizeof(DevCtl) <= 1024, "control block layout");
 
 struct Geometry {
     uint32_t L;
@@ -72,7 +81,14 @@ struct StepParams {
     unsigned long long t0;      // first update of this launch
     unsigned long long n;       // updates in this launch
     unsigned long long wait_ns; // bound of every device-side wait
+    uint32_t t_up;              // leader hands a frontier larger than this to the grid
+    uint32_t t_down;            // grid hands a frontier this small back to the leader
 };
+
+// Leader-local frontier capacity (shared memory) and the cluster-list prefix
+// kept in shared memory for the leader-only energy/unmark pass.
+constexpr uint32_t kLocalFrontierCap = 2048;
+constexpr uint32_t kLocalListCap = 4096;
 
 // Launch helpers implemented in wolff_kernels.cu (C++ linkage, internal).
 cudaError_t launch_init(uint8_t *spins, Geometry g, uint32_t k0, uint32_t k1,

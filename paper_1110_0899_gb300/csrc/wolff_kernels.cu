@@ -183,7 +183,7 @@ cudaError_t launch_reset_ctl(DevCtl *ctl, unsigned long long t, cudaStream_t s) 
 // two, so only the time limit can end the wait.
 __global__ void k_selftest_wait(DevCtl *scratch, unsigned long long wait_ns) {
     unsigned int gen = 0;
-    grid_barrier(scratch, 2u, gen, wait_ns, 0x7E57u);
+    grid_sync(scratch, 2u, gen, wait_ns, 0x7E57u, nullptr, nullptr);
 }
 
 cudaError_t launch_selftest_wait(DevCtl *scratch, unsigned long long wait_ns, cudaStream_t s) {
@@ -250,8 +250,8 @@ __device__ __forceinline__ void unmark_range(const StepParams &p, uint32_t C, ui
 __device__ __forceinline__ void finish_update(const StepParams &p, DevCtl *ctl,
                                               wolff_record *records, unsigned long long rec_index,
                                               uint32_t C, uint32_t levels, uint32_t sig0bit,
-                                              unsigned long long t) {
-    const long long dE = *reinterpret_cast<volatile long long *>(&ctl->dE);
+                                              unsigned long long t, long long dE_local) {
+    const long long dE = *reinterpret_cast<volatile long long *>(&ctl->dE) + dE_local;
     const long long E = ctl->E + 2 * dE;
     const long long M = ctl->M + (sig0bit ? -2LL : 2LL) * (long long)C;
     ctl->E = E;
@@ -273,52 +273,243 @@ __device__ __forceinline__ void finish_update(const StepParams &p, DevCtl *ctl,
 }
 
 // ---------------------------------------------------------------------------
-// Persistent cooperative schedule.
+// Persistent cooperative schedule: a leader CTA and worker CTAs.
+//
+// CTA 0 (the leader) runs every update.  While the wave front is small it
+// grows the cluster alone -- frontier and cluster-list prefix in shared
+// memory, __syncthreads as the level barrier -- which is the on-GPU form of
+// the paper's hybrid (section 6: small wave fronts are cheaper on one
+// processor).  When a level produces more than t_up new sites it publishes a
+// GROW command and all CTAs expand the following levels together, separated
+// by the bounded grid barrier, until a level produces t_down sites or fewer;
+// then the workers go back to waiting and the leader continues alone.  A
+// cluster that fits the shared-memory list and never went to the grid is
+// closed by the leader alone; otherwise a FINISH command runs the energy and
+// unmark passes on all CTAs.  t_up = 0 gives the plain grid-synchronous
+// schedule (every level on all CTAs).
+
+enum : unsigned int { kCmdGrow = 1, kCmdFinish = 2, kCmdExit = 3 };
+
+struct SharedLocal {
+    uint32_t front[2][kLocalFrontierCap];
+    uint32_t list[kLocalListCap];
+    unsigned int cnt[3];
+    unsigned int flag;
+    unsigned int cmd[8];
+};
+
+// All CTAs: expand list[lo, hi) level after level until the next frontier is
+// empty (*finished = true) or holds t_down sites or fewer.
+template <int DIM>
+__device__ __forceinline__ bool grid_levels(const StepParams &p, unsigned int &gen, uint32_t &lo,
+                                            uint32_t &hi, uint32_t &level, uint32_t sig0bit,
+                                            uint32_t tlo, uint32_t thi, bool *finished) {
+    DevCtl *ctl = p.ctl;
+    while (true) {
+        expand_range<DIM>(p, lo, hi, sig0bit, tlo, thi, &ctl->cnt[0]);
+        unsigned int added = 0;
+        if (!grid_sync(ctl, gridDim.x, gen, p.wait_ns, 1, &ctl->cnt[0], &added)) return false;
+        ++level;
+        if (added > p.g.N - hi) {   // cannot happen: every site joins at most once
+            if (blockIdx.x == 0 && threadIdx.x == 0) raise_status(ctl, WOLFF_EINVAL, 0xC1u);
+            return false;
+        }
+        lo = hi;
+        hi += added;
+        if (added == 0) { *finished = true; return true; }
+        if (added <= p.t_down) { *finished = false; return true; }
+    }
+}
+
+// All CTAs: energy change over list[0, C), then unmark, then close the update.
+template <int DIM>
+__device__ __forceinline__ bool grid_finish(const StepParams &p, unsigned int &gen, uint32_t C,
+                                            uint32_t levels, uint32_t sig0bit,
+                                            unsigned long long t, unsigned long long rec) {
+    DevCtl *ctl = p.ctl;
+    const long long acc = block_sum(boundary_range<DIM>(p, C, sig0bit));
+    if (threadIdx.x == 0 && acc != 0)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->dE), (unsigned long long)acc);
+    if (!grid_sync(ctl, gridDim.x, gen, p.wait_ns, 2, nullptr, nullptr)) return false;
+    unmark_range<DIM>(p, C, sig0bit);
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        finish_update(p, ctl, p.records, rec, C, levels, sig0bit, t, 0);
+    return grid_sync(ctl, gridDim.x, gen, p.wait_ns, 3, nullptr, nullptr);
+}
+
+// Leader thread 0: publish a command to the workers (release on cmd_seq).
+__device__ __forceinline__ void publish(DevCtl *ctl, unsigned int &seq, unsigned int kind,
+                                        uint32_t lo, uint32_t hi, uint32_t level,
+                                        uint32_t sig0bit, unsigned long long t,
+                                        unsigned long long rec) {
+    ctl->cmd_kind = kind;
+    ctl->cmd_lo = lo;
+    ctl->cmd_hi = hi;
+    ctl->cmd_level = level;
+    ctl->cmd_sig0bit = sig0bit;
+    ctl->cmd_t = t;
+    ctl->cmd_rec = rec;
+    __threadfence();
+    seq += 1;
+    st_release_u32(&ctl->cmd_seq, seq);
+}
+
+template <int DIM>
+__device__ void worker_loop(const StepParams &p, SharedLocal &sh, unsigned int &gen,
+                            unsigned int seq) {
+    DevCtl *ctl = p.ctl;
+    while (true) {
+        if (threadIdx.x == 0) {
+            bool ok = true;
+            const unsigned int v = bounded_wait_change(ctl, &ctl->cmd_seq, seq, &ctl->t,
+                                                       p.wait_ns, 4, &ok);
+            if (!ok) {
+                sh.cmd[0] = kCmdExit;
+            } else {
+                seq = v;
+                sh.cmd[0] = ld_volatile_u32(&ctl->cmd_kind);
+                sh.cmd[1] = ctl->cmd_lo;
+                sh.cmd[2] = ctl->cmd_hi;
+                sh.cmd[3] = ctl->cmd_level;
+                sh.cmd[4] = ctl->cmd_sig0bit;
+                const unsigned long long t = ctl->cmd_t, rec = ctl->cmd_rec;
+                sh.cmd[5] = (uint32_t)t;
+                sh.cmd[6] = (uint32_t)(t >> 32);
+                sh.cmd[7] = (uint32_t)rec;
+            }
+        }
+        __syncthreads();
+        const unsigned int kind = sh.cmd[0];
+        uint32_t lo = sh.cmd[1], hi = sh.cmd[2], level = sh.cmd[3];
+        const uint32_t sig0bit = sh.cmd[4], tlo = sh.cmd[5], thi = sh.cmd[6];
+        __syncthreads();
+        if (kind == kCmdGrow) {
+            bool finished = false;
+            if (!grid_levels<DIM>(p, gen, lo, hi, level, sig0bit, tlo, thi, &finished)) return;
+        } else if (kind == kCmdFinish) {
+            const unsigned long long t = ((unsigned long long)thi << 32) | tlo;
+            if (!grid_finish<DIM>(p, gen, hi, level, sig0bit, t, 0)) return;
+        } else {
+            return;
+        }
+    }
+}
+
 template <int DIM>
 __global__ void __launch_bounds__(1024) k_persistent(StepParams p) {
     DevCtl *ctl = p.ctl;
-    __shared__ unsigned int s_gen;
-    if (threadIdx.x == 0) s_gen = ld_volatile_u32(&ctl->bar_gen);
+    __shared__ SharedLocal sh;
+    __shared__ unsigned int s_gen, s_seq;
+    if (threadIdx.x == 0) {
+        s_gen = ld_volatile_u32(&ctl->bar_gen);
+        s_seq = ld_volatile_u32(&ctl->cmd_seq);
+    }
     __syncthreads();
-    unsigned int gen = s_gen;   // meaningful in thread 0 only
-    const unsigned int nblocks = gridDim.x;
-    const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned int gen = s_gen;   // meaningful in thread 0
+    unsigned int seq = s_seq;
+    // every CTA has read the command sequence before the leader can publish
+    if (!grid_sync(ctl, gridDim.x, gen, p.wait_ns, 5, nullptr, nullptr)) return;
+    if (blockIdx.x != 0) {
+        worker_loop<DIM>(p, sh, gen, seq);
+        return;
+    }
+    const bool t0 = threadIdx.x == 0;
+    const uint32_t nwarps = blockDim.x >> 5;
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t t_up = min(p.t_up, kLocalFrontierCap);
 
     for (unsigned long long u = 0; u < p.n; ++u) {
         const unsigned long long t = p.t0 + u;
         const uint32_t tlo = (uint32_t)t, thi = (uint32_t)(t >> 32);
         const uint32_t i0 = seed_site(p, t);
-        // bit 1 holds the spin at the start of the update and never changes
-        // during growth, so every CTA can read the seed spin at any time
-        const uint32_t sig0bit = (__ldcg(p.spins + i0) >> 1) & 1u;
-        if (leader) {
+        const uint32_t sig0bit = (p.spins[i0] >> 1) & 1u;
+        if (t0) {
             claim_site(p.spins, i0, sig0bit);
-            p.list[0] = pack_index<DIM>(p.g, i0);
+            const uint32_t p0 = pack_index<DIM>(p.g, i0);
+            p.list[0] = p0;
+            sh.list[0] = p0;
+            sh.front[0][0] = p0;
+            sh.cnt[0] = sh.cnt[1] = sh.cnt[2] = 0;
+            sh.flag = ld_volatile_u32(&ctl->status);
         }
-        uint32_t lo = 0, hi = 1, level = 0;
-        while (true) {
-            expand_range<DIM>(p, lo, hi, sig0bit, tlo, thi, &ctl->cnt[level % 3]);
-            if (leader) ctl->cnt[(level + 1) % 3] = 0;
-            if (!grid_barrier(ctl, nblocks, gen, p.wait_ns, 1)) return;
-            const uint32_t added = ld_volatile_u32(&ctl->cnt[level % 3]);
-            ++level;
-            if (added == 0) break;
-            if (added > p.g.N - hi) {   // cannot happen: each site joins once
-                if (leader) raise_status(ctl, WOLFF_EINVAL, 0xC1u);
-                return;
+        __syncthreads();
+        if (sh.flag != 0u) break;
+        uint32_t C = 1, f = 1, level = 0, cur = 0;
+        bool went_grid = false, ok = true;
+        while (f > 0) {
+            if (f > t_up) {
+                // hand the wave front list[C-f, C) to all CTAs
+                went_grid = true;
+                if (t0) publish(ctl, seq, kCmdGrow, C - f, C, level, sig0bit, t, u);
+                uint32_t lo = C - f, hi = C;
+                bool finished = false;
+                if (!grid_levels<DIM>(p, gen, lo, hi, level, sig0bit, tlo, thi, &finished)) {
+                    ok = false;
+                    break;
+                }
+                C = hi;
+                f = finished ? 0u : hi - lo;
+                if (f) {   // back to the leader: load the small front
+                    for (uint32_t k = threadIdx.x; k < f; k += blockDim.x)
+                        sh.front[cur][k] = __ldcg(p.list + lo + k);
+                    if (t0) sh.cnt[0] = sh.cnt[1] = sh.cnt[2] = 0;
+                    __syncthreads();
+                }
+                continue;
             }
-            lo = hi;
-            hi += added;
+            // one level on the leader alone
+            const uint32_t nxt = cur ^ 1u;
+            unsigned int *cnt = &sh.cnt[level % 3];
+            if (t0) sh.cnt[(level + 1) % 3] = 0;
+            for (uint32_t base = warp * 32u; base < f; base += nwarps * 32u) {
+                const uint32_t k = base + lane;
+                Neighbours<DIM> nb;
+                uint32_t won = 0;
+                if (k < f) won = expand_site<DIM>(p, sh.front[cur][k], sig0bit, tlo, thi, nb);
+                uint32_t pos = warp_reserve(cnt, __popc(won));
+#pragma unroll
+                for (int s = 0; s < 2 * DIM; ++s) {
+                    if (won & (1u << s)) {
+                        const uint32_t gpos = C + pos;
+                        if (gpos < p.g.N) p.list[gpos] = nb.packed[s];
+                        else raise_status(ctl, WOLFF_EINVAL, 0xC3u);
+                        if (gpos < kLocalListCap) sh.list[gpos] = nb.packed[s];
+                        if (pos < kLocalFrontierCap) sh.front[nxt][pos] = nb.packed[s];
+                        ++pos;
+                    }
+                }
+            }
+            __syncthreads();
+            const uint32_t added = *cnt;
+            ++level;
+            C += added;
+            f = added;
+            cur = nxt;
         }
-        const uint32_t C = hi;
-        const long long acc = block_sum(boundary_range<DIM>(p, C, sig0bit));
-        if (threadIdx.x == 0 && acc != 0)
-            atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->dE), (unsigned long long)acc);
-        if (!grid_barrier(ctl, nblocks, gen, p.wait_ns, 2)) return;
-        unmark_range<DIM>(p, C, sig0bit);
-        if (leader) finish_update(p, ctl, p.records, u, C, level, sig0bit, t);
-        if (!grid_barrier(ctl, nblocks, gen, p.wait_ns, 3)) return;
+        if (!ok) return;
+        if (went_grid || C > kLocalListCap) {
+            if (t0) publish(ctl, seq, kCmdFinish, 0, C, level, sig0bit, t, u);
+            if (!grid_finish<DIM>(p, gen, C, level, sig0bit, t, u)) return;
+        } else {
+            // the leader closes a small cluster alone from its shared list
+            long long acc = 0;
+            for (uint32_t k = threadIdx.x; k < C; k += blockDim.x) {
+                uint32_t i;
+                acc += boundary_term<DIM>(p, sh.list[k], sig0bit, &i);
+            }
+            acc = block_sum(acc);
+            __syncthreads();
+            const uint8_t v = sig0bit ? 0x00 : 0x03;
+            for (uint32_t k = threadIdx.x; k < C; k += blockDim.x) {
+                uint32_t c[DIM];
+                unpack<DIM>(sh.list[k], c);
+                p.spins[site_index<DIM>(p.g, c)] = v;
+            }
+            if (t0) finish_update(p, ctl, p.records, u, C, level, sig0bit, t, acc);
+            __syncthreads();
+        }
     }
+    if (t0) publish(ctl, seq, kCmdExit, 0, 0, 0, 0, 0, 0);
 }
 
 const void *persistent_kernel(int dim) {
@@ -408,7 +599,7 @@ __global__ void __launch_bounds__(1024) k_graph_finish(StepParams p,
     if (last_block_done(ctl) && threadIdx.x == 0) {
         const unsigned long long t = ctl->t;
         ctl->done = 0;
-        finish_update(p, ctl, ctl->records, t - ctl->rec_t0, C, ctl->levels, sig0bit, t);
+        finish_update(p, ctl, ctl->records, t - ctl->rec_t0, C, ctl->levels, sig0bit, t, 0);
         cudaGraphSetConditional(h_update, (t + 1 < ctl->t_end) ? 1u : 0u);
     }
 }

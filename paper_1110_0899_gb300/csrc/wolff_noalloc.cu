@@ -90,6 +90,8 @@ extern "C" wolff_status wolff_step_static(int dim, int L, double J, double T, ui
     p.t0 = t0;
     p.n = n_updates;
     p.wait_ns = 2000000000ull;
+    p.t_up = 512;
+    p.t_down = 256;
 
     // every call starts from a cleared control block: the array keeps the
     // previous call's contents

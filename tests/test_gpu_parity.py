@@ -121,6 +121,28 @@ def test_medium_lattices(sched):
         assert np.array_equal(spins, s_ref)
 
 
+THRESHOLDS = [(0, 0), (1, 1), (8, 4), (64, 8), (512, 256), (2048, 2048)]
+
+
+@pytest.mark.parametrize("t_up,t_down", THRESHOLDS)
+def test_leader_grid_handoffs(t_up, t_down):
+    """Large clusters from an ordered start cross between the leader-only and
+    the all-CTA phases many times; every threshold gives the oracle's chain."""
+    torch, w = require_cuda()
+    for dim, L, T, n in ((2, 256, TC2, 40), (3, 32, 4.5115, 30), (2, 100, 2.1, 30)):
+        up = np.ones(L ** dim, dtype=np.int8)
+        ref, s_ref = oracle_trajectory(dim, L, T, 31, n, s=up)
+        lat = w.WolffLattice(dim, L, T, seed=31)
+        lat.set_local_thresholds(t_up, t_down)
+        lat.set_state(up, 0)
+        rec = lat.step(n)
+        spins, _ = lat.get_state()
+        assert (lat.measure()[:2]) == lat.measure_full()
+        lat.close()
+        assert_records_equal(rec, ref, "%dD L=%d thresholds %d/%d" % (dim, L, t_up, t_down))
+        assert np.array_equal(spins, s_ref)
+
+
 def test_checkpoint_resume_and_segments():
     torch, w = require_cuda()
     dim, L, T, seed = 2, 128, TC2, 9

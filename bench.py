@@ -38,9 +38,15 @@ UNIT = "flipped spins/s"
 # neighbour re-read 2D B, mark write 1 B)
 ALGO_BYTES_PER_FLIP = {2: 23.0, 3: 27.0}
 
+TC2 = 2.0 / math.log(1.0 + math.sqrt(2.0))
 WORKLOADS = {
-    "2d": dict(dim=2, L=4096, T=2.0 / math.log(1.0 + math.sqrt(2.0)), seed=2, equil=2000),
-    "3d": dict(dim=3, L=256, T=4.5115, seed=3, equil=2000),
+    # the configurations as specified: random start, 2000 equilibration updates
+    "2d": dict(dim=2, L=4096, T=TC2, seed=2, equil=2000, start="random"),
+    "3d": dict(dim=3, L=256, T=4.5115, seed=3, equil=2000, start="random"),
+    # the same lattices at equilibrium (ordered start, which the cluster
+    # update equilibrates quickly at T_c), where clusters are large
+    "2d-eq": dict(dim=2, L=4096, T=TC2, seed=2, equil=1000, start="ordered"),
+    "3d-eq": dict(dim=3, L=256, T=4.5115, seed=3, equil=1000, start="ordered"),
 }
 
 
@@ -53,7 +59,7 @@ def parse():
     ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS))
     ap.add_argument("--updates-per-step", type=int, default=100)
     ap.add_argument("--equil", type=int, default=None)
-    ap.add_argument("--schedule", default="persistent", choices=["persistent", "graph"])
+    ap.add_argument("--schedule", default="persistent", choices=["persistent", "graph", "cluster"])
     ap.add_argument("--blocks", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--t-up", type=int, default=None,
@@ -213,7 +219,8 @@ def main():
     seed = wl["seed"] + rank
     equil = wl["equil"] if args.equil is None else args.equil
     U = args.updates_per_step
-    sched = {"persistent": w.SCHED_PERSISTENT, "graph": w.SCHED_GRAPH}[args.schedule]
+    sched = {"persistent": w.SCHED_PERSISTENT, "graph": w.SCHED_GRAPH,
+             "cluster": w.SCHED_CLUSTER}[args.schedule]
 
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -223,6 +230,8 @@ def main():
             lat.set_local_thresholds(args.t_up, args.t_down if args.t_down is not None
                                      else args.t_up // 2)
         info = lat.info()
+        if wl["start"] == "ordered":
+            lat.set_state(np.ones(lat.N, dtype=np.int8), 0)
         rec_buf = lat.record_buffer(U)
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
         # equilibration (untimed)
@@ -237,6 +246,7 @@ def main():
         for _ in range(args.warmup):
             w.wolff_step(lat.handle, U, rec_buf)
         torch.cuda.synchronize()
+        stats0 = lat.stats()
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         recs = []
@@ -253,6 +263,7 @@ def main():
             recs.append(rec_buf[: U * w.RECORD_BYTES].clone())
         torch.cuda.synchronize()
         clk = clocks.stop()
+        stats1 = lat.stats()
         if world > 1:
             torch.distributed.barrier()
         step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
@@ -294,21 +305,22 @@ def main():
     achieved = ALGO_BYTES_PER_FLIP[dim] * per_launch_flips / avg_launch_s / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-            "peak_kind": peak_kind, "kernel": "k_persistent<%d>" % dim if
-            args.schedule == "persistent" else "k_graph_level<%d>" % dim}
+            "peak_kind": peak_kind,
+            "kernel": {"persistent": "k_persistent<%d>", "graph": "k_graph_level<%d>",
+                       "cluster": "k_team<%d>"}[args.schedule] % dim}
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(dim, L, T, seed, snap, t_snap, args.cpu_seconds)
-    launches = args.steps if args.schedule == "persistent" else int(
+    launches = args.steps if args.schedule != "graph" else int(
         args.steps + (levels + 3).sum())
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
         "data": "synthetic",
-        "config": {"workload": "%dD L=%d T=%.6g J=1 seed %d, %d equilibration + %d x %d "
+        "config": {"workload": "%dD L=%d T=%.6g J=1 seed %d, %s start, %d equilibration + %d x %d "
                                "recorded updates, one lattice per launch"
-                               % (dim, L, T, seed, equil, args.steps, U),
+                               % (dim, L, T, seed, wl["start"], equil, args.steps, U),
                    "dim": dim, "L": L, "T": T, "seed": seed, "updates_per_step": U,
                    "schedule": args.schedule, "grid_blocks": info["grid_blocks"],
                    "t_up": args.t_up, "t_down": args.t_down,
@@ -319,7 +331,7 @@ def main():
         "clocks": clk,
         "detail": {"mean_cluster": flips / len(records), "mean_levels": float(levels.mean()),
                    "max_levels": int(levels.max()), "ms_per_update": total_ms / len(records),
-                   "p50_update_ms": None},
+                   "persistent_counters": {k: stats1[k] - stats0[k] for k in stats1}},
     }
     print(json.dumps(line), flush=True)
     lat.close()

@@ -61,14 +61,20 @@ enum { WOLFF_LAYOUT_INT8 = 0 };
 
 /* How one update's levels are synchronised (section 3 of the paper replaced):
  *   PERSISTENT  one cooperative launch per wolff_step; all updates and levels
- *               run inside it, separated by a bounded grid-wide barrier;
+ *               run inside it; CTA 0 grows small wave fronts alone and hands
+ *               large ones to every CTA, levels then separated by a bounded
+ *               grid-wide barrier;
  *   GRAPH       a CUDA graph: one kernel node per level inside a conditional
  *               WHILE node, nested inside a WHILE node over updates;
+ *   CLUSTER     one thread-block cluster (1..16 CTAs) per lattice: CTA 0
+ *               grows small fronts alone, larger ones are shared by the
+ *               cluster with the hardware cluster barrier between levels;
  *   AUTO        the library's choice (see wolff_set_schedule). */
 enum {
     WOLFF_SCHED_AUTO = 0,
     WOLFF_SCHED_PERSISTENT = 1,
-    WOLFF_SCHED_GRAPH = 2
+    WOLFF_SCHED_GRAPH = 2,
+    WOLFF_SCHED_CLUSTER = 3
 };
 
 /* One record per update, written after the update's flip
@@ -153,8 +159,10 @@ wolff_status wolff_get_state(wolff_ctx *ctx, int8_t *h_spins, uint64_t *t);
 wolff_status wolff_set_state(wolff_ctx *ctx, const int8_t *h_spins, uint64_t t);
 
 /* Chooses the schedule and the CTA shape of the growth kernels (0 = keep /
- * library default).  The persistent schedule caps grid_blocks at what can be
- * co-resident.  Results do not depend on the choice. */
+ * library default).  For PERSISTENT and GRAPH grid_blocks is the number of
+ * CTAs (PERSISTENT caps it at what can be co-resident); for CLUSTER it is the
+ * cluster size (1, 2, 4, 8 or 16; 16 needs a GPU that allows non-portable
+ * cluster sizes).  Results do not depend on the choice. */
 wolff_status wolff_set_schedule(wolff_ctx *ctx, int schedule, int grid_blocks,
                                 int block_threads);
 
@@ -166,6 +174,22 @@ wolff_status wolff_set_schedule(wolff_ctx *ctx, int schedule, int grid_blocks,
 wolff_status wolff_set_local_thresholds(wolff_ctx *ctx, uint32_t t_up, uint32_t t_down);
 
 wolff_status wolff_get_info(wolff_ctx *ctx, wolff_info *info);
+
+/* Counters of the persistent schedule, accumulated since ising_init or the
+ * last wolff_set_state (tracing aid; the leader CTA's thread 0 keeps them). */
+typedef struct {
+    uint64_t updates;
+    uint64_t levels_local;     /* levels grown by the leader CTA alone */
+    uint64_t levels_grid;      /* levels grown by all CTAs */
+    uint64_t ns_local;         /* device time (globaltimer) in leader-only growth */
+    uint64_t ns_grid;          /* device time in all-CTA growth phases */
+    uint64_t ns_finish;        /* device time closing updates (energy, unmark, record) */
+    uint64_t handoffs;         /* leader -> all-CTA hand-offs */
+    uint64_t grid_finishes;    /* updates closed by all CTAs */
+} wolff_stats;
+
+/* Reads the counters above.  Synchronises. */
+wolff_status wolff_get_stats(wolff_ctx *ctx, wolff_stats *stats);
 
 /* Host-side Philox threshold the library uses for (J, T). */
 uint64_t wolff_bond_threshold(double J, double T);
@@ -213,6 +237,32 @@ wolff_status wolff_selftest_wait_timeout(wolff_ctx *ctx, uint64_t wait_ns, int *
 wolff_status wolff_step_static(int dim, int L, double J, double T, uint64_t seed,
                                uint64_t t0, uint64_t n_updates, void *d_spins,
                                void *d_records, void *stream);
+
+/* ---- batched form: many lattices in one launch ----------------------------
+ * A batch runs the next updates of several contexts in one kernel launch,
+ * one thread-block cluster per context (the CLUSTER schedule's engine), so
+ * hundreds of small lattices share the GPU instead of running one lattice per
+ * launch.  Every context keeps its own chain: the results are those of
+ * wolff_step on each context alone.  The batch owns a small descriptor table
+ * on the device and a pinned host staging copy of it. */
+typedef struct wolff_batch wolff_batch;
+
+/* capacity: most contexts one wolff_batch_run may take; stream: where the
+ * batched launches go (NULL = default stream). */
+wolff_status wolff_batch_create(wolff_batch **out, int capacity, void *stream);
+
+/* Enqueues n_updates[i] updates of ctxs[i] for i < n (0 skips a context),
+ * records to d_records[i] (nullable entries).  The contexts must be distinct,
+ * live on the batch's device, and have no work pending on other streams.
+ * Larger lattices are launched first.  cluster_size (1..16) and
+ * block_threads (multiple of 32, <= 1024) set the team shape.  Asynchronous
+ * on the batch's stream; device errors are reported by each context's next
+ * synchronising call. */
+wolff_status wolff_batch_run(wolff_batch *b, wolff_ctx *const *ctxs, int n,
+                             const uint64_t *n_updates, void *const *d_records,
+                             int cluster_size, int block_threads);
+
+wolff_status wolff_batch_free(wolff_batch *b);
 
 /* Releases the context (and the workspace if the library allocated it).
  * Synchronises the stream first. */

@@ -21,7 +21,7 @@ WOLFF_OK, WOLFF_EINVAL, WOLFF_ENOMEM, WOLFF_ECUDA, WOLFF_ETIMEOUT, WOLFF_EUNSUPP
 STATUS_NAMES = {0: "WOLFF_OK", 1: "WOLFF_EINVAL", 2: "WOLFF_ENOMEM", 3: "WOLFF_ECUDA",
                 4: "WOLFF_ETIMEOUT", 5: "WOLFF_EUNSUPPORTED"}
 LAYOUT_INT8 = 0
-SCHED_AUTO, SCHED_PERSISTENT, SCHED_GRAPH = 0, 1, 2
+SCHED_AUTO, SCHED_PERSISTENT, SCHED_GRAPH, SCHED_CLUSTER = 0, 1, 2, 3
 
 RECORD_DTYPE = np.dtype([("C", "<u4"), ("levels", "<u4"), ("E", "<i8"), ("M", "<i8")])
 RECORD_BYTES = RECORD_DTYPE.itemsize  # 24
@@ -43,6 +43,12 @@ class _Info(ctypes.Structure):
                 ("schedule", ctypes.c_int), ("grid_blocks", ctypes.c_int),
                 ("block_threads", ctypes.c_int), ("sm_count", ctypes.c_int),
                 ("workspace_bytes", ctypes.c_size_t)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in
+                ("updates", "levels_local", "levels_grid", "ns_local", "ns_grid", "ns_finish",
+                 "handoffs", "grid_finishes")]
 
 
 _lib = None
@@ -77,6 +83,10 @@ def load_library():
         "wolff_set_schedule": (i, [v, i, i, i]),
         "wolff_get_info": (i, [v, P(_Info)]),
         "wolff_set_local_thresholds": (i, [v, u32, u32]),
+        "wolff_get_stats": (i, [v, P(_Stats)]),
+        "wolff_batch_create": (i, [P(v), i, v]),
+        "wolff_batch_run": (i, [v, v, i, v, v, i, i]),
+        "wolff_batch_free": (i, [v]),
         "wolff_step_static": (i, [i, i, d, d, u64, u64, u64, v, v, v]),
         "wolff_bond_threshold": (u64, [d, d]),
         "wolff_philox": (i, [u32, u32, v, v, u64, v]),
@@ -228,6 +238,11 @@ class WolffLattice:
         _check(load_library().wolff_get_info(self.handle, ctypes.byref(inf)), self.handle)
         return {k: getattr(inf, k) for k, _ in _Info._fields_}
 
+    def stats(self):
+        st = _Stats()
+        _check(load_library().wolff_get_stats(self.handle, ctypes.byref(st)), self.handle)
+        return {k: int(getattr(st, k)) for k, _ in _Stats._fields_}
+
     def record_buffer(self, n):
         torch = _torch()
         need = int(n) * RECORD_BYTES
@@ -277,3 +292,41 @@ class WolffLattice:
             self.close()
         except Exception:
             pass
+
+
+class WolffBatch:
+    """Runs the next updates of many WolffLattice objects in one launch (one
+    thread-block cluster per lattice).  Each lattice's chain is the one it
+    would follow alone."""
+
+    def __init__(self, capacity, stream=None):
+        self.handle = ctypes.c_void_p()
+        _check(load_library().wolff_batch_create(ctypes.byref(self.handle), int(capacity),
+                                                 _stream_handle(stream)))
+        self.capacity = int(capacity)
+
+    def run(self, lattices, n_updates, records=None, cluster_size=1, block_threads=256):
+        """lattices: list of WolffLattice; n_updates: int or per-lattice list;
+        records: None or a list of device uint8 tensors (or None entries)."""
+        n = len(lattices)
+        if isinstance(n_updates, int):
+            n_updates = [n_updates] * n
+        ctxs = (ctypes.c_void_p * n)(*[lat.handle.value for lat in lattices])
+        nu = (ctypes.c_uint64 * n)(*[int(x) for x in n_updates])
+        recs = None
+        if records is not None:
+            recs = (ctypes.c_void_p * n)(*[None if r is None else r.data_ptr() for r in records])
+        _check(load_library().wolff_batch_run(self.handle, ctxs, n, nu, recs, int(cluster_size),
+                                              int(block_threads)))
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            load_library().wolff_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

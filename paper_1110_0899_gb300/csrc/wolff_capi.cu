@@ -10,6 +10,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 
@@ -48,6 +49,7 @@ struct wolff_ctx {
     size_t rec_stage_bytes = 0;
     unsigned long long wait_ns = 2000000000ull;
     uint32_t t_up = 512, t_down = 256;
+    int cluster = 8;
     std::string err;
 };
 
@@ -116,6 +118,11 @@ wolff_status sync_and_check(wolff_ctx *c, DevCtl *host_copy) {
         return (wolff_status)dst->status;
     }
     return WOLFF_OK;
+}
+
+// Every cluster-list slot holds kEmptySlot between updates.
+cudaError_t empty_list(wolff_ctx *c) {
+    return cudaMemsetAsync(c->list, 0xFF, (size_t)c->N * sizeof(uint32_t), c->stream);
 }
 
 int default_blocks(const wolff_ctx *c) {
@@ -205,6 +212,7 @@ wolff_status ising_init(wolff_ctx **out, int dim, int L, double J, double T, uin
 
     const StepParams p = make_params(c);
     e = cudaMemsetAsync(c->ws, 0, 2 * sizeof(DevCtl) + round_up(c->N, kAlign), c->stream);
+    if (e == cudaSuccess) e = empty_list(c);
     if (e == cudaSuccess) e = launch_reset_ctl(c->ctl, 0, c->stream);
     if (e == cudaSuccess) e = launch_init(c->spins, p.g, p.key0, p.key1, c->stream);
     if (e == cudaSuccess) e = launch_measure_full(dim, c->spins, p.g, c->ctl, 1, c->stream);
@@ -224,14 +232,21 @@ wolff_status ising_init(wolff_ctx **out, int dim, int L, double J, double T, uin
 
 wolff_status wolff_set_schedule(wolff_ctx *c, int schedule, int grid_blocks, int block_threads) {
     if (!c) return WOLFF_EINVAL;
-    if (schedule < WOLFF_SCHED_AUTO || schedule > WOLFF_SCHED_GRAPH)
+    if (schedule < WOLFF_SCHED_AUTO || schedule > WOLFF_SCHED_CLUSTER)
         return fail(c, WOLFF_EINVAL, "unknown schedule");
+    if (schedule == WOLFF_SCHED_CLUSTER && grid_blocks != 0 && grid_blocks != 1 &&
+        grid_blocks != 2 && grid_blocks != 4 && grid_blocks != 8 && grid_blocks != 16)
+        return fail(c, WOLFF_EINVAL, "cluster size must be 1, 2, 4, 8 or 16");
     if (block_threads != 0 && (block_threads < 32 || block_threads > 1024 || block_threads % 32))
         return fail(c, WOLFF_EINVAL, "block_threads must be a multiple of 32 in [32, 1024]");
     if (grid_blocks < 0) return fail(c, WOLFF_EINVAL, "grid_blocks must be >= 0");
     c->schedule = schedule == WOLFF_SCHED_AUTO ? WOLFF_SCHED_PERSISTENT : schedule;
     if (block_threads) c->threads = block_threads;
-    c->blocks = grid_blocks ? grid_blocks : default_blocks(c);
+    if (c->schedule == WOLFF_SCHED_CLUSTER) {
+        c->cluster = grid_blocks ? grid_blocks : 8;
+    } else {
+        c->blocks = grid_blocks ? grid_blocks : default_blocks(c);
+    }
     if (c->gexec && (c->graph_blocks != c->blocks || c->graph_threads != c->threads)) {
         cudaGraphExecDestroy(c->gexec);
         cudaGraphDestroy(c->graph);
@@ -257,7 +272,10 @@ wolff_status wolff_step(wolff_ctx *c, uint64_t n_updates, void *d_records) {
     p.records = reinterpret_cast<wolff_record *>(d_records);
     p.n = n_updates;
     cudaError_t e;
-    if (c->schedule == WOLFF_SCHED_GRAPH) {
+    if (c->schedule == WOLFF_SCHED_CLUSTER) {
+        e = launch_team(c->dim, p, nullptr, 1, c->cluster, c->threads, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cluster launch");
+    } else if (c->schedule == WOLFF_SCHED_GRAPH) {
         if (!c->gexec) {
             e = build_update_graph(c->dim, p, c->blocks, c->threads, &c->gexec, &c->graph);
             if (e != cudaSuccess) return cuda_fail(c, e, "build_update_graph");
@@ -275,8 +293,10 @@ wolff_status wolff_step(wolff_ctx *c, uint64_t n_updates, void *d_records) {
         if (blocks > per_sm * c->sm_count) blocks = per_sm * c->sm_count;
         if (blocks < 1) return fail(c, WOLFF_EUNSUPPORTED, "persistent kernel cannot be resident");
         void *args[] = {&p};
-        e = cudaLaunchCooperativeKernel(persistent_kernel(c->dim), dim3(blocks), dim3(c->threads),
-                                        args, 0, c->stream);
+        e = launch_prelaunch(c->ctl, c->stream);
+        if (e == cudaSuccess)
+            e = cudaLaunchCooperativeKernel(persistent_kernel(c->dim), dim3(blocks),
+                                            dim3(c->threads), args, 0, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "cooperative launch");
     }
     c->t_host += n_updates;
@@ -314,6 +334,7 @@ wolff_status wolff_get_state(wolff_ctx *c, int8_t *h_spins, uint64_t *t) {
         cudaError_t e = launch_to_pm1(scratch, c->spins, c->N, c->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(h_spins, scratch, c->N, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = empty_list(c);
         if (e != cudaSuccess) return cuda_fail(c, e, "get_state");
     }
     DevCtl h;
@@ -331,6 +352,7 @@ wolff_status wolff_set_state(wolff_ctx *c, const int8_t *h_spins, uint64_t t) {
     if (e == cudaSuccess) e = launch_reset_ctl(c->ctl, t, c->stream);
     if (e == cudaSuccess) e = launch_from_pm1(c->spins, scratch, c->N, c->ctl, c->stream);
     if (e == cudaSuccess) e = launch_measure_full(c->dim, c->spins, p.g, c->ctl, 1, c->stream);
+    if (e == cudaSuccess) e = empty_list(c);
     if (e != cudaSuccess) return cuda_fail(c, e, "set_state");
     c->t_host = t;
     return sync_and_check(c, nullptr);
@@ -385,10 +407,26 @@ wolff_status wolff_get_info(wolff_ctx *c, wolff_info *info) {
     info->seed = c->seed;
     info->t = c->t_host;
     info->schedule = c->schedule;
-    info->grid_blocks = c->blocks;
+    info->grid_blocks = c->schedule == WOLFF_SCHED_CLUSTER ? c->cluster : c->blocks;
     info->block_threads = c->threads;
     info->sm_count = c->sm_count;
     info->workspace_bytes = c->ws_bytes;
+    return WOLFF_OK;
+}
+
+wolff_status wolff_get_stats(wolff_ctx *c, wolff_stats *st) {
+    if (!c || !st) return WOLFF_EINVAL;
+    DevCtl h;
+    wolff_status s = sync_and_check(c, &h);
+    if (s != WOLFF_OK) return s;
+    st->updates = h.st_updates;
+    st->levels_local = h.st_levels_local;
+    st->levels_grid = h.st_levels_grid;
+    st->ns_local = h.st_ns_local;
+    st->ns_grid = h.st_ns_grid;
+    st->ns_finish = h.st_ns_finish;
+    st->handoffs = h.st_handoffs;
+    st->grid_finishes = h.st_grid_finishes;
     return WOLFF_OK;
 }
 
@@ -413,6 +451,93 @@ wolff_status ising_free(wolff_ctx *c) {
 const char *wolff_last_error(wolff_ctx *c) {
     if (!c) return "";
     return c->err.c_str();
+}
+
+struct wolff_batch {
+    int capacity = 0;
+    cudaStream_t stream = nullptr;
+    StepParams *h_table = nullptr;   // pinned staging copy
+    StepParams *d_table = nullptr;
+    cudaEvent_t copied = nullptr;    // the staging copy may be overwritten after it
+    bool pending = false;
+};
+
+wolff_status wolff_batch_create(wolff_batch **out, int capacity, void *stream) {
+    if (!out || capacity <= 0 || capacity > (1 << 20)) return WOLFF_EINVAL;
+    *out = nullptr;
+    wolff_batch *b = new (std::nothrow) wolff_batch;
+    if (!b) return WOLFF_ENOMEM;
+    b->capacity = capacity;
+    b->stream = reinterpret_cast<cudaStream_t>(stream);
+    const size_t bytes = (size_t)capacity * sizeof(StepParams);
+    if (cudaMallocHost(&b->h_table, bytes) != cudaSuccess ||
+        cudaMalloc(&b->d_table, bytes) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->copied, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        wolff_batch_free(b);
+        return WOLFF_ENOMEM;
+    }
+    *out = b;
+    return WOLFF_OK;
+}
+
+wolff_status wolff_batch_run(wolff_batch *b, wolff_ctx *const *ctxs, int n,
+                             const uint64_t *n_updates, void *const *d_records, int cluster_size,
+                             int block_threads) {
+    if (!b || n < 0 || n > b->capacity || (n && (!ctxs || !n_updates))) return WOLFF_EINVAL;
+    if (cluster_size != 1 && cluster_size != 2 && cluster_size != 4 && cluster_size != 8 &&
+        cluster_size != 16)
+        return WOLFF_EINVAL;
+    if (block_threads < 32 || block_threads > 1024 || block_threads % 32) return WOLFF_EINVAL;
+    if (b->pending) {   // the previous staging copy must have been consumed
+        if (cudaEventSynchronize(b->copied) != cudaSuccess) return WOLFF_ECUDA;
+        b->pending = false;
+    }
+    // jobs: 2D first then 3D, each group largest lattice first
+    int n2 = 0, n3 = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) return WOLFF_EINVAL;
+        if (n_updates[i] == 0) continue;
+        (ctxs[i]->dim == 2 ? n2 : n3) += 1;
+    }
+    int k2 = 0, k3 = n2;
+    for (int i = 0; i < n; ++i) {
+        wolff_ctx *c = ctxs[i];
+        if (n_updates[i] == 0) continue;
+        StepParams p = make_params(c);
+        p.records = d_records ? reinterpret_cast<wolff_record *>(d_records[i]) : nullptr;
+        p.n = n_updates[i];
+        b->h_table[c->dim == 2 ? k2++ : k3++] = p;
+    }
+    auto by_size = [](const StepParams &a, const StepParams &c) { return a.g.N > c.g.N; };
+    std::stable_sort(b->h_table, b->h_table + n2, by_size);
+    std::stable_sort(b->h_table + n2, b->h_table + n2 + n3, by_size);
+    const int total = n2 + n3;
+    if (total == 0) return WOLFF_OK;
+    cudaError_t e = cudaMemcpyAsync(b->d_table, b->h_table, (size_t)total * sizeof(StepParams),
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->copied, b->stream);
+    if (e != cudaSuccess) return WOLFF_ECUDA;
+    b->pending = true;
+    StepParams none = {};
+    if (n2) e = launch_team(2, none, b->d_table, n2, cluster_size, block_threads, b->stream);
+    if (e == cudaSuccess && n3)
+        e = launch_team(3, none, b->d_table + n2, n3, cluster_size, block_threads, b->stream);
+    if (e != cudaSuccess) return WOLFF_ECUDA;
+    for (int i = 0; i < n; ++i) ctxs[i]->t_host += n_updates[i];
+    return WOLFF_OK;
+}
+
+wolff_status wolff_batch_free(wolff_batch *b) {
+    if (!b) return WOLFF_OK;
+    if (b->copied) {
+        cudaStreamSynchronize(b->stream);
+        cudaEventDestroy(b->copied);
+    }
+    if (b->h_table) cudaFreeHost(b->h_table);
+    if (b->d_table) cudaFree(b->d_table);
+    delete b;
+    return WOLFF_OK;
 }
 
 // Test hook for the failure-detection path: runs the library's bounded

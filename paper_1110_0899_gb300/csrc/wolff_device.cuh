@@ -145,6 +145,34 @@ __device__ __forceinline__ void st_release_u32(unsigned int *p, unsigned int v) 
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long atom_add_acq_rel_u64(unsigned long long *p,
+                                                                   unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;"
+                 : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 __device__ __forceinline__ unsigned int ld_volatile_u32(const unsigned int *p) {
     return *reinterpret_cast<const volatile unsigned int *>(p);
 }
@@ -189,49 +217,116 @@ __device__ __forceinline__ unsigned int bounded_wait_change(DevCtl *ctl, const u
     }
 }
 
-// ---- bounded grid-wide barrier that carries the level's append count --------
-// Generation barrier: every CTA adds one arrival; the last arrival takes the
-// append counter (atomicExch to 0, so the next level starts from zero), puts
-// it in the broadcast slot of the new generation, resets the arrival count
-// and publishes generation g+1 with a release store.  The others poll the
-// generation with acquire loads (bounded, see bounded_wait_change).  Every
-// thread of every CTA returns the broadcast count in *value.  Returns false
-// when a wait ran out or another CTA raised an error: the caller must leave.
-// `gen` is the CTA's copy of the generation (meaningful in thread 0).
-__device__ __forceinline__ bool grid_sync(DevCtl *ctl, unsigned int nblocks, unsigned int &gen,
-                                          unsigned long long wait_ns, unsigned int where,
-                                          unsigned int *counter, unsigned int *value) {
+// ---- bounded team barrier that carries the append count ---------------------
+// bar_word = arrivals << 32 | entries appended since the team's phase began.
+// The warps reserve cluster-list slots by adding to the low half during a
+// level and every CTA arrives by adding 2^32, so the CTA whose add makes the
+// arrivals reach (phase+1)*nblocks is the last one and reads the appended
+// total from the same atomic.  It publishes (generation+1, total) in bar_pub;
+// the others poll bar_pub (bounded: wait_ns of globaltimer without change or
+// 2^28 polls raise WOLFF_ETIMEOUT; an error raised elsewhere also ends the
+// wait).  The word is reset only when a new phase is published, while every
+// other CTA is idle, so no reset can race with a reservation.
+//   full = false: relaxed arrival and publication.  Enough between growth
+//     levels: claims are atomics already performed when a CTA arrives, and
+//     list entries are recognised by the empty-slot sentinel.
+//   full = true: acq_rel arrival, release publication, acquire polling.
+//     Needed where plain stores or reductions must be visible after the
+//     barrier (the unmark pass).
+// Returns false if the wait failed; the caller must leave the kernel.
+// `gen` and `phase` are the CTA's copies (meaningful in thread 0).
+__device__ __forceinline__ bool team_barrier(DevCtl *ctl, unsigned int nblocks, unsigned int &gen,
+                                             unsigned int &phase, bool full,
+                                             unsigned long long wait_ns, unsigned int where,
+                                             unsigned int *count) {
     __shared__ unsigned int s_ok, s_val;
     __syncthreads();
     if (threadIdx.x == 0) {
         bool ok = true;
         const unsigned int my = gen;
-        __threadfence();
-        const unsigned int arrived = atomicAdd(&ctl->bar_count, 1u);
-        if (arrived == nblocks - 1) {
-            const unsigned int v = counter ? atomicExch(counter, 0u) : 0u;
-            ctl->bcast[(my + 1) & 3u] = v;
-            ctl->bar_count = 0;
-            st_release_u32(&ctl->bar_gen, my + 1);
+        unsigned int val = 0;
+        const unsigned int last = (phase + 1u) * nblocks - 1u;
+        const unsigned long long old = full ? atom_add_acq_rel_u64(&ctl->bar_word, 1ull << 32)
+                                            : atomicAdd(&ctl->bar_word, 1ull << 32);
+        if ((unsigned int)(old >> 32) == last) {
+            val = (unsigned int)old;
+            const unsigned long long pub = ((unsigned long long)(my + 1) << 32) | val;
+            if (full) st_release_u64(&ctl->bar_pub, pub);
+            else st_relaxed_u64(&ctl->bar_pub, pub);
         } else {
-            bounded_wait_change(ctl, &ctl->bar_gen, my, nullptr, wait_ns, where, &ok);
+            unsigned long long start = global_ns();
+            unsigned int polls = 0;
+            while (true) {
+                const unsigned long long v = full ? ld_acquire_u64(&ctl->bar_pub)
+                                                  : ld_relaxed_u64(&ctl->bar_pub);
+                if ((unsigned int)(v >> 32) != my) { val = (unsigned int)v; break; }
+                if ((++polls & 63u) == 0u) {
+                    if (ld_volatile_u32(&ctl->status) != 0u) { ok = false; break; }
+                    if (global_ns() - start > wait_ns || polls > (1u << 28)) {
+                        raise_status(ctl, WOLFF_ETIMEOUT, where);
+                        ok = false;
+                        break;
+                    }
+                }
+            }
         }
-        __threadfence();
         gen = my + 1;
+        phase += 1;
         if (ld_volatile_u32(&ctl->status) != 0u) ok = false;
-        s_val = ld_volatile_u32(&ctl->bcast[(my + 1) & 3u]);
+        s_val = val;
         s_ok = ok ? 1u : 0u;
     }
     __syncthreads();
-    if (value) *value = s_val;
+    if (count) *count = s_val;
     return s_ok != 0u;
+}
+
+// Waits until list slot k holds this update's entry (bounded like the
+// barrier).  Returns kEmptySlot if the wait failed; the status word then says
+// why and the caller's next barrier ends the kernel.
+__device__ __forceinline__ uint32_t wait_slot(const StepParams &p, uint32_t k) {
+    uint32_t v = __ldcg(p.list + k);
+    if (v != kEmptySlot) return v;
+    const unsigned long long start = global_ns();
+    unsigned int polls = 0;
+    while (true) {
+        v = ld_volatile_u32(p.list + k);
+        if (v != kEmptySlot) return v;
+        if ((++polls & 31u) == 0u) {
+            if (ld_volatile_u32(&p.ctl->status) != 0u) return kEmptySlot;
+            if (global_ns() - start > p.wait_ns || polls > (1u << 26)) {
+                raise_status(p.ctl, WOLFF_ETIMEOUT, 6);
+                return kEmptySlot;
+            }
+        }
+    }
+}
+
+// Unmark: bit 1 of a member takes the member's new spin (= its bit 0), with a
+// reduction on the containing word so that it never races a later claim of a
+// neighbouring byte.
+__device__ __forceinline__ void unmark_site(uint8_t *spins, uint32_t j, uint32_t sig0bit) {
+    unsigned int *w = reinterpret_cast<unsigned int *>(spins) + (j >> 2);
+    const unsigned int bit1 = 2u << ((j & 3u) * 8u);
+    if (sig0bit) atomicAnd(w, ~bit1);
+    else atomicOr(w, bit1);
 }
 
 // ---- warp-aggregated append -------------------------------------------------
 // Each lane contributes `mine` entries; one atomicAdd per warp reserves the
 // warp's range in the cluster list.  Returns the lane's first slot.  All 32
 // lanes must call it.
-__device__ __forceinline__ uint32_t warp_reserve(unsigned int *counter, uint32_t mine) {
+// The counter is a 32-bit word (shared or global) or the 64-bit barrier word,
+// whose low half counts entries.
+__device__ __forceinline__ uint32_t reserve_add(unsigned int *c, uint32_t n) {
+    return atomicAdd(c, n);
+}
+__device__ __forceinline__ uint32_t reserve_add(unsigned long long *c, uint32_t n) {
+    return (uint32_t)atomicAdd(c, (unsigned long long)n);
+}
+
+template <typename Counter>
+__device__ __forceinline__ uint32_t warp_reserve(Counter *counter, uint32_t mine) {
     const int lane = threadIdx.x & 31;
     uint32_t incl = mine;
 #pragma unroll
@@ -242,7 +337,7 @@ __device__ __forceinline__ uint32_t warp_reserve(unsigned int *counter, uint32_t
     const uint32_t total = __shfl_sync(kFullMask, incl, 31);
     uint32_t base = 0;
     if (total != 0u) {
-        if (lane == 31) base = atomicAdd(counter, total);
+        if (lane == 31) base = reserve_add(counter, total);
         base = __shfl_sync(kFullMask, base, 31);
     }
     return base + incl - mine;
@@ -268,35 +363,30 @@ __device__ __forceinline__ long long block_sum(long long v) {
 }
 
 // ---- the expansion of one wave-front site (step (iii') of section 4) -------
-// Loads the 2*DIM neighbour bytes (L2, bypassing L1 because other CTAs write
-// them), draws the site's own forward bonds with one Philox call and each
-// backward bond from its owner's call only when that neighbour is still
-// parallel to the seed spin, and claims every neighbour whose bond is active.
-// Returns the mask of neighbour slots won; nb receives their coordinates.
+// Draws the site's 2*DIM bond random words -- its own forward bonds from one
+// Philox call, each backward bond from its owner's call -- and claims every
+// neighbour behind an active bond directly.  No neighbour is read first: the
+// claim's old bit says whether the neighbour was still parallel to the seed
+// spin and unclaimed, so one L2 round trip per level is saved.  Returns the
+// mask of neighbour slots won; nb receives their coordinates.
 template <int DIM>
 __device__ __forceinline__ uint32_t expand_site(const StepParams &p, uint32_t packed,
                                                 uint32_t sig0bit, uint32_t tlo,
                                                 uint32_t thi, Neighbours<DIM> &nb) {
     uint32_t i;
     neighbours<DIM>(p.g, packed, &i, nb);
-    uint8_t v[2 * DIM];
-#pragma unroll
-    for (int s = 0; s < 2 * DIM; ++s) v[s] = __ldcg(p.spins + nb.idx[s]);
+    uint32_t r[2 * DIM];
     const Philox4 fwd = philox4x32_10(i, tlo, thi, kTagBond, p.key0, p.key1);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        r[2 * d] = fwd.v[d];
+        r[2 * d + 1] = philox4x32_10(nb.idx[2 * d + 1], tlo, thi, kTagBond, p.key0, p.key1).v[d];
+    }
     uint32_t won = 0;
 #pragma unroll
-    for (int s = 0; s < 2 * DIM; ++s) {
-        const int d = s >> 1;
-        if ((uint32_t)(v[s] & 1u) != sig0bit) continue;
-        uint32_t r;
-        if ((s & 1) == 0) {
-            r = fwd.v[d];
-        } else {
-            r = philox4x32_10(nb.idx[s], tlo, thi, kTagBond, p.key0, p.key1).v[d];
-        }
-        if ((unsigned long long)r < p.thr && claim_site(p.spins, nb.idx[s], sig0bit))
+    for (int s = 0; s < 2 * DIM; ++s)
+        if ((unsigned long long)r[s] < p.thr && claim_site(p.spins, nb.idx[s], sig0bit))
             won |= 1u << s;
-    }
     return won;
 }
 

@@ -23,11 +23,18 @@ constexpr uint32_t kTagBond = 0;
 constexpr uint32_t kTagSeed = 1;
 constexpr uint32_t kTagInit = 2;
 
+// Value of an empty cluster-list slot.  Every slot holds it between updates
+// (the unmark pass restores it), so a reader that finds anything else in a
+// slot of the running update is looking at that update's entry: list entries
+// need no release/acquire ordering, only the level counts do.  Packed
+// coordinates never take this value (2D coordinates are < 2^15, 3D < 2^10).
+constexpr uint32_t kEmptySlot = 0xFFFFFFFFu;
+
 // Control block living at the start of the workspace.  Fields are grouped
 // into 128-byte lines by who touches them: the chain state (one thread at a
 // time), the grid barrier, the leader's command word, the append counters and
 // the graph schedule's state.
-struct alignas(128) DevCtl {
+struct alignas(256) DevCtl {
     // line 0: chain state
     unsigned long long t;          // next update index
     long long E;                   // bond sum
@@ -40,9 +47,12 @@ struct alignas(128) DevCtl {
     long long full_E;              // full recount results
     long long full_M;
     // line 1: grid barrier
-    alignas(128) unsigned int bar_count;   // arrivals (atomic)
-    unsigned int bar_gen;                  // generation
-    unsigned int bcast[4];                 // per-generation broadcast slot
+    // bar_word = arrivals << 32 | entries appended this level (atomic): the
+    // warps reserve list slots and the CTAs arrive on the same word, so the
+    // last arrival knows the level's total without another round trip.
+    // bar_pub = generation << 32 | that total, published with a release store.
+    alignas(128) unsigned long long bar_word;
+    unsigned long long bar_pub;
     // line 2: leader -> worker commands
     alignas(128) unsigned int cmd_seq;
     unsigned int cmd_kind;
@@ -61,6 +71,11 @@ struct alignas(128) DevCtl {
     unsigned long long t_end;              // graph loop stops when t == t_end
     unsigned long long rec_t0;             // t of records[0] for this call
     wolff_record *records;                 // destination of this call's records
+    // line 5: persistent-schedule counters (leader thread, accumulated)
+    alignas(128) unsigned long long st_updates;
+    unsigned long long st_levels_local, st_levels_grid;
+    unsigned long long st_ns_local, st_ns_grid, st_ns_finish;
+    unsigned long long st_handoffs, st_grid_finishes;
 };
 static_assert(sizeof(DevCtl) % 256 == 0 && sizeof(DevCtl) <= 1024, "control block layout");
 
@@ -102,10 +117,18 @@ cudaError_t launch_to_pm1(int8_t *dst, const uint8_t *spins, uint32_t N,
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, const uint32_t *ctr,
                           uint32_t *out, unsigned long long n, cudaStream_t s);
 cudaError_t launch_reset_ctl(DevCtl *ctl, unsigned long long t, cudaStream_t s);
+cudaError_t launch_prelaunch(DevCtl *ctl, cudaStream_t s);
 
 // Persistent cooperative schedule.
 const void *persistent_kernel(int dim);
 int persistent_max_blocks_per_sm(int dim, int threads, int *err);
+
+// Team schedule (wolff_team.cu): one thread-block cluster per job; the jobs
+// come from d_table (device array of njobs StepParams) or, when d_table is
+// null, the single job `single` (njobs must be 1).
+const void *team_kernel(int dim);
+cudaError_t launch_team(int dim, const StepParams &single, const StepParams *d_table, int njobs,
+                        int cluster_size, int threads, cudaStream_t s);
 
 // Graph schedule: builds the nested-WHILE graph; returns its executable.
 cudaError_t build_update_graph(int dim, const StepParams &p, int blocks,

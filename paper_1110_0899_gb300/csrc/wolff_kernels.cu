@@ -165,13 +165,31 @@ __global__ void k_reset_ctl(DevCtl *ctl, unsigned long long t) {
     ctl->err_detail = 0;
     for (int k = 0; k < 4; ++k) ctl->cnt[k] = 0;
     ctl->dE = 0;
-    ctl->bar_count = 0;
-    ctl->bar_gen = 0;
+    ctl->bar_word = 0;
+    ctl->bar_pub = 0;
     ctl->lo = ctl->hi = ctl->levels = ctl->done = 0;
     ctl->sig0bit = 0;
     ctl->t_end = t;
     ctl->rec_t0 = t;
     ctl->records = nullptr;
+    ctl->cmd_seq = 0;
+    ctl->st_updates = ctl->st_levels_local = ctl->st_levels_grid = 0;
+    ctl->st_ns_local = ctl->st_ns_grid = ctl->st_ns_finish = 0;
+    ctl->st_handoffs = ctl->st_grid_finishes = 0;
+}
+
+// Before every persistent launch: command sequence, barrier word and
+// generation start from zero, so no CTA has to read them at start-up.
+__global__ void k_prelaunch(DevCtl *ctl) {
+    ctl->cmd_seq = 0;
+    ctl->bar_word = 0;
+    ctl->bar_pub = 0;
+    ctl->dE = 0;
+}
+
+cudaError_t launch_prelaunch(DevCtl *ctl, cudaStream_t s) {
+    k_prelaunch<<<1, 1, 0, s>>>(ctl);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_reset_ctl(DevCtl *ctl, unsigned long long t, cudaStream_t s) {
@@ -182,8 +200,8 @@ cudaError_t launch_reset_ctl(DevCtl *ctl, unsigned long long t, cudaStream_t s) 
 // Failure-detection self test: one CTA waits at a grid barrier that expects
 // two, so only the time limit can end the wait.
 __global__ void k_selftest_wait(DevCtl *scratch, unsigned long long wait_ns) {
-    unsigned int gen = 0;
-    grid_sync(scratch, 2u, gen, wait_ns, 0x7E57u, nullptr, nullptr);
+    unsigned int gen = 0, phase = 0;
+    team_barrier(scratch, 2u, gen, phase, true, wait_ns, 0x7E57u, nullptr);
 }
 
 cudaError_t launch_selftest_wait(DevCtl *scratch, unsigned long long wait_ns, cudaStream_t s) {
@@ -196,10 +214,10 @@ cudaError_t launch_selftest_wait(DevCtl *scratch, unsigned long long wait_ns, cu
 
 // Expands list[lo, hi) with all warps of the grid; new members go to
 // list[hi + ...] through `counter`.
-template <int DIM>
+template <int DIM, typename Counter>
 __device__ __forceinline__ void expand_range(const StepParams &p, uint32_t lo, uint32_t hi,
                                              uint32_t sig0bit, uint32_t tlo, uint32_t thi,
-                                             unsigned int *counter) {
+                                             Counter *counter) {
     const uint32_t warps_per_block = blockDim.x >> 5;
     const uint32_t gwarp = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
     const uint32_t nwarps = gridDim.x * warps_per_block;
@@ -234,15 +252,15 @@ __device__ __forceinline__ long long boundary_range(const StepParams &p, uint32_
     return acc;
 }
 
-// Unmark: both bits of every member take the new spin (opposite of sigma0).
+// Unmark list[0, C) (grid-stride) and give the slots back their empty value.
 template <int DIM>
 __device__ __forceinline__ void unmark_range(const StepParams &p, uint32_t C, uint32_t sig0bit) {
-    const uint8_t v = sig0bit ? 0x00 : 0x03;
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < C;
          k += gridDim.x * blockDim.x) {
         uint32_t c[DIM];
         unpack<DIM>(__ldcg(p.list + k), c);
-        p.spins[site_index<DIM>(p.g, c)] = v;
+        unmark_site(p.spins, site_index<DIM>(p.g, c), sig0bit);
+        p.list[k] = kEmptySlot;
     }
 }
 
@@ -281,12 +299,13 @@ __device__ __forceinline__ void finish_update(const StepParams &p, DevCtl *ctl,
 // the paper's hybrid (section 6: small wave fronts are cheaper on one
 // processor).  When a level produces more than t_up new sites it publishes a
 // GROW command and all CTAs expand the following levels together, separated
-// by the bounded grid barrier, until a level produces t_down sites or fewer;
+// by the relaxed team barrier, until a level produces t_down sites or fewer;
 // then the workers go back to waiting and the leader continues alone.  A
 // cluster that fits the shared-memory list and never went to the grid is
 // closed by the leader alone; otherwise a FINISH command runs the energy and
-// unmark passes on all CTAs.  t_up = 0 gives the plain grid-synchronous
-// schedule (every level on all CTAs).
+// unmark passes on all CTAs, closed by full barriers.  t_up = 0 gives the
+// plain grid-synchronous schedule (every level on all CTAs).  The leader
+// keeps the chain state (t, E, M) in registers and writes it back at exit.
 
 enum : unsigned int { kCmdGrow = 1, kCmdFinish = 2, kCmdExit = 3 };
 
@@ -294,70 +313,109 @@ struct SharedLocal {
     uint32_t front[2][kLocalFrontierCap];
     uint32_t list[kLocalListCap];
     unsigned int cnt[3];
+    unsigned int sig0bit;
     unsigned int flag;
     unsigned int cmd[8];
 };
 
-// All CTAs: expand list[lo, hi) level after level until the next frontier is
-// empty (*finished = true) or holds t_down sites or fewer.
+// All CTAs: from the wave front list[lo, hi) (phase just published, entries
+// appended at base + the barrier word's count), expand level after level until
+// the next front is empty (*finished = true) or has t_down sites or fewer.
 template <int DIM>
-__device__ __forceinline__ bool grid_levels(const StepParams &p, unsigned int &gen, uint32_t &lo,
-                                            uint32_t &hi, uint32_t &level, uint32_t sig0bit,
-                                            uint32_t tlo, uint32_t thi, bool *finished) {
+__device__ __forceinline__ bool grid_levels(const StepParams &p, unsigned int &gen,
+                                            unsigned int &phase, uint32_t &lo, uint32_t &hi,
+                                            uint32_t &level, uint32_t sig0bit, uint32_t tlo,
+                                            uint32_t thi, bool *finished) {
     DevCtl *ctl = p.ctl;
+    const uint32_t base = hi;
+    const uint32_t warps_per_block = blockDim.x >> 5;
+    const uint32_t gwarp = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
+    const uint32_t nwarps = gridDim.x * warps_per_block;
+    const uint32_t lane = threadIdx.x & 31;
     while (true) {
-        expand_range<DIM>(p, lo, hi, sig0bit, tlo, thi, &ctl->cnt[0]);
-        unsigned int added = 0;
-        if (!grid_sync(ctl, gridDim.x, gen, p.wait_ns, 1, &ctl->cnt[0], &added)) return false;
+        for (uint32_t b = lo + gwarp * 32u; b < hi; b += nwarps * 32u) {
+            const uint32_t k = b + lane;
+            Neighbours<DIM> nb;
+            uint32_t won = 0;
+            if (k < hi) {
+                const uint32_t packed = wait_slot(p, k);
+                if (packed != kEmptySlot) won = expand_site<DIM>(p, packed, sig0bit, tlo, thi, nb);
+            }
+            uint32_t pos = base + warp_reserve(&ctl->bar_word, __popc(won));
+#pragma unroll
+            for (int s = 0; s < 2 * DIM; ++s) {
+                if (won & (1u << s)) {
+                    if (pos < p.g.N) p.list[pos] = nb.packed[s];
+                    else raise_status(ctl, WOLFF_EINVAL, 0xC0FFu);
+                    ++pos;
+                }
+            }
+        }
+        unsigned int total = 0;
+        if (!team_barrier(ctl, gridDim.x, gen, phase, false, p.wait_ns, 1, &total)) return false;
         ++level;
-        if (added > p.g.N - hi) {   // cannot happen: every site joins at most once
+        const uint32_t next_hi = base + total;
+        if (next_hi < hi || next_hi > p.g.N) {   // cannot happen: each site joins once
             if (blockIdx.x == 0 && threadIdx.x == 0) raise_status(ctl, WOLFF_EINVAL, 0xC1u);
             return false;
         }
+        const uint32_t added = next_hi - hi;
         lo = hi;
-        hi += added;
+        hi = next_hi;
         if (added == 0) { *finished = true; return true; }
         if (added <= p.t_down) { *finished = false; return true; }
     }
 }
 
-// All CTAs: energy change over list[0, C), then unmark, then close the update.
+// All CTAs: energy change over list[0, C), then unmark; closed by full
+// barriers so that the unmark and the emptied slots are visible before the
+// next update.  Returns the update's boundary sum in thread 0 of CTA 0.
 template <int DIM>
-__device__ __forceinline__ bool grid_finish(const StepParams &p, unsigned int &gen, uint32_t C,
-                                            uint32_t levels, uint32_t sig0bit,
-                                            unsigned long long t, unsigned long long rec) {
+__device__ __forceinline__ bool grid_finish(const StepParams &p, unsigned int &gen,
+                                            unsigned int &phase, uint32_t C, uint32_t sig0bit,
+                                            long long *dE_out) {
     DevCtl *ctl = p.ctl;
-    const long long acc = block_sum(boundary_range<DIM>(p, C, sig0bit));
+    long long acc = 0;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < C;
+         k += gridDim.x * blockDim.x) {
+        const uint32_t packed = wait_slot(p, k);
+        uint32_t i;
+        if (packed != kEmptySlot) acc += boundary_term<DIM>(p, packed, sig0bit, &i);
+    }
+    acc = block_sum(acc);
     if (threadIdx.x == 0 && acc != 0)
         atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->dE), (unsigned long long)acc);
-    if (!grid_sync(ctl, gridDim.x, gen, p.wait_ns, 2, nullptr, nullptr)) return false;
+    if (!team_barrier(ctl, gridDim.x, gen, phase, true, p.wait_ns, 2, nullptr)) return false;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *dE_out = *reinterpret_cast<volatile long long *>(&ctl->dE);
+    }
     unmark_range<DIM>(p, C, sig0bit);
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        finish_update(p, ctl, p.records, rec, C, levels, sig0bit, t, 0);
-    return grid_sync(ctl, gridDim.x, gen, p.wait_ns, 3, nullptr, nullptr);
+    if (!team_barrier(ctl, gridDim.x, gen, phase, true, p.wait_ns, 3, nullptr)) return false;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->dE = 0;   // read above, before the barrier
+    return true;
 }
 
-// Leader thread 0: publish a command to the workers (release on cmd_seq).
+// Leader thread 0: start a new team phase (barrier word cleared while every
+// worker is idle) and publish a command (release on cmd_seq).
 __device__ __forceinline__ void publish(DevCtl *ctl, unsigned int &seq, unsigned int kind,
                                         uint32_t lo, uint32_t hi, uint32_t level,
-                                        uint32_t sig0bit, unsigned long long t,
-                                        unsigned long long rec) {
+                                        uint32_t sig0bit, unsigned long long t) {
+    ctl->bar_word = 0;
     ctl->cmd_kind = kind;
     ctl->cmd_lo = lo;
     ctl->cmd_hi = hi;
     ctl->cmd_level = level;
     ctl->cmd_sig0bit = sig0bit;
     ctl->cmd_t = t;
-    ctl->cmd_rec = rec;
     __threadfence();
     seq += 1;
     st_release_u32(&ctl->cmd_seq, seq);
 }
 
 template <int DIM>
-__device__ void worker_loop(const StepParams &p, SharedLocal &sh, unsigned int &gen,
-                            unsigned int seq) {
+__device__ void worker_loop(const StepParams &p, SharedLocal &sh, unsigned int &gen) {
     DevCtl *ctl = p.ctl;
+    unsigned int seq = 0;
     while (true) {
         if (threadIdx.x == 0) {
             bool ok = true;
@@ -372,10 +430,9 @@ __device__ void worker_loop(const StepParams &p, SharedLocal &sh, unsigned int &
                 sh.cmd[2] = ctl->cmd_hi;
                 sh.cmd[3] = ctl->cmd_level;
                 sh.cmd[4] = ctl->cmd_sig0bit;
-                const unsigned long long t = ctl->cmd_t, rec = ctl->cmd_rec;
+                const unsigned long long t = ctl->cmd_t;
                 sh.cmd[5] = (uint32_t)t;
                 sh.cmd[6] = (uint32_t)(t >> 32);
-                sh.cmd[7] = (uint32_t)rec;
             }
         }
         __syncthreads();
@@ -383,12 +440,14 @@ __device__ void worker_loop(const StepParams &p, SharedLocal &sh, unsigned int &
         uint32_t lo = sh.cmd[1], hi = sh.cmd[2], level = sh.cmd[3];
         const uint32_t sig0bit = sh.cmd[4], tlo = sh.cmd[5], thi = sh.cmd[6];
         __syncthreads();
+        unsigned int phase = 0;
         if (kind == kCmdGrow) {
             bool finished = false;
-            if (!grid_levels<DIM>(p, gen, lo, hi, level, sig0bit, tlo, thi, &finished)) return;
+            if (!grid_levels<DIM>(p, gen, phase, lo, hi, level, sig0bit, tlo, thi, &finished))
+                return;
         } else if (kind == kCmdFinish) {
-            const unsigned long long t = ((unsigned long long)thi << 32) | tlo;
-            if (!grid_finish<DIM>(p, gen, hi, level, sig0bit, t, 0)) return;
+            long long dE = 0;
+            if (!grid_finish<DIM>(p, gen, phase, hi, sig0bit, &dE)) return;
         } else {
             return;
         }
@@ -399,70 +458,92 @@ template <int DIM>
 __global__ void __launch_bounds__(1024) k_persistent(StepParams p) {
     DevCtl *ctl = p.ctl;
     __shared__ SharedLocal sh;
-    __shared__ unsigned int s_gen, s_seq;
-    if (threadIdx.x == 0) {
-        s_gen = ld_volatile_u32(&ctl->bar_gen);
-        s_seq = ld_volatile_u32(&ctl->cmd_seq);
-    }
-    __syncthreads();
-    unsigned int gen = s_gen;   // meaningful in thread 0
-    unsigned int seq = s_seq;
-    // every CTA has read the command sequence before the leader can publish
-    if (!grid_sync(ctl, gridDim.x, gen, p.wait_ns, 5, nullptr, nullptr)) return;
+    unsigned int gen = 0;   // the pre-launch kernel zeroed the generation
     if (blockIdx.x != 0) {
-        worker_loop<DIM>(p, sh, gen, seq);
+        worker_loop<DIM>(p, sh, gen);
         return;
     }
     const bool t0 = threadIdx.x == 0;
     const uint32_t nwarps = blockDim.x >> 5;
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t t_up = min(p.t_up, kLocalFrontierCap);
-
+    unsigned int seq = 0;
+    // chain state, kept by thread 0 in registers
+    long long E = 0, M = 0;
+    unsigned long long total_C = 0;
+    uint32_t last_C = 0, last_levels = 0;
+    unsigned long long st_local = 0, st_grid = 0, ns_local = 0, ns_grid = 0, ns_finish = 0;
+    unsigned long long handoffs = 0, grid_fin = 0;
+    if (t0) {
+        E = ctl->E;
+        M = ctl->M;
+        total_C = ctl->total_C;
+        last_C = ctl->last_C;
+        last_levels = ctl->last_levels;
+    }
+    unsigned long long done = 0;
     for (unsigned long long u = 0; u < p.n; ++u) {
         const unsigned long long t = p.t0 + u;
         const uint32_t tlo = (uint32_t)t, thi = (uint32_t)(t >> 32);
-        const uint32_t i0 = seed_site(p, t);
-        const uint32_t sig0bit = (p.spins[i0] >> 1) & 1u;
+        unsigned long long clk = 0;
         if (t0) {
-            claim_site(p.spins, i0, sig0bit);
+            // seed: one uncontended XOR flips its bit 0 and returns its spin
+            const uint32_t i0 = seed_site(p, t);
+            unsigned int *w = reinterpret_cast<unsigned int *>(p.spins) + (i0 >> 2);
+            const unsigned int sh0 = (i0 & 3u) * 8u;
+            const uint32_t s0 = (atomicXor(w, 1u << sh0) >> sh0) & 1u;
             const uint32_t p0 = pack_index<DIM>(p.g, i0);
             p.list[0] = p0;
             sh.list[0] = p0;
             sh.front[0][0] = p0;
             sh.cnt[0] = sh.cnt[1] = sh.cnt[2] = 0;
-            sh.flag = ld_volatile_u32(&ctl->status);
+            sh.sig0bit = s0;
+            sh.flag = ((u & 31u) == 31u) ? ld_volatile_u32(&ctl->status) : 0u;
+            clk = global_ns();
         }
         __syncthreads();
         if (sh.flag != 0u) break;
+        const uint32_t sig0bit = sh.sig0bit;
         uint32_t C = 1, f = 1, level = 0, cur = 0;
-        bool went_grid = false, ok = true;
+        bool went_grid = false;
         while (f > 0) {
             if (f > t_up) {
                 // hand the wave front list[C-f, C) to all CTAs
                 went_grid = true;
-                if (t0) publish(ctl, seq, kCmdGrow, C - f, C, level, sig0bit, t, u);
-                uint32_t lo = C - f, hi = C;
-                bool finished = false;
-                if (!grid_levels<DIM>(p, gen, lo, hi, level, sig0bit, tlo, thi, &finished)) {
-                    ok = false;
-                    break;
+                unsigned long long g0 = 0;
+                if (t0) {
+                    g0 = global_ns();
+                    ns_local += g0 - clk;
+                    ++handoffs;
+                    publish(ctl, seq, kCmdGrow, C - f, C, level, sig0bit, t);
                 }
+                __syncthreads();
+                uint32_t lo = C - f, hi = C, phase = 0, lv0 = level;
+                bool finished = false;
+                if (!grid_levels<DIM>(p, gen, phase, lo, hi, level, sig0bit, tlo, thi,
+                                      &finished))
+                    return;
                 C = hi;
                 f = finished ? 0u : hi - lo;
                 if (f) {   // back to the leader: load the small front
                     for (uint32_t k = threadIdx.x; k < f; k += blockDim.x)
-                        sh.front[cur][k] = __ldcg(p.list + lo + k);
+                        sh.front[cur][k] = wait_slot(p, lo + k);
                     if (t0) sh.cnt[0] = sh.cnt[1] = sh.cnt[2] = 0;
-                    __syncthreads();
                 }
+                if (t0) {
+                    st_grid += level - lv0;
+                    clk = global_ns();
+                    ns_grid += clk - g0;
+                }
+                __syncthreads();
                 continue;
             }
             // one level on the leader alone
             const uint32_t nxt = cur ^ 1u;
             unsigned int *cnt = &sh.cnt[level % 3];
             if (t0) sh.cnt[(level + 1) % 3] = 0;
-            for (uint32_t base = warp * 32u; base < f; base += nwarps * 32u) {
-                const uint32_t k = base + lane;
+            for (uint32_t b = warp * 32u; b < f; b += nwarps * 32u) {
+                const uint32_t k = b + lane;
                 Neighbours<DIM> nb;
                 uint32_t won = 0;
                 if (k < f) won = expand_site<DIM>(p, sh.front[cur][k], sig0bit, tlo, thi, nb);
@@ -482,14 +563,25 @@ __global__ void __launch_bounds__(1024) k_persistent(StepParams p) {
             __syncthreads();
             const uint32_t added = *cnt;
             ++level;
+            if (t0) ++st_local;
             C += added;
             f = added;
             cur = nxt;
         }
-        if (!ok) return;
+        long long dE = 0;
+        unsigned long long f0 = 0;
+        if (t0) {
+            f0 = global_ns();
+            ns_local += f0 - clk;
+        }
         if (went_grid || C > kLocalListCap) {
-            if (t0) publish(ctl, seq, kCmdFinish, 0, C, level, sig0bit, t, u);
-            if (!grid_finish<DIM>(p, gen, C, level, sig0bit, t, u)) return;
+            if (t0) {
+                ++grid_fin;
+                publish(ctl, seq, kCmdFinish, 0, C, level, sig0bit, t);
+            }
+            __syncthreads();
+            uint32_t phase = 0;
+            if (!grid_finish<DIM>(p, gen, phase, C, sig0bit, &dE)) return;
         } else {
             // the leader closes a small cluster alone from its shared list
             long long acc = 0;
@@ -497,19 +589,52 @@ __global__ void __launch_bounds__(1024) k_persistent(StepParams p) {
                 uint32_t i;
                 acc += boundary_term<DIM>(p, sh.list[k], sig0bit, &i);
             }
-            acc = block_sum(acc);
+            dE = block_sum(acc);
             __syncthreads();
-            const uint8_t v = sig0bit ? 0x00 : 0x03;
             for (uint32_t k = threadIdx.x; k < C; k += blockDim.x) {
                 uint32_t c[DIM];
                 unpack<DIM>(sh.list[k], c);
-                p.spins[site_index<DIM>(p.g, c)] = v;
+                unmark_site(p.spins, site_index<DIM>(p.g, c), sig0bit);
+                p.list[k] = kEmptySlot;
             }
-            if (t0) finish_update(p, ctl, p.records, u, C, level, sig0bit, t, acc);
-            __syncthreads();
         }
+        if (t0) {
+            E += 2 * dE;
+            M += (sig0bit ? -2LL : 2LL) * (long long)C;
+            total_C += C;
+            last_C = C;
+            last_levels = level;
+            if (p.records) {
+                wolff_record r;
+                r.C = C;
+                r.levels = level;
+                r.E_bond = E;
+                r.M = M;
+                p.records[u] = r;
+            }
+            *reinterpret_cast<volatile unsigned long long *>(&ctl->t) = t + 1;   // progress
+            ns_finish += global_ns() - f0;
+        }
+        ++done;
+        __syncthreads();
     }
-    if (t0) publish(ctl, seq, kCmdExit, 0, 0, 0, 0, 0, 0);
+    if (t0) {
+        ctl->E = E;
+        ctl->M = M;
+        ctl->total_C = total_C;
+        ctl->last_C = last_C;
+        ctl->last_levels = last_levels;
+        ctl->t = p.t0 + done;
+        ctl->st_updates += done;
+        ctl->st_levels_local += st_local;
+        ctl->st_levels_grid += st_grid;
+        ctl->st_ns_local += ns_local;
+        ctl->st_ns_grid += ns_grid;
+        ctl->st_ns_finish += ns_finish;
+        ctl->st_handoffs += handoffs;
+        ctl->st_grid_finishes += grid_fin;
+        publish(ctl, seq, kCmdExit, 0, 0, 0, 0, 0);
+    }
 }
 
 const void *persistent_kernel(int dim) {

@@ -99,6 +99,8 @@ extern "C" wolff_status wolff_step_static(int dim, int L, double J, double T, ui
     if (e == cudaSuccess)
         e = launch_from_pm1(p.spins, static_cast<const int8_t *>(d_spins), p.g.N, p.ctl, s);
     if (e == cudaSuccess) e = launch_measure_full(dim, p.spins, p.g, p.ctl, 1, s);
+    // the update expects every cluster-list slot to hold the empty marker
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.list, 0xFF, (size_t)p.g.N * sizeof(uint32_t), s);
     if (e == cudaSuccess && n_updates) {
         const int threads = 256;
         int per_sm = 0;

@@ -202,3 +202,81 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     ref, _ = oracle_trajectory(2, 16, TC2, 1, 100)
     assert_records_equal(lat.step(100), ref, "after self test")
     lat.close()
+
+
+# ---- cluster ("team") schedule and the batched form --------------------------
+
+@pytest.mark.parametrize("cluster", [1, 2, 4, 8, 16])
+def test_cluster_schedule_matches_oracle(cluster):
+    torch, w = require_cuda()
+    for dim, L, T, n, start in ((2, 16, TC2, 2000, "random"), (3, 9, 4.5115, 400, "random"),
+                                (2, 128, TC2, 40, "ordered"), (3, 24, 4.5115, 30, "ordered"),
+                                (2, 37, 2.0, 60, "ordered")):
+        s0 = oracle.init_lattice(dim, L, 77) if start == "random" else np.ones(L ** dim, np.int8)
+        ref, s_ref = oracle_trajectory(dim, L, T, 77, n, s=s0)
+        lat = w.WolffLattice(dim, L, T, seed=77)
+        try:
+            lat.set_schedule(w.SCHED_CLUSTER, cluster, 256)
+        except w.WolffError:
+            pytest.skip("cluster size %d not accepted" % cluster)
+        lat.set_state(s0, 0)
+        lat.set_local_thresholds(64, 16)
+        try:
+            rec = lat.step(n)
+        except w.WolffError as e:
+            if cluster == 16:
+                pytest.skip("16-CTA clusters not launchable here: %s" % e)
+            raise
+        spins, t = lat.get_state()
+        assert lat.measure()[:2] == lat.measure_full()
+        lat.close()
+        assert_records_equal(rec, ref, "cluster %d %dD L=%d" % (cluster, dim, L))
+        assert np.array_equal(spins, s_ref) and t == n
+
+
+@pytest.mark.parametrize("t_up,t_down", [(0, 0), (8, 2), (2048, 1024)])
+def test_cluster_thresholds(t_up, t_down):
+    torch, w = require_cuda()
+    dim, L, T, n = 2, 200, TC2, 30
+    up = np.ones(L * L, np.int8)
+    ref, s_ref = oracle_trajectory(dim, L, T, 5, n, s=up)
+    lat = w.WolffLattice(dim, L, T, seed=5, schedule=w.SCHED_CLUSTER, grid_blocks=8,
+                         block_threads=512)
+    lat.set_local_thresholds(t_up, t_down)
+    lat.set_state(up, 0)
+    rec = lat.step(n)
+    spins, _ = lat.get_state()
+    lat.close()
+    assert_records_equal(rec, ref, "cluster thresholds %d/%d" % (t_up, t_down))
+    assert np.array_equal(spins, s_ref)
+
+
+def test_batched_replicas_match_each_alone():
+    """Uneven lattices and temperatures in one launch, several calls in a row:
+    every replica's records and lattice equal the oracle's chain alone."""
+    torch, w = require_cuda()
+    rng = np.random.default_rng(4)
+    specs = []
+    for i in range(24):
+        dim = 2 if i % 4 else 3
+        L = int(rng.choice([8, 13, 32, 64])) if dim == 2 else int(rng.choice([5, 8, 11]))
+        T = float(rng.uniform(0.9, 1.1)) * (TC2 if dim == 2 else 4.5115)
+        specs.append((dim, L, T, 1000 + i))
+    lats = [w.WolffLattice(d, L, T, seed=s) for d, L, T, s in specs]
+    batch = w.WolffBatch(len(lats))
+    calls = [(60, 1, 128), (40, 2, 256), (75, 4, 256)]
+    got = [[] for _ in lats]
+    for n, cs, thr in calls:
+        bufs = [lat.record_buffer(n) for lat in lats]
+        batch.run(lats, [n] * len(lats), bufs, cluster_size=cs, block_threads=thr)
+        torch.cuda.synchronize()
+        for k, (lat, b) in enumerate(zip(lats, bufs)):
+            got[k].append(w.records_to_numpy(b, n))
+    total = sum(c[0] for c in calls)
+    for k, ((dim, L, T, seed), lat) in enumerate(zip(specs, lats)):
+        ref, s_ref = oracle_trajectory(dim, L, T, seed, total)
+        assert_records_equal(np.concatenate(got[k]), ref, "replica %d" % k)
+        spins, t = lat.get_state()
+        assert t == total and np.array_equal(spins, s_ref)
+        lat.close()
+    batch.close()

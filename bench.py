@@ -56,10 +56,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS) + ["batched", "served"])
     ap.add_argument("--updates-per-step", type=int, default=100)
     ap.add_argument("--equil", type=int, default=None)
-    ap.add_argument("--schedule", default="persistent", choices=["persistent", "graph", "cluster"])
+    ap.add_argument("--schedule", default="auto",
+                    choices=["auto", "persistent", "graph", "cluster"])
     ap.add_argument("--blocks", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--t-up", type=int, default=None,
@@ -69,6 +70,12 @@ def parse():
                     help="bound of the oracle sample timed beside the GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=120.0)
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched-vs-plain comparison in the default line")
+    ap.add_argument("--no-served", action="store_true",
+                    help="skip the serving run in the default line")
+    ap.add_argument("--embed-serve-seconds", type=float, default=30.0)
     return ap.parse_args()
 
 
@@ -178,6 +185,99 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args, n_replicas=512, updates=None, embed=False):
+    """512 independent 2D replicas (L in {64..1024}, T in [2.0, 2.6], seeds
+    1000+i) through the autotuned batched plan, against the same replicas run
+    one lattice per launch.  Both arms run the same updates from the same
+    random starts, so their records must agree bit for bit."""
+    import numpy as np
+    import torch
+
+    import paper_1110_0899_gb300 as w
+    from paper_1110_0899_gb300 import batched, workloads
+    torch.cuda.set_device(0)
+    U = updates or args.updates_per_step
+    specs = workloads.batched_replicas(n_replicas)
+    plan, table = batched.autotune(specs, probe_updates=max(10, U // 4))
+    lat_b = [w.WolffLattice(s["dim"], s["L"], s["T"], seed=s["seed"]) for s in specs]
+    runner = batched.BatchedRunner(lat_b, plan)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    recs_b, lat_ms = [], []
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record()
+        bufs = runner.run(U)
+        ev[k][1].record()
+        torch.cuda.synchronize()
+        recs_b.append([r for r in runner.records_numpy(bufs, U)])
+        st = [x.stats() for x in lat_b]
+        t_start = min(x["start_ns"] for x in st)
+        lat_ms.extend((x["end_ns"] - t_start) / 1e6 for x in st)
+    t_b = sum(a.elapsed_time(b) for a, b in ev) / 1000.0
+    flips_b = sum(int(r["C"].astype(np.int64).sum()) for step in recs_b for r in step)
+    runner.close()
+    # plain: one lattice per launch, the same updates
+    lat_p = [w.WolffLattice(s["dim"], s["L"], s["T"], seed=s["seed"],
+                            schedule=w.SCHED_CLUSTER, grid_blocks=1, block_threads=256)
+             for s in specs]
+    bufs_p = [x.record_buffer(U) for x in lat_p]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    same = True
+    flips_p = 0
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record()
+        for x, b in zip(lat_p, bufs_p):
+            w.wolff_step(x.handle, U, b)
+        ev[k][1].record()
+        torch.cuda.synchronize()
+        for i, (x, b) in enumerate(zip(lat_p, bufs_p)):
+            r = w.records_to_numpy(b, U)
+            flips_p += int(r["C"].astype(np.int64).sum())
+            same = same and np.array_equal(r, recs_b[k][i])
+    t_p = sum(a.elapsed_time(b) for a, b in ev) / 1000.0
+    for x in lat_b + lat_p:
+        x.close()
+    out = {
+        "workload": "%d 2D replicas, L in {64..1024}, T in [2.0, 2.6], seeds 1000+i, "
+                    "%d x %d updates each" % (n_replicas, args.steps, U),
+        "batched_flips_per_s": flips_b / t_b, "plain_flips_per_s": flips_p / t_p,
+        "speedup": (flips_b / t_b) / (flips_p / t_p),
+        "batched_s": t_b, "plain_s": t_p, "records_identical": bool(same),
+        "replica_latency_ms_p50": float(np.percentile(lat_ms, 50)),
+        "replica_latency_ms_p99": float(np.percentile(lat_ms, 99)),
+        "plan": plan.to_json(), "autotune": table,
+    }
+    if embed:
+        return out
+    print(json.dumps({"metric": METRIC, "value": out["batched_flips_per_s"], "unit": UNIT,
+                      "n_gpus": 1, "steps": args.steps, "warmup": 0, "higher_is_better": True,
+                      "config": {"workload": out["workload"]}, "batched": out}), flush=True)
+
+
+def run_served(args, n_requests=200, embed=False):
+    """Poisson stream of Wolff-run requests (the 200-request trace at 200
+    req/s) through the continuous-batching server."""
+    import torch
+
+    from paper_1110_0899_gb300 import serving, workloads
+    torch.cuda.set_device(0)
+    trace = workloads.serving_trace(n_requests)
+    srv = serving.WolffServer(keep_records=True)
+    reqs, summary = srv.serve(trace, max_seconds=args.serve_seconds)
+    srv.close()
+    summary["workload"] = ("%d requests, Poisson 200 req/s, 70%% 2D L 32..2048, 30%% 3D L 16..128, "
+                           "T in [0.9, 1.1] Tc, 1e3..1e5 updates" % n_requests)
+    if embed:
+        return summary
+    print(json.dumps({"metric": METRIC, "value": summary["flips_per_s"], "unit": UNIT,
+                      "n_gpus": 1, "higher_is_better": True,
+                      "config": {"workload": summary["workload"]}, "served": summary}), flush=True)
+
+
 def cpu_baseline(dim, L, T, seed, spins, t, seconds):
     """The oracle (single-threaded C) from the GPU's equilibrated lattice, a
     few updates at a time until `seconds` of CPU work have run."""
@@ -202,6 +302,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "served":
+        return run_served(args)
     import numpy as np
     import torch
 
@@ -219,7 +323,7 @@ def main():
     seed = wl["seed"] + rank
     equil = wl["equil"] if args.equil is None else args.equil
     U = args.updates_per_step
-    sched = {"persistent": w.SCHED_PERSISTENT, "graph": w.SCHED_GRAPH,
+    sched = {"auto": w.SCHED_AUTO, "persistent": w.SCHED_PERSISTENT, "graph": w.SCHED_GRAPH,
              "cluster": w.SCHED_CLUSTER}[args.schedule]
 
     stream = torch.cuda.Stream()
@@ -307,12 +411,31 @@ def main():
             "frac": achieved / peaks["hbm_gbs"], "traffic": None,
             "peak_kind": peak_kind,
             "kernel": {"persistent": "k_persistent<%d>", "graph": "k_graph_level<%d>",
-                       "cluster": "k_team<%d>"}[args.schedule] % dim}
+                       "cluster": "k_team<%d>", "auto": "k_team<%d>"}[args.schedule] % dim}
+    lat.close()
+    batched_out = served_out = None
+    if world == 1 and args.workload in ("2d", "3d") and not args.no_batched:
+        class _A:   # a short batched comparison beside the headline
+            steps, updates_per_step = 3, 100
+        batched_out = run_batched(_A, embed=True)
+        batched_out.pop("autotune", None)
+    if world == 1 and args.workload in ("2d", "3d") and not args.no_served:
+        class _S:
+            serve_seconds = args.embed_serve_seconds
+        served_out = run_served(_S, embed=True)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(dim, L, T, seed, snap, t_snap, args.cpu_seconds)
-    launches = args.steps if args.schedule != "graph" else int(
-        args.steps + (levels + 3).sum())
+    # kernels per step: an L2 warm-up for lattices of 2^22 sites or more, the
+    # persistent schedule's pre-launch reset, the update kernel (or, for the
+    # graph schedule, one call kernel and levels + 3 nodes per update)
+    warm = 1 if L ** dim >= (1 << 22) else 0
+    if args.schedule == "graph":
+        launches = int(args.steps * (1 + warm) + (levels + 3).sum())
+    elif args.schedule == "persistent":
+        launches = args.steps * (2 + warm)
+    else:
+        launches = args.steps * (1 + warm)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps,
@@ -328,13 +451,12 @@ def main():
                    "l2": "256 MB buffer written between timed steps",
                    "parallelism": "replicas x%d" % world},
         "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
-        "clocks": clk,
+        "clocks": clk, "batched": batched_out, "served": served_out,
         "detail": {"mean_cluster": flips / len(records), "mean_levels": float(levels.mean()),
                    "max_levels": int(levels.max()), "ms_per_update": total_ms / len(records),
                    "persistent_counters": {k: stats1[k] - stats0[k] for k in stats1}},
     }
     print(json.dumps(line), flush=True)
-    lat.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 

@@ -69,7 +69,9 @@ enum { WOLFF_LAYOUT_INT8 = 0 };
  *   CLUSTER     one thread-block cluster (1..16 CTAs) per lattice: CTA 0
  *               grows small fronts alone, larger ones are shared by the
  *               cluster with the hardware cluster barrier between levels;
- *   AUTO        the library's choice (see wolff_set_schedule). */
+ *   AUTO        the library's choice: CLUSTER with the largest cluster the
+ *               GPU launches (16 where non-portable sizes are allowed, else
+ *               8), 256 threads, t_up = 128, t_down = 64 (the default). */
 enum {
     WOLFF_SCHED_AUTO = 0,
     WOLFF_SCHED_PERSISTENT = 1,
@@ -162,7 +164,8 @@ wolff_status wolff_set_state(wolff_ctx *ctx, const int8_t *h_spins, uint64_t t);
  * library default).  For PERSISTENT and GRAPH grid_blocks is the number of
  * CTAs (PERSISTENT caps it at what can be co-resident); for CLUSTER it is the
  * cluster size (1, 2, 4, 8 or 16; 16 needs a GPU that allows non-portable
- * cluster sizes).  Results do not depend on the choice. */
+ * cluster sizes).  block_threads: a multiple of 32, at most 512 for PERSISTENT
+ * and CLUSTER, 1024 for GRAPH.  Results do not depend on the choice. */
 wolff_status wolff_set_schedule(wolff_ctx *ctx, int schedule, int grid_blocks,
                                 int block_threads);
 
@@ -175,8 +178,9 @@ wolff_status wolff_set_local_thresholds(wolff_ctx *ctx, uint32_t t_up, uint32_t 
 
 wolff_status wolff_get_info(wolff_ctx *ctx, wolff_info *info);
 
-/* Counters of the persistent schedule, accumulated since ising_init or the
- * last wolff_set_state (tracing aid; the leader CTA's thread 0 keeps them). */
+/* Counters of the persistent and cluster schedules, accumulated since
+ * ising_init or the last wolff_set_state (tracing aid; the leader CTA's
+ * thread 0 keeps them; in the cluster schedule "grid" means "cluster"). */
 typedef struct {
     uint64_t updates;
     uint64_t levels_local;     /* levels grown by the leader CTA alone */
@@ -186,6 +190,8 @@ typedef struct {
     uint64_t ns_finish;        /* device time closing updates (energy, unmark, record) */
     uint64_t handoffs;         /* leader -> all-CTA hand-offs */
     uint64_t grid_finishes;    /* updates closed by all CTAs */
+    uint64_t start_ns;         /* device globaltimer when the last launch began this lattice */
+    uint64_t end_ns;           /* ... and when it finished it */
 } wolff_stats;
 
 /* Reads the counters above.  Synchronises. */
@@ -255,7 +261,7 @@ wolff_status wolff_batch_create(wolff_batch **out, int capacity, void *stream);
  * records to d_records[i] (nullable entries).  The contexts must be distinct,
  * live on the batch's device, and have no work pending on other streams.
  * Larger lattices are launched first.  cluster_size (1..16) and
- * block_threads (multiple of 32, <= 1024) set the team shape.  Asynchronous
+ * block_threads (multiple of 32, <= 512) set the team shape.  Asynchronous
  * on the batch's stream; device errors are reported by each context's next
  * synchronising call. */
 wolff_status wolff_batch_run(wolff_batch *b, wolff_ctx *const *ctxs, int n,

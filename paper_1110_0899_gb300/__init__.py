@@ -48,7 +48,7 @@ class _Info(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in
                 ("updates", "levels_local", "levels_grid", "ns_local", "ns_grid", "ns_finish",
-                 "handoffs", "grid_finishes")]
+                 "handoffs", "grid_finishes", "start_ns", "end_ns")]
 
 
 _lib = None

@@ -39,7 +39,7 @@ struct wolff_ctx {
     cudaStream_t stream = nullptr;
     int device = 0;
     int sm_count = 0;
-    int schedule = WOLFF_SCHED_PERSISTENT;
+    int schedule = WOLFF_SCHED_CLUSTER;
     int blocks = 0, threads = 256;
     int graph_blocks = 0, graph_threads = 0;
     cudaGraphExec_t gexec = nullptr;
@@ -48,8 +48,10 @@ struct wolff_ctx {
     void *rec_stage = nullptr;
     size_t rec_stage_bytes = 0;
     unsigned long long wait_ns = 2000000000ull;
-    uint32_t t_up = 512, t_down = 256;
+    uint32_t t_up = 128, t_down = 64;
+    bool thresholds_set = false;
     int cluster = 8;
+    int max_cluster = 8;
     std::string err;
 };
 
@@ -118,6 +120,32 @@ wolff_status sync_and_check(wolff_ctx *c, DevCtl *host_copy) {
         return (wolff_status)dst->status;
     }
     return WOLFF_OK;
+}
+
+// Largest cluster size (16 or 8) the cluster schedule can launch here.
+int max_cluster_size(int dim, int threads) {
+    const void *fn = team_kernel(dim);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 8;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3((unsigned)threads);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 16;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        return 8;
+    }
+    return 16;
 }
 
 // Every cluster-list slot holds kEmptySlot between updates.
@@ -209,6 +237,8 @@ wolff_status ising_init(wolff_ctx **out, int dim, int L, double J, double T, uin
     c->list = reinterpret_cast<uint32_t *>(base + 2 * sizeof(DevCtl) + round_up(c->N, kAlign));
     c->blocks = default_blocks(c);
     c->threads = 256;
+    c->max_cluster = max_cluster_size(dim, c->threads);
+    c->cluster = c->max_cluster;
 
     const StepParams p = make_params(c);
     e = cudaMemsetAsync(c->ws, 0, 2 * sizeof(DevCtl) + round_up(c->N, kAlign), c->stream);
@@ -240,12 +270,19 @@ wolff_status wolff_set_schedule(wolff_ctx *c, int schedule, int grid_blocks, int
     if (block_threads != 0 && (block_threads < 32 || block_threads > 1024 || block_threads % 32))
         return fail(c, WOLFF_EINVAL, "block_threads must be a multiple of 32 in [32, 1024]");
     if (grid_blocks < 0) return fail(c, WOLFF_EINVAL, "grid_blocks must be >= 0");
-    c->schedule = schedule == WOLFF_SCHED_AUTO ? WOLFF_SCHED_PERSISTENT : schedule;
+    const int sched_eff = schedule == WOLFF_SCHED_AUTO ? WOLFF_SCHED_CLUSTER : schedule;
+    if (sched_eff != WOLFF_SCHED_GRAPH && (block_threads ? block_threads : c->threads) > 512)
+        return fail(c, WOLFF_EINVAL, "persistent and cluster schedules take at most 512 threads");
+    c->schedule = sched_eff;
     if (block_threads) c->threads = block_threads;
     if (c->schedule == WOLFF_SCHED_CLUSTER) {
-        c->cluster = grid_blocks ? grid_blocks : 8;
+        c->cluster = grid_blocks ? grid_blocks : c->max_cluster;
     } else {
         c->blocks = grid_blocks ? grid_blocks : default_blocks(c);
+    }
+    if (!c->thresholds_set) {   // measured defaults of each schedule
+        c->t_up = c->schedule == WOLFF_SCHED_PERSISTENT ? 512u : 128u;
+        c->t_down = c->t_up / 2;
     }
     if (c->gexec && (c->graph_blocks != c->blocks || c->graph_threads != c->threads)) {
         cudaGraphExecDestroy(c->gexec);
@@ -262,6 +299,7 @@ wolff_status wolff_set_local_thresholds(wolff_ctx *c, uint32_t t_up, uint32_t t_
         return fail(c, WOLFF_EINVAL, "need t_down <= t_up <= 2048");
     c->t_up = t_up;
     c->t_down = t_down;
+    c->thresholds_set = true;
     return WOLFF_OK;
 }
 
@@ -272,6 +310,11 @@ wolff_status wolff_step(wolff_ctx *c, uint64_t n_updates, void *d_records) {
     p.records = reinterpret_cast<wolff_record *>(d_records);
     p.n = n_updates;
     cudaError_t e;
+    // a large lattice may have been pushed out of L2 since the last call
+    if (c->N >= (1u << 22)) {
+        e = launch_prefetch_l2(c->spins, c->N, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "prefetch");
+    }
     if (c->schedule == WOLFF_SCHED_CLUSTER) {
         e = launch_team(c->dim, p, nullptr, 1, c->cluster, c->threads, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "cluster launch");
@@ -427,6 +470,8 @@ wolff_status wolff_get_stats(wolff_ctx *c, wolff_stats *st) {
     st->ns_finish = h.st_ns_finish;
     st->handoffs = h.st_handoffs;
     st->grid_finishes = h.st_grid_finishes;
+    st->start_ns = h.st_start_ns;
+    st->end_ns = h.st_end_ns;
     return WOLFF_OK;
 }
 
@@ -488,7 +533,7 @@ wolff_status wolff_batch_run(wolff_batch *b, wolff_ctx *const *ctxs, int n,
     if (cluster_size != 1 && cluster_size != 2 && cluster_size != 4 && cluster_size != 8 &&
         cluster_size != 16)
         return WOLFF_EINVAL;
-    if (block_threads < 32 || block_threads > 1024 || block_threads % 32) return WOLFF_EINVAL;
+    if (block_threads < 32 || block_threads > 512 || block_threads % 32) return WOLFF_EINVAL;
     if (b->pending) {   // the previous staging copy must have been consumed
         if (cudaEventSynchronize(b->copied) != cudaSuccess) return WOLFF_ECUDA;
         b->pending = false;

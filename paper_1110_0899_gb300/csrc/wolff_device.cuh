@@ -46,6 +46,48 @@ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1,
     return out;
 }
 
+// K independent Philox4x32-10 evaluations sharing the key and the last three
+// counter words, run in lockstep so that their dependent multiply chains
+// overlap (one evaluation's latency for all K).
+template <int K>
+__device__ __forceinline__ void philox4x32_10_lanes(const uint32_t c0[K], uint32_t c1,
+                                                    uint32_t c2, uint32_t c3, uint32_t k0,
+                                                    uint32_t k1, Philox4 out[K]) {
+    const uint32_t kMul0 = 0xD2511F53u, kMul1 = 0xCD9E8D57u;
+    const uint32_t kWeyl0 = 0x9E3779B9u, kWeyl1 = 0xBB67AE85u;
+    uint32_t a[K], b[K], c[K], d[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        a[k] = c0[k];
+        b[k] = c1;
+        c[k] = c2;
+        d[k] = c3;
+    }
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const uint32_t hi0 = __umulhi(kMul0, a[k]);
+            const uint32_t lo0 = kMul0 * a[k];
+            const uint32_t hi1 = __umulhi(kMul1, c[k]);
+            const uint32_t lo1 = kMul1 * c[k];
+            a[k] = hi1 ^ b[k] ^ k0;
+            b[k] = lo1;
+            c[k] = hi0 ^ d[k] ^ k1;
+            d[k] = lo0;
+        }
+        k0 += kWeyl0;
+        k1 += kWeyl1;
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        out[k].v[0] = a[k];
+        out[k].v[1] = b[k];
+        out[k].v[2] = c[k];
+        out[k].v[3] = d[k];
+    }
+}
+
 // ---- lattice coordinates ---------------------------------------------------
 template <int DIM> struct Pack;
 template <> struct Pack<2> {
@@ -363,30 +405,55 @@ __device__ __forceinline__ long long block_sum(long long v) {
 }
 
 // ---- the expansion of one wave-front site (step (iii') of section 4) -------
-// Draws the site's 2*DIM bond random words -- its own forward bonds from one
-// Philox call, each backward bond from its owner's call -- and claims every
-// neighbour behind an active bond directly.  No neighbour is read first: the
-// claim's old bit says whether the neighbour was still parallel to the seed
-// spin and unclaimed, so one L2 round trip per level is saved.  Returns the
-// mask of neighbour slots won; nb receives their coordinates.
+// Issues the 2*DIM neighbour loads (L2, bypassing L1 because other CTAs
+// write them) and, while they are in flight, the DIM+1 Philox draws the
+// site's bonds need -- its own call for the forward bonds, each backward
+// neighbour's call for the bond it owns -- interleaved so that they cost one
+// draw's latency.  Then claims only the neighbours still parallel to the seed
+// spin behind an active bond: atomics from one thread overlap poorly, so
+// they are spent only where a claim can succeed.  Returns the mask of
+// neighbour slots won; nb receives their coordinates.
 template <int DIM>
 __device__ __forceinline__ uint32_t expand_site(const StepParams &p, uint32_t packed,
                                                 uint32_t sig0bit, uint32_t tlo,
                                                 uint32_t thi, Neighbours<DIM> &nb) {
     uint32_t i;
     neighbours<DIM>(p.g, packed, &i, nb);
-    uint32_t r[2 * DIM];
-    const Philox4 fwd = philox4x32_10(i, tlo, thi, kTagBond, p.key0, p.key1);
+    uint8_t v[2 * DIM];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-        r[2 * d] = fwd.v[d];
-        r[2 * d + 1] = philox4x32_10(nb.idx[2 * d + 1], tlo, thi, kTagBond, p.key0, p.key1).v[d];
+    for (int s = 0; s < 2 * DIM; ++s) v[s] = __ldcg(p.spins + nb.idx[s]);
+    uint32_t owners[DIM + 1];
+    owners[0] = i;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) owners[d + 1] = nb.idx[2 * d + 1];
+    Philox4 draw[DIM + 1];
+    philox4x32_10_lanes<DIM + 1>(owners, tlo, thi, kTagBond, p.key0, p.key1, draw);
+    // decide every claim first, then issue the atomics back to back: a claim
+    // whose outcome gated the next one would serialise their latencies
+    uint32_t want = 0;
+#pragma unroll
+    for (int s = 0; s < 2 * DIM; ++s) {
+        const int d = s >> 1;
+        const uint32_t r = (s & 1) ? draw[d + 1].v[d] : draw[0].v[d];
+        if ((uint32_t)(v[s] & 1u) == sig0bit && (unsigned long long)r < p.thr) want |= 1u << s;
+    }
+    unsigned int old[2 * DIM];
+#pragma unroll
+    for (int s = 0; s < 2 * DIM; ++s) {
+        old[s] = 0;
+        if (want & (1u << s)) {
+            unsigned int *w = reinterpret_cast<unsigned int *>(p.spins) + (nb.idx[s] >> 2);
+            const unsigned int bit = 1u << ((nb.idx[s] & 3u) * 8u);
+            old[s] = sig0bit ? atomicAnd(w, ~bit) : atomicOr(w, bit);
+        }
     }
     uint32_t won = 0;
 #pragma unroll
-    for (int s = 0; s < 2 * DIM; ++s)
-        if ((unsigned long long)r[s] < p.thr && claim_site(p.spins, nb.idx[s], sig0bit))
-            won |= 1u << s;
+    for (int s = 0; s < 2 * DIM; ++s) {
+        const unsigned int bit = 1u << ((nb.idx[s] & 3u) * 8u);
+        // the claim wins when bit 0 still held the seed spin (see claim_site)
+        if ((want & (1u << s)) && (((old[s] & bit) != 0u) == (sig0bit != 0u))) won |= 1u << s;
+    }
     return won;
 }
 

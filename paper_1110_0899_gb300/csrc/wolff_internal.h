@@ -76,6 +76,7 @@ struct alignas(256) DevCtl {
     unsigned long long st_levels_local, st_levels_grid;
     unsigned long long st_ns_local, st_ns_grid, st_ns_finish;
     unsigned long long st_handoffs, st_grid_finishes;
+    unsigned long long st_start_ns, st_end_ns;   // globaltimer at the last launch's start/end
 };
 static_assert(sizeof(DevCtl) % 256 == 0 && sizeof(DevCtl) <= 1024, "control block layout");
 
@@ -118,6 +119,7 @@ cudaError_t launch_philox(uint32_t k0, uint32_t k1, const uint32_t *ctr,
                           uint32_t *out, unsigned long long n, cudaStream_t s);
 cudaError_t launch_reset_ctl(DevCtl *ctl, unsigned long long t, cudaStream_t s);
 cudaError_t launch_prelaunch(DevCtl *ctl, cudaStream_t s);
+cudaError_t launch_prefetch_l2(const void *base, unsigned long long bytes, cudaStream_t s);
 
 // Persistent cooperative schedule.
 const void *persistent_kernel(int dim);

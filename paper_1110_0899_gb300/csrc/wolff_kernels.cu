@@ -42,6 +42,25 @@ cudaError_t launch_init(uint8_t *spins, Geometry g, uint32_t k0, uint32_t k1,
 }
 
 // ---------------------------------------------------------------------------
+// L2 warm-up: a lattice evicted from L2 (by other work between calls) would
+// make every early access of the update chain a DRAM round trip; streaming
+// it once at full bandwidth brings it back.  Each thread touches one 128-byte
+// line with a prefetch.
+__global__ void k_prefetch_l2(const uint8_t *base, unsigned long long bytes) {
+    for (unsigned long long off = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) * 128ull;
+         off < bytes; off += (unsigned long long)gridDim.x * blockDim.x * 128ull)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(base + off));
+}
+
+cudaError_t launch_prefetch_l2(const void *base, unsigned long long bytes, cudaStream_t s) {
+    if (bytes == 0) return cudaSuccess;
+    const unsigned long long lines = (bytes + 127) / 128;
+    k_prefetch_l2<<<grid_for((lines + 255) / 256, 2048ull), 256, 0, s>>>(
+        static_cast<const uint8_t *>(base), bytes);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // a8: full recount.  One CTA per row of L sites (rows along x), threads over
 // x; E_bond gets s_i (s_{x+1} + s_{y+1} [+ s_{z+1}]), M gets s_i.
 template <int DIM>
@@ -176,6 +195,7 @@ __global__ void k_reset_ctl(DevCtl *ctl, unsigned long long t) {
     ctl->st_updates = ctl->st_levels_local = ctl->st_levels_grid = 0;
     ctl->st_ns_local = ctl->st_ns_grid = ctl->st_ns_finish = 0;
     ctl->st_handoffs = ctl->st_grid_finishes = 0;
+    ctl->st_start_ns = ctl->st_end_ns = 0;
 }
 
 // Before every persistent launch: command sequence, barrier word and
@@ -455,7 +475,7 @@ __device__ void worker_loop(const StepParams &p, SharedLocal &sh, unsigned int &
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(1024) k_persistent(StepParams p) {
+__global__ void __launch_bounds__(512, 1) k_persistent(StepParams p) {
     DevCtl *ctl = p.ctl;
     __shared__ SharedLocal sh;
     unsigned int gen = 0;   // the pre-launch kernel zeroed the generation
@@ -475,6 +495,7 @@ __global__ void __launch_bounds__(1024) k_persistent(StepParams p) {
     unsigned long long st_local = 0, st_grid = 0, ns_local = 0, ns_grid = 0, ns_finish = 0;
     unsigned long long handoffs = 0, grid_fin = 0;
     if (t0) {
+        ctl->st_start_ns = global_ns();
         E = ctl->E;
         M = ctl->M;
         total_C = ctl->total_C;
@@ -633,6 +654,7 @@ __global__ void __launch_bounds__(1024) k_persistent(StepParams p) {
         ctl->st_ns_finish += ns_finish;
         ctl->st_handoffs += handoffs;
         ctl->st_grid_finishes += grid_fin;
+        ctl->st_end_ns = global_ns();
         publish(ctl, seq, kCmdExit, 0, 0, 0, 0, 0);
     }
 }

@@ -174,6 +174,7 @@ __device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_gro
     unsigned long long st_local = 0, st_team = 0, ns_local = 0, ns_team = 0, ns_finish = 0;
     unsigned long long handoffs = 0, team_fin = 0;
     if (t0) {
+        ctl->st_start_ns = global_ns();
         E = ctl->E;
         M = ctl->M;
         total_C = ctl->total_C;
@@ -325,6 +326,7 @@ __device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_gro
         ctl->st_ns_finish += ns_finish;
         ctl->st_handoffs += handoffs;
         ctl->st_grid_finishes += team_fin;
+        ctl->st_end_ns = global_ns();
     }
     if (has_team) {
         announce(sh, cl, kTeamExit, 0, 0, 0, 0, 0);
@@ -333,7 +335,7 @@ __device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_gro
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(1024) k_team(StepParams single, const StepParams *table) {
+__global__ void __launch_bounds__(512, 1) k_team(StepParams single, const StepParams *table) {
     cg::cluster_group cl = cg::this_cluster();
     __shared__ TeamShared sh;
     const unsigned int job = blockIdx.x / cl.num_blocks();

@@ -1,0 +1,188 @@
+"""Serving loop: continuous batching of Wolff-run requests on one GPU.
+
+A request asks for n updates of a fresh lattice (dim, L, T, seed) and gets
+back its per-update records (|C|, levels, E_bond, M) and final E, M.  The
+server keeps every admitted lattice resident on the device and works in
+epochs: at each epoch boundary it admits the requests that have arrived, as
+long as their memory (workspace + record buffer) fits the budget, then runs
+up to `epoch_updates` updates of every active request in shared batched
+launches (one thread-block cluster per lattice; large lattices get larger
+teams on a second stream), and retires the requests that are done.
+Requests that arrive while others are on the GPU therefore join at the next
+epoch and their work overlaps on the device.  A request's chain does not
+depend on what it shares the GPU with: its records equal those of the same
+request run alone.
+"""
+import collections
+import time
+
+import numpy as np
+
+from . import RECORD_BYTES, WolffBatch, WolffLattice, records_to_numpy, wolff_workspace_bytes
+
+
+class Request:
+    __slots__ = ("spec", "lattice", "records", "done", "admitted_s", "finished_s", "result",
+                 "ns_per_update", "quota")
+
+    def __init__(self, spec):
+        self.spec = spec
+        self.lattice = None
+        self.records = None
+        self.done = 0
+        self.admitted_s = None
+        self.finished_s = None
+        self.result = None
+        self.ns_per_update = None
+        self.quota = 0
+
+    @property
+    def remaining(self):
+        return self.spec["n_updates"] - self.done
+
+    def memory_bytes(self):
+        s = self.spec
+        return wolff_workspace_bytes(s["dim"], s["L"]) + s["n_updates"] * RECORD_BYTES
+
+
+class WolffServer:
+    def __init__(self, memory_budget=None, epoch_updates=1 << 20, big_sites=1 << 18,
+                 small_team=(1, 256), big_team=(4, 256), max_active=4096, keep_records=True,
+                 epoch_seconds=0.02, first_quota=16):
+        import torch
+        if memory_budget is None:
+            free, _ = torch.cuda.mem_get_info()
+            memory_budget = int(free * 0.6)
+        self.memory_budget = int(memory_budget)
+        self.epoch_updates = int(epoch_updates)
+        self.big_sites = int(big_sites)
+        self.small_team = small_team
+        self.big_team = big_team
+        self.max_active = int(max_active)
+        self.keep_records = keep_records
+        # each request's share of an epoch is sized from its measured cost per
+        # update so that one slow lattice does not hold the others back
+        self.epoch_seconds = float(epoch_seconds)
+        self.first_quota = int(first_quota)
+        self.streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        self.batches = [WolffBatch(max_active, stream=s) for s in self.streams]
+
+    def _admit(self, req, now):
+        import torch
+        s = req.spec
+        req.lattice = WolffLattice(s["dim"], s["L"], s["T"], seed=s["seed"])
+        req.records = torch.empty(max(1, s["n_updates"]) * RECORD_BYTES, dtype=torch.uint8,
+                                  device="cuda")
+        req.admitted_s = now
+
+    def _quota(self, r):
+        if r.ns_per_update is None:
+            q = self.first_quota
+        else:
+            q = int(self.epoch_seconds * 1e9 / max(r.ns_per_update, 1.0))
+        return max(1, min(q, self.epoch_updates, r.remaining))
+
+    def _epoch(self, active):
+        import torch
+        cur = torch.cuda.current_stream()
+        groups = [[], []]
+        for r in active:
+            groups[1 if r.lattice.N >= self.big_sites else 0].append(r)
+        for g, (cs, th), st, b in zip(groups, (self.small_team, self.big_team), self.streams,
+                                      self.batches):
+            if not g:
+                continue
+            st.wait_stream(cur)
+            for r in g:
+                r.quota = self._quota(r)
+            recs = [r.records[r.done * RECORD_BYTES:] for r in g]
+            b.run([r.lattice for r in g], [r.quota for r in g], recs, cluster_size=cs,
+                  block_threads=th)
+        for st in self.streams:
+            cur.wait_stream(st)
+        torch.cuda.synchronize()
+        for r in active:
+            st = r.lattice.stats()
+            dt = max(1, st["end_ns"] - st["start_ns"])
+            per = dt / r.quota
+            r.ns_per_update = per if r.ns_per_update is None else 0.5 * (r.ns_per_update + per)
+            r.done += r.quota
+
+    def _retire(self, req, now):
+        E, M, C = req.lattice.measure()
+        rec = records_to_numpy(req.records, req.spec["n_updates"]) if self.keep_records else None
+        req.result = {"E_bond": E, "M": M, "last_C": C, "records": rec,
+                      "flips": int(rec["C"].astype(np.int64).sum()) if rec is not None else None}
+        req.finished_s = now
+        req.lattice.close()
+        req.lattice = None
+        req.records = None
+
+    def serve(self, trace, time_scale=1.0, max_seconds=None):
+        """Runs the trace (arrival_s scaled by time_scale) in real time.
+        Returns (requests, summary)."""
+        pending = collections.deque(sorted((Request(s) for s in trace),
+                                           key=lambda r: r.spec["arrival_s"]))
+        everyone = list(pending)
+        active = []
+        mem_used = 0
+        max_backlog = 0
+        epochs = 0
+        t0 = time.perf_counter()
+        while pending or active:
+            now = time.perf_counter() - t0
+            if max_seconds is not None and now > max_seconds:
+                break
+            while (pending and pending[0].spec["arrival_s"] * time_scale <= now
+                   and len(active) < self.max_active
+                   and mem_used + pending[0].memory_bytes() <= self.memory_budget):
+                r = pending.popleft()
+                self._admit(r, now)
+                mem_used += r.memory_bytes()
+                active.append(r)
+            waiting = sum(1 for r in pending if r.spec["arrival_s"] * time_scale <= now)
+            max_backlog = max(max_backlog, waiting)
+            if not active:
+                if pending:
+                    delay = pending[0].spec["arrival_s"] * time_scale - now
+                    if delay > 0:
+                        time.sleep(min(delay, 0.01))
+                continue
+            self._epoch(active)
+            epochs += 1
+            now = time.perf_counter() - t0
+            still = []
+            for r in active:
+                if r.remaining == 0:
+                    self._retire(r, now)
+                    mem_used -= r.memory_bytes()
+                else:
+                    still.append(r)
+            active = still
+        wall = time.perf_counter() - t0
+        partial_flips = 0
+        for r in active:   # stopped early: count the updates already run
+            if r.done:
+                partial_flips += int(records_to_numpy(r.records, r.done)["C"].astype(np.int64).sum())
+            r.lattice.close()
+        done = [r for r in everyone if r.finished_s is not None]
+        lat = np.array([r.finished_s - r.spec["arrival_s"] * time_scale for r in done])
+        flips = sum(r.result["flips"] or 0 for r in done) + partial_flips
+        updates = sum(r.spec["n_updates"] for r in done) + sum(r.done for r in active)
+        last_arrival = max((r.spec["arrival_s"] for r in everyone), default=0.0) * time_scale
+        summary = {
+            "requests": len(everyone), "completed": len(done), "epochs": epochs,
+            "wall_s": wall, "flips": flips, "updates": updates,
+            "flips_per_s": flips / wall if wall > 0 else 0.0,
+            "updates_per_s": updates / wall if wall > 0 else 0.0,
+            "latency_p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
+            "latency_p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
+            "max_backlog": max_backlog,
+            "offered_span_s": last_arrival,
+            "saturated": wall > 1.5 * last_arrival + 1.0,
+        }
+        return everyone, summary
+
+    def close(self):
+        for b in self.batches:
+            b.close()

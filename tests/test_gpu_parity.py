@@ -16,15 +16,18 @@ from _gpu import assert_records_equal, oracle_trajectory, require_cuda
 pytestmark = pytest.mark.gpu
 
 TC2 = 2.0 / math.log(1.0 + math.sqrt(2.0))
-SCHEDS = ("persistent", "graph")
+SCHEDS = ("persistent", "graph", "cluster")
 
 
 def sched_id(w, name):
-    return {"persistent": w.SCHED_PERSISTENT, "graph": w.SCHED_GRAPH}[name]
+    return {"persistent": w.SCHED_PERSISTENT, "graph": w.SCHED_GRAPH,
+            "cluster": w.SCHED_CLUSTER}[name]
 
 
 def run_gpu(w, dim, L, T, seed, n, sched, blocks=0, threads=0):
     lat = w.WolffLattice(dim, L, T, seed=seed)
+    if sched == "cluster" and blocks not in (0, 1, 2, 4, 8, 16):
+        blocks = 8   # CTA counts of the other schedules map to a cluster size
     lat.set_schedule(sched_id(w, sched), blocks, threads)
     rec = lat.step(n)
     spins, t = lat.get_state()
@@ -77,7 +80,7 @@ def test_3d_l8(sched):
 # a single CTA, a one-warp CTA and many CTAs over a tiny lattice
 SHAPES = [
     (2, 2, 1.0, 300, 1, 32), (2, 3, TC2, 300, 0, 0), (3, 2, 4.5115, 300, 3, 64),
-    (3, 3, 3.0, 300, 0, 0), (2, 37, TC2, 400, 5, 96), (2, 100, 2.0, 300, 0, 1024),
+    (3, 3, 3.0, 300, 0, 0), (2, 37, TC2, 400, 5, 96), (2, 100, 2.0, 300, 0, 512),
     (3, 13, 4.5115, 300, 0, 0), (3, 17, 4.0, 200, 64, 256), (2, 64, 2.6, 400, 152, 128),
     (2, 255, TC2, 150, 0, 0),
 ]
@@ -124,8 +127,9 @@ def test_medium_lattices(sched):
 THRESHOLDS = [(0, 0), (1, 1), (8, 4), (64, 8), (512, 256), (2048, 2048)]
 
 
+@pytest.mark.parametrize("sched", ["persistent", "cluster"])
 @pytest.mark.parametrize("t_up,t_down", THRESHOLDS)
-def test_leader_grid_handoffs(t_up, t_down):
+def test_leader_grid_handoffs(t_up, t_down, sched):
     """Large clusters from an ordered start cross between the leader-only and
     the all-CTA phases many times; every threshold gives the oracle's chain."""
     torch, w = require_cuda()
@@ -133,6 +137,7 @@ def test_leader_grid_handoffs(t_up, t_down):
         up = np.ones(L ** dim, dtype=np.int8)
         ref, s_ref = oracle_trajectory(dim, L, T, 31, n, s=up)
         lat = w.WolffLattice(dim, L, T, seed=31)
+        lat.set_schedule(w.SCHED_PERSISTENT if sched == "persistent" else w.SCHED_CLUSTER)
         lat.set_local_thresholds(t_up, t_down)
         lat.set_state(up, 0)
         rec = lat.step(n)

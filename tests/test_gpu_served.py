@@ -1,0 +1,97 @@
+"""Batched plans, the autotuner and the serving loop do not change results.
+
+Every lattice follows the chain it would follow alone, whatever it shares a
+launch with: records from the batched runner and from the server are
+compared bit for bit with the same lattice run alone (and, for a few, with
+the CPU oracle)."""
+import numpy as np
+import pytest
+
+from _gpu import assert_records_equal, oracle_trajectory, require_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _small_specs(n=40):
+    from paper_1110_0899_gb300 import workloads
+    specs = workloads.batched_replicas(n, sizes=(16, 32, 48, 64, 96))
+    # a few 3D lattices too
+    for i in range(0, n, 7):
+        specs[i] = dict(dim=3, L=int(8 + i % 5), T=4.5115 * (0.9 + 0.01 * i), seed=specs[i]["seed"])
+    return specs
+
+
+def test_split_plan_runner_matches_alone():
+    torch, w = require_cuda()
+    from paper_1110_0899_gb300 import batched
+    specs = _small_specs()
+    lats = [w.WolffLattice(s["dim"], s["L"], s["T"], seed=s["seed"]) for s in specs]
+    big = [i for i, s in enumerate(specs) if s["L"] ** s["dim"] >= 48 * 48]
+    small = [i for i in range(len(specs)) if i not in big]
+    plan = batched.Plan([(big, 4, 256), (small, 1, 128)], "test split")
+    r = batched.BatchedRunner(lats, plan)
+    got = []
+    for n in (30, 45):
+        bufs = r.run(n)
+        torch.cuda.synchronize()
+        got.append(r.records_numpy(bufs, n))
+    r.close()
+    for i, s in enumerate(specs):
+        rec = np.concatenate([got[0][i], got[1][i]])
+        if i % 5 == 0:
+            ref, s_ref = oracle_trajectory(s["dim"], s["L"], s["T"], s["seed"], 75)
+            assert_records_equal(rec, ref, "replica %d vs oracle" % i)
+            assert np.array_equal(lats[i].get_state()[0], s_ref)
+        else:
+            alone = w.WolffLattice(s["dim"], s["L"], s["T"], seed=s["seed"])
+            assert_records_equal(rec, alone.step(75), "replica %d vs alone" % i)
+            alone.close()
+    for x in lats:
+        x.close()
+
+
+def test_autotune_returns_a_working_plan():
+    torch, w = require_cuda()
+    from paper_1110_0899_gb300 import batched
+    specs = _small_specs(16)
+    plan, table = batched.autotune(specs, probe_updates=8, use_cache=False)
+    assert len(table) == len(batched.candidate_plans(specs))
+    assert all(t["seconds"] > 0 for t in table)
+    lats = [w.WolffLattice(s["dim"], s["L"], s["T"], seed=s["seed"]) for s in specs]
+    r = batched.BatchedRunner(lats, plan)
+    bufs = r.run(20)
+    torch.cuda.synchronize()
+    got = r.records_numpy(bufs, 20)
+    r.close()
+    for i, s in enumerate(specs):
+        ref, _ = oracle_trajectory(s["dim"], s["L"], s["T"], s["seed"], 20)
+        assert_records_equal(got[i], ref, "autotuned plan replica %d" % i)
+        lats[i].close()
+
+
+def test_served_requests_equal_their_runs_alone():
+    """Requests of mixed size and dimension arrive while others run; each
+    result equals the same request run alone."""
+    torch, w = require_cuda()
+    from paper_1110_0899_gb300 import serving, workloads
+    trace = workloads.serving_trace(24, rate=400.0, l2d=(16, 200), l3d=(6, 24),
+                                    updates=(50, 3000))
+    srv = serving.WolffServer(epoch_updates=400, big_sites=1 << 12, big_team=(2, 256),
+                              memory_budget=1 << 30)
+    reqs, summary = srv.serve(trace)
+    srv.close()
+    assert summary["completed"] == len(trace)
+    assert summary["epochs"] > 1
+    overlapped = sum(1 for r in reqs if r.spec["n_updates"] > 400)
+    assert overlapped > 0   # some requests spanned several epochs next to others
+    for k, r in enumerate(reqs):
+        s = r.spec
+        alone = w.WolffLattice(s["dim"], s["L"], s["T"], seed=s["seed"])
+        ref = alone.step(s["n_updates"])
+        E, M, _ = alone.measure()
+        alone.close()
+        assert_records_equal(r.result["records"], ref, "request %d" % s["id"])
+        assert (r.result["E_bond"], r.result["M"]) == (E, M)
+        if k < 3:
+            orc, _ = oracle_trajectory(s["dim"], s["L"], s["T"], s["seed"], s["n_updates"])
+            assert_records_equal(r.result["records"], orc, "request %d vs oracle" % s["id"])

@@ -39,6 +39,25 @@ UNIT = "flipped spins/s"
 ALGO_BYTES_PER_FLIP = {2: 23.0, 3: 27.0}
 
 TC2 = 2.0 / math.log(1.0 + math.sqrt(2.0))
+# DRAM traffic of one timed k_team launch of the default workload, from the
+# committed ncu capture (profiles/k_team_2d_L4096_random_start.md), valid only
+# while the kernel sources hash to the captured value.
+TRAFFIC_CAPTURES = {
+    ("2d", 100): {"src": "1566f913e7cc", "bytes_per_launch": 120064 + 0},
+}
+
+
+def kernel_source_hash():
+    import glob
+    import hashlib
+    h = hashlib.sha1()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1110_0899_gb300", "csrc", "*"))):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
 WORKLOADS = {
     # the configurations as specified: random start, 2000 equilibration updates
     "2d": dict(dim=2, L=4096, T=TC2, seed=2, equil=2000, start="random"),
@@ -135,6 +154,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def rank_seed(base_seed, rank):
+    """Replicas only: every rank runs its own lattice, seeded base + rank."""
+    return base_seed + rank
+
+
+def aggregate_ranks(total_ms, flips, device):
+    """Whole-job numbers over the ranks: the slowest rank's time and the sum
+    of all ranks' flipped spins (the only collective, on the host path)."""
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    ff = torch.tensor([float(flips)], dtype=torch.float64, device=device)
+    dist.all_reduce(ff, op=dist.ReduceOp.SUM)
+    return float(tt.item()), float(ff.item())
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -154,7 +190,11 @@ def run_reference(args):
     dim, L, T, seed = wl["dim"], wl["L"], wl["T"], wl["seed"]
     thr = oracle.bond_threshold(1.0, T)
     s = oracle.init_lattice(dim, L, seed)
-    equil = 300 if args.equil is None else args.equil
+    if wl["start"] == "ordered":
+        s[:] = 1
+    # the configuration's equilibration, unrecorded (the oracle skips its full
+    # recount when no record is asked for)
+    equil = wl["equil"] if args.equil is None else args.equil
     oracle.run(dim, L, thr, seed, 0, equil, s, records=False)
     t = equil
     per_step = 4
@@ -320,7 +360,7 @@ def main():
 
     wl = WORKLOADS[args.workload]
     dim, L, T = wl["dim"], wl["L"], wl["T"]
-    seed = wl["seed"] + rank
+    seed = rank_seed(wl["seed"], rank)
     equil = wl["equil"] if args.equil is None else args.equil
     U = args.updates_per_step
     sched = {"auto": w.SCHED_AUTO, "persistent": w.SCHED_PERSISTENT, "graph": w.SCHED_GRAPH,
@@ -376,12 +416,7 @@ def main():
         total_ms = float(sum(step_ms))
         levels = records["levels"].astype(np.int64)
         if world > 1:
-            import torch.distributed as dist
-            tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ff = torch.tensor([flips], device="cuda", dtype=torch.float64)
-            dist.all_reduce(ff, op=dist.ReduceOp.SUM)
-            total_ms_all, flips_all = float(tt.item()), float(ff.item())
+            total_ms_all, flips_all = aggregate_ranks(total_ms, flips, "cuda")
         else:
             total_ms_all, flips_all = total_ms, float(flips)
         value = flips_all / (total_ms_all / 1000.0)
@@ -407,8 +442,12 @@ def main():
     per_launch_flips = flips / args.steps
     avg_launch_s = total_ms / args.steps / 1000.0
     achieved = ALGO_BYTES_PER_FLIP[dim] * per_launch_flips / avg_launch_s / 1e9
+    cap = TRAFFIC_CAPTURES.get((args.workload, U))
+    traffic = None
+    if cap and args.schedule in ("auto", "cluster") and kernel_source_hash() == cap["src"]:
+        traffic = cap["bytes_per_launch"]
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
             "peak_kind": peak_kind,
             "kernel": {"persistent": "k_persistent<%d>", "graph": "k_graph_level<%d>",
                        "cluster": "k_team<%d>", "auto": "k_team<%d>"}[args.schedule] % dim}

@@ -43,7 +43,7 @@ TC2 = 2.0 / math.log(1.0 + math.sqrt(2.0))
 # committed ncu capture (profiles/k_team_2d_L4096_random_start.md), valid only
 # while the kernel sources hash to the captured value.
 TRAFFIC_CAPTURES = {
-    ("2d", 100): {"src": "1566f913e7cc", "bytes_per_launch": 120064 + 0},
+    ("2d", 100): {"src": "1566f913e7cc", "bytes_per_launch": 120064 + 0},   # superseded kernel
 }
 
 
@@ -72,11 +72,11 @@ WORKLOADS = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS) + ["batched", "served"])
-    ap.add_argument("--updates-per-step", type=int, default=100)
+    ap.add_argument("--updates-per-step", type=int, default=1000)
     ap.add_argument("--equil", type=int, default=None)
     ap.add_argument("--schedule", default="auto",
                     choices=["auto", "persistent", "graph", "cluster"])

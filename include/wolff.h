@@ -71,7 +71,8 @@ enum { WOLFF_LAYOUT_INT8 = 0 };
  *               cluster with the hardware cluster barrier between levels;
  *   AUTO        the library's choice: CLUSTER with the largest cluster the
  *               GPU launches (16 where non-portable sizes are allowed, else
- *               8), 256 threads, t_up = 128, t_down = 64 (the default). */
+ *               8), 512 threads, t_up = 128, t_down = 64, bursts on (the
+ *               default). */
 enum {
     WOLFF_SCHED_AUTO = 0,
     WOLFF_SCHED_PERSISTENT = 1,
@@ -176,6 +177,14 @@ wolff_status wolff_set_schedule(wolff_ctx *ctx, int schedule, int grid_blocks,
  * t_down <= t_up <= 2048.  Results do not depend on the values. */
 wolff_status wolff_set_local_thresholds(wolff_ctx *ctx, uint32_t t_up, uint32_t t_down);
 
+/* Cluster schedule and batched runs: burst mode (on by default).  While the
+ * recent clusters are small the leader CTA grows up to one update per warp at
+ * once on the same lattice, then commits in order the longest prefix whose
+ * updates read no site flipped by an earlier update of the prefix; the rest
+ * run the ordinary way.  A committed update is exactly the serial one, so
+ * results do not depend on the setting. */
+wolff_status wolff_set_burst(wolff_ctx *ctx, int enable);
+
 wolff_status wolff_get_info(wolff_ctx *ctx, wolff_info *info);
 
 /* Counters of the persistent and cluster schedules, accumulated since
@@ -192,6 +201,8 @@ typedef struct {
     uint64_t grid_finishes;    /* updates closed by all CTAs */
     uint64_t start_ns;         /* device globaltimer when the last launch began this lattice */
     uint64_t end_ns;           /* ... and when it finished it */
+    uint64_t burst_updates;    /* updates committed by burst mode (cluster schedule) */
+    uint64_t bursts;           /* bursts attempted */
 } wolff_stats;
 
 /* Reads the counters above.  Synchronises. */

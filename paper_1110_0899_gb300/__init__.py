@@ -48,7 +48,7 @@ class _Info(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in
                 ("updates", "levels_local", "levels_grid", "ns_local", "ns_grid", "ns_finish",
-                 "handoffs", "grid_finishes", "start_ns", "end_ns")]
+                 "handoffs", "grid_finishes", "start_ns", "end_ns", "burst_updates", "bursts")]
 
 
 _lib = None
@@ -84,6 +84,7 @@ def load_library():
         "wolff_get_info": (i, [v, P(_Info)]),
         "wolff_set_local_thresholds": (i, [v, u32, u32]),
         "wolff_get_stats": (i, [v, P(_Stats)]),
+        "wolff_set_burst": (i, [v, i]),
         "wolff_batch_create": (i, [P(v), i, v]),
         "wolff_batch_run": (i, [v, v, i, v, v, i, i]),
         "wolff_batch_free": (i, [v]),
@@ -237,6 +238,9 @@ class WolffLattice:
         inf = _Info()
         _check(load_library().wolff_get_info(self.handle, ctypes.byref(inf)), self.handle)
         return {k: getattr(inf, k) for k, _ in _Info._fields_}
+
+    def set_burst(self, enable):
+        _check(load_library().wolff_set_burst(self.handle, 1 if enable else 0), self.handle)
 
     def stats(self):
         st = _Stats()

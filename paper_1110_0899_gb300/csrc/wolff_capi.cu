@@ -50,6 +50,7 @@ struct wolff_ctx {
     unsigned long long wait_ns = 2000000000ull;
     uint32_t t_up = 128, t_down = 64;
     bool thresholds_set = false;
+    bool burst = true;
     int cluster = 8;
     int max_cluster = 8;
     std::string err;
@@ -102,6 +103,7 @@ StepParams make_params(const wolff_ctx *c) {
     p.wait_ns = c->wait_ns;
     p.t_up = c->t_up;
     p.t_down = c->t_down;
+    p.burst = c->burst ? 1u : 0u;
     return p;
 }
 
@@ -236,7 +238,7 @@ wolff_status ising_init(wolff_ctx **out, int dim, int L, double J, double T, uin
     c->spins = reinterpret_cast<uint8_t *>(base + 2 * sizeof(DevCtl));
     c->list = reinterpret_cast<uint32_t *>(base + 2 * sizeof(DevCtl) + round_up(c->N, kAlign));
     c->blocks = default_blocks(c);
-    c->threads = 256;
+    c->threads = 512;
     c->max_cluster = max_cluster_size(dim, c->threads);
     c->cluster = c->max_cluster;
 
@@ -300,6 +302,12 @@ wolff_status wolff_set_local_thresholds(wolff_ctx *c, uint32_t t_up, uint32_t t_
     c->t_up = t_up;
     c->t_down = t_down;
     c->thresholds_set = true;
+    return WOLFF_OK;
+}
+
+wolff_status wolff_set_burst(wolff_ctx *c, int enable) {
+    if (!c) return WOLFF_EINVAL;
+    c->burst = enable != 0;
     return WOLFF_OK;
 }
 
@@ -472,6 +480,8 @@ wolff_status wolff_get_stats(wolff_ctx *c, wolff_stats *st) {
     st->grid_finishes = h.st_grid_finishes;
     st->start_ns = h.st_start_ns;
     st->end_ns = h.st_end_ns;
+    st->burst_updates = h.st_burst_updates;
+    st->bursts = h.st_bursts;
     return WOLFF_OK;
 }
 

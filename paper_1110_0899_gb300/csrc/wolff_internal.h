@@ -77,6 +77,8 @@ struct alignas(256) DevCtl {
     unsigned long long st_ns_local, st_ns_grid, st_ns_finish;
     unsigned long long st_handoffs, st_grid_finishes;
     unsigned long long st_start_ns, st_end_ns;   // globaltimer at the last launch's start/end
+    unsigned long long st_burst_updates;         // updates committed by burst mode
+    unsigned long long st_bursts;                // bursts attempted
 };
 static_assert(sizeof(DevCtl) % 256 == 0 && sizeof(DevCtl) <= 1024, "control block layout");
 
@@ -99,6 +101,7 @@ struct StepParams {
     unsigned long long wait_ns; // bound of every device-side wait
     uint32_t t_up;              // leader hands a frontier larger than this to the grid
     uint32_t t_down;            // grid hands a frontier this small back to the leader
+    uint32_t burst;             // cluster schedule: speculative bursts of small updates
 };
 
 // Leader-local frontier capacity (shared memory) and the cluster-list prefix

@@ -196,6 +196,8 @@ __global__ void k_reset_ctl(DevCtl *ctl, unsigned long long t) {
     ctl->st_ns_local = ctl->st_ns_grid = ctl->st_ns_finish = 0;
     ctl->st_handoffs = ctl->st_grid_finishes = 0;
     ctl->st_start_ns = ctl->st_end_ns = 0;
+    ctl->st_burst_updates = 0;
+    ctl->st_bursts = 0;
 }
 
 // Before every persistent launch: command sequence, barrier word and

@@ -31,7 +31,23 @@ namespace wolff {
 
 namespace {
 
-enum : unsigned int { kTeamLevels = 1, kTeamFinish = 2, kTeamExit = 3 };
+enum : unsigned int { kTeamLevels = 1, kTeamFinish = 2, kTeamExit = 3, kTeamBurst = 4 };
+
+// ---- burst mode --------------------------------------------------------------
+// While clusters are small, consecutive updates rarely touch the same sites.
+// The leader then grows up to one update per warp at once, all on the same
+// lattice, without claiming anything (each warp keeps its cluster in a
+// shared-memory hash set), and afterwards commits, in order, the longest
+// prefix whose updates read no site that an earlier update of the prefix
+// flips.  Update t+j reads its members and their neighbours; if none of them
+// was flipped by updates t..t+j-1, it sees exactly the lattice the serial
+// chain would show it, so every committed update is the serial one -- the
+// same component, level count, boundary sum and record.  The first update that
+// conflicts, or whose cluster outgrows kBurstCap, is left for the ordinary path.
+constexpr int kBurstMaxWarps = 16;
+constexpr uint32_t kBurstCap = 64;          // members per speculative update (128 at <= 8 warps)
+constexpr uint32_t kBurstMapSlots = 2048;   // flipped-site map of the whole burst
+constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;
 
 struct TeamShared {
     uint32_t front[2][kLocalFrontierCap];
@@ -40,6 +56,10 @@ struct TeamShared {
     unsigned int sig0bit;
     unsigned int cmd[8];        // kind, lo, hi, level, sig0bit, t_lo, t_hi
     unsigned long long dE;      // team boundary sum (leader's copy)
+    // burst mode (leader only): per-warp results and the commit cut
+    int bres[kBurstMaxWarps][4];  // |C| (or -1 when too big), levels, dE_bond, sig0bit
+    unsigned int bcut;
+    unsigned int bflag;
 };
 
 // All CTAs of the team: expand level after level from list[lo, hi) until the
@@ -122,6 +142,12 @@ __device__ __forceinline__ long long team_finish(const StepParams &p, TeamShared
 }
 
 template <int DIM>
+__device__ uint32_t team_burst(const StepParams &p, TeamShared &sh, cg::cluster_group &cl,
+                               unsigned long long u0, uint32_t nb, long long &E, long long &M,
+                               unsigned long long &total_C, uint32_t &last_C,
+                               uint32_t &last_levels);
+
+template <int DIM>
 __device__ void team_worker(const StepParams &p, TeamShared &sh, cg::cluster_group &cl) {
     TeamShared *lead = cl.map_shared_rank(&sh, 0);
     while (true) {
@@ -135,6 +161,12 @@ __device__ void team_worker(const StepParams &p, TeamShared &sh, cg::cluster_gro
             team_levels<DIM>(p, sh, cl, lo, hi, level, sig0bit, tlo, thi, &finished);
         } else if (kind == kTeamFinish) {
             team_finish<DIM>(p, sh, cl, hi, sig0bit);
+        } else if (kind == kTeamBurst) {
+            long long E = 0, M = 0;
+            unsigned long long tc = 0;
+            uint32_t lc = 0, ll = 0;
+            team_burst<DIM>(p, sh, cl, ((unsigned long long)hi << 32) | lo, level, E, M, tc, lc,
+                            ll);
         } else {
             // the leader's shared memory (read above) must outlive every
             // remote access: leave together, after one more cluster barrier
@@ -142,6 +174,289 @@ __device__ void team_worker(const StepParams &p, TeamShared &sh, cg::cluster_gro
             return;
         }
     }
+}
+
+
+__device__ __forceinline__ uint32_t burst_hash(uint32_t key, uint32_t slots) {
+    return (key * 0x9E3779B1u) >> (32 - __ffs(slots) + 1);
+}
+
+// Inserts key into an open-addressing set of `slots` entries (power of two).
+// Returns 1 if newly inserted, 0 if present, -1 if the set is full.
+__device__ __forceinline__ int burst_insert(uint32_t *set, uint32_t slots, uint32_t key) {
+    uint32_t h = burst_hash(key, slots);
+    for (uint32_t probe = 0; probe < slots; ++probe) {
+        const uint32_t prev = atomicCAS(set + h, kEmptyKey, key);
+        if (prev == kEmptyKey) return 1;
+        if (prev == key) return 0;
+        h = (h + 1) & (slots - 1);
+    }
+    return -1;
+}
+
+__device__ __forceinline__ bool burst_contains(const uint32_t *set, uint32_t slots, uint32_t key) {
+    uint32_t h = burst_hash(key, slots);
+    for (uint32_t probe = 0; probe < slots; ++probe) {
+        const uint32_t v = set[h];
+        if (v == key) return true;
+        if (v == kEmptyKey) return false;
+        h = (h + 1) & (slots - 1);
+    }
+    return false;
+}
+
+// Owner CTA of a site in the team's distributed flipped-site map.
+__device__ __forceinline__ uint32_t burst_owner(uint32_t site, uint32_t cs) {
+    return ((site * 0x85EBCA6Bu) >> 16) & (cs - 1u);
+}
+
+// All CTAs of the team: grow, check and commit up to nb consecutive updates
+// starting at p.t0 + u0, update u0 + g on warp g % W of CTA g / W (W warps per
+// CTA).  The map "lowest update index that flips a site" is spread over the
+// CTAs' shared memory (each site has an owner CTA) and reached through
+// distributed shared memory; cluster barriers separate growth, insertion,
+// checking and commit.  Returns how many updates were committed (0 when the
+// first one is too big); the leader's thread 0 advances the chain state and
+// writes their records.
+template <int DIM>
+__device__ uint32_t team_burst(const StepParams &p, TeamShared &sh, cg::cluster_group &cl,
+                               unsigned long long u0, uint32_t nb, long long &E, long long &M,
+                               unsigned long long &total_C, uint32_t &last_C,
+                               uint32_t &last_levels) {
+    const uint32_t W = min((uint32_t)(blockDim.x >> 5), (uint32_t)kBurstMaxWarps);
+    const uint32_t rank = cl.block_rank(), cs = cl.num_blocks();
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t g = rank * W + warp;
+    const bool active = warp < W && g < nb;
+    TeamShared *lead = cl.map_shared_rank(&sh, 0);
+    uint32_t *raw = &sh.front[0][0];                 // 8192 words, free outside growth
+    uint32_t *map_key = raw;                         // kBurstMapSlots
+    uint32_t *map_val = raw + kBurstMapSlots;        // kBurstMapSlots
+    // a CTA with 8 warps or fewer gives each of them room for 128 members
+    const uint32_t cap = W <= 8 ? 2 * kBurstCap : kBurstCap, hslots = 2 * cap;
+    uint32_t *mine = raw + 2 * kBurstMapSlots + (warp % kBurstMaxWarps) * (cap + hslots);
+    uint32_t *members = mine, *hset = mine + cap;
+    for (uint32_t k = threadIdx.x; k < kBurstMapSlots; k += blockDim.x) {
+        map_key[k] = kEmptyKey;
+        map_val[k] = 0xFFFFFFFFu;
+    }
+    bool too_big = false;
+    uint32_t n = 0;
+    // ---- grow
+    if (active) {
+        for (uint32_t k = lane; k < hslots; k += 32) hset[k] = kEmptyKey;
+        __syncwarp();
+        const unsigned long long t = p.t0 + u0 + g;
+        const uint32_t tlo = (uint32_t)t, thi = (uint32_t)(t >> 32);
+        const uint32_t i0 = seed_site(p, t);
+        const uint32_t sig0bit = __ldcg(p.spins + i0) & 1u;
+        if (lane == 0) {
+            burst_insert(hset, hslots, i0);
+            members[0] = pack_index<DIM>(p.g, i0);
+        }
+        __syncwarp();
+        n = 1;
+        uint32_t lo = 0, levels = 0;
+        while (lo < n && !too_big) {
+            const uint32_t hi = n;
+            for (uint32_t b = lo; b < hi; b += 32) {
+                const uint32_t k = b + lane;
+                Neighbours<DIM> nb2;
+                uint32_t fresh = 0;
+                bool full = false;
+                if (k < hi) {
+                    uint32_t i;
+                    neighbours<DIM>(p.g, members[k], &i, nb2);
+                    uint8_t v[2 * DIM];
+#pragma unroll
+                    for (int s = 0; s < 2 * DIM; ++s) v[s] = __ldcg(p.spins + nb2.idx[s]);
+                    uint32_t owners[DIM + 1];
+                    owners[0] = i;
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) owners[d + 1] = nb2.idx[2 * d + 1];
+                    Philox4 draw[DIM + 1];
+                    philox4x32_10_lanes<DIM + 1>(owners, tlo, thi, kTagBond, p.key0, p.key1, draw);
+#pragma unroll
+                    for (int s = 0; s < 2 * DIM; ++s) {
+                        const int d = s >> 1;
+                        const uint32_t r = (s & 1) ? draw[d + 1].v[d] : draw[0].v[d];
+                        if ((uint32_t)(v[s] & 1u) == sig0bit && (unsigned long long)r < p.thr) {
+                            const int ins = burst_insert(hset, hslots, nb2.idx[s]);
+                            if (ins > 0) fresh |= 1u << s;
+                            if (ins < 0) full = true;
+                        }
+                    }
+                }
+                const uint32_t cnt = __popc(fresh);
+                uint32_t incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(kFullMask, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const uint32_t total = __shfl_sync(kFullMask, incl, 31);
+                uint32_t pos = n + incl - cnt;
+#pragma unroll
+                for (int s = 0; s < 2 * DIM; ++s) {
+                    if (fresh & (1u << s)) {
+                        if (pos < cap) members[pos] = nb2.packed[s];
+                        ++pos;
+                    }
+                }
+                n += total;
+                if (__any_sync(kFullMask, full) || n > cap) too_big = true;
+            }
+            __syncwarp();
+            ++levels;
+            lo = hi;
+        }
+        int dE = 0;
+        if (!too_big) {
+            for (uint32_t k = lane; k < n; k += 32) {
+                uint32_t i;
+                Neighbours<DIM> nb2;
+                neighbours<DIM>(p.g, members[k], &i, nb2);
+#pragma unroll
+                for (int s = 0; s < 2 * DIM; ++s) {
+                    if (burst_contains(hset, hslots, nb2.idx[s])) continue;
+                    const uint32_t cur = __ldcg(p.spins + nb2.idx[s]) & 1u;
+                    dE += (cur == sig0bit) ? -1 : 1;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dE += __shfl_down_sync(kFullMask, dE, o);
+        }
+        if (lane == 0) {
+            sh.bres[warp][0] = too_big ? -1 : (int)n;
+            sh.bres[warp][1] = (int)levels;
+            sh.bres[warp][2] = dE;
+            sh.bres[warp][3] = (int)sig0bit;
+            if (too_big) atomicMin(&lead->bcut, g);
+        }
+    }
+    cl.sync();   // every CTA has grown its updates and cleared its part of the map
+    // ---- the lowest update index that flips each site, in the owner CTA's map
+    if (active && !too_big) {
+        bool lost = false;
+        for (uint32_t k = lane; k < n; k += 32) {
+            uint32_t c[DIM];
+            unpack<DIM>(members[k], c);
+            const uint32_t site = site_index<DIM>(p.g, c);
+            uint32_t *rraw = cl.map_shared_rank(raw, burst_owner(site, cs));
+            uint32_t h = burst_hash(site * 0x9E3779B1u + 0x7F4A7C15u, kBurstMapSlots);
+            bool placed = false;
+            for (uint32_t probe = 0; probe < kBurstMapSlots; ++probe) {
+                const uint32_t prev = atomicCAS(rraw + h, kEmptyKey, site);
+                if (prev == kEmptyKey || prev == site) {
+                    atomicMin(rraw + kBurstMapSlots + h, g);
+                    placed = true;
+                    break;
+                }
+                h = (h + 1) & (kBurstMapSlots - 1);
+            }
+            if (!placed) lost = true;
+        }
+        // a map too full to record a flip makes the update unsafe to commit
+        if (__any_sync(kFullMask, lost) && lane == 0) atomicMin(&lead->bcut, g);
+    }
+    cl.sync();
+    // ---- update g conflicts if it read a site flipped by an earlier update
+    if (active && !too_big) {
+        bool conflict = false;
+        for (uint32_t k = lane; k < n && !conflict; k += 32) {
+            uint32_t i;
+            Neighbours<DIM> nb2;
+            neighbours<DIM>(p.g, members[k], &i, nb2);
+            uint32_t probe_sites[2 * DIM + 1];
+            probe_sites[0] = i;
+#pragma unroll
+            for (int s = 0; s < 2 * DIM; ++s) probe_sites[s + 1] = nb2.idx[s];
+#pragma unroll
+            for (int q = 0; q < 2 * DIM + 1; ++q) {
+                const uint32_t site = probe_sites[q];
+                const uint32_t *rraw = cl.map_shared_rank(raw, burst_owner(site, cs));
+                uint32_t h = burst_hash(site * 0x9E3779B1u + 0x7F4A7C15u, kBurstMapSlots);
+                for (uint32_t probe = 0; probe < kBurstMapSlots; ++probe) {
+                    const uint32_t key = rraw[h];
+                    if (key == site) {
+                        if (rraw[kBurstMapSlots + h] < g) conflict = true;
+                        break;
+                    }
+                    if (key == kEmptyKey) break;
+                    h = (h + 1) & (kBurstMapSlots - 1);
+                }
+            }
+        }
+        if (__any_sync(kFullMask, conflict) && lane == 0) atomicMin(&lead->bcut, g);
+    }
+    cl.sync();
+    const uint32_t cut = *reinterpret_cast<volatile unsigned int *>(&lead->bcut);
+    // ---- commit updates [0, cut): flip their members (both bits)
+    if (active && g < cut) {
+        const uint8_t v = sh.bres[warp][3] ? 0x00 : 0x03;
+        for (uint32_t k = lane; k < n; k += 32) {
+            uint32_t c[DIM];
+            unpack<DIM>(members[k], c);
+            p.spins[site_index<DIM>(p.g, c)] = v;
+        }
+    }
+    if (rank == 0 && cut > 0) {
+        // records of the committed updates in parallel: a scan of the energy
+        // and magnetisation steps over the leader CTA
+        __shared__ long long s_e[512], s_m[512];
+        __shared__ unsigned long long s_c[512];
+        __shared__ long long s_base[2];
+        const uint32_t j = threadIdx.x;
+        int res[4] = {0, 0, 0, 0};
+        if (j < cut) {
+            const TeamShared *src = cl.map_shared_rank(&sh, j / W);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) res[q] = src->bres[j % W][q];
+        }
+        s_e[j] = j < cut ? 2LL * res[2] : 0;
+        s_m[j] = j < cut ? (res[3] ? -2LL : 2LL) * res[0] : 0;
+        s_c[j] = j < cut ? (unsigned long long)res[0] : 0;
+        if (j == 0) {
+            s_base[0] = E;
+            s_base[1] = M;
+        }
+        __syncthreads();
+        for (uint32_t off = 1; off < cut; off <<= 1) {
+            const long long ve = j >= off ? s_e[j - off] : 0;
+            const long long vm = j >= off ? s_m[j - off] : 0;
+            const unsigned long long vc = j >= off ? s_c[j - off] : 0;
+            __syncthreads();
+            s_e[j] += ve;
+            s_m[j] += vm;
+            s_c[j] += vc;
+            __syncthreads();
+        }
+        if (j < cut && p.records) {
+            wolff_record r;
+            r.C = (uint32_t)res[0];
+            r.levels = (uint32_t)res[1];
+            r.E_bond = s_base[0] + s_e[j];
+            r.M = s_base[1] + s_m[j];
+            p.records[u0 + j] = r;
+        }
+        if (j == cut - 1) {
+            s_base[0] += s_e[j];
+            s_base[1] += s_m[j];
+            s_c[511] = s_c[j];
+            s_e[511] = res[0];
+            s_m[511] = res[1];
+        }
+        __syncthreads();
+        if (j == 0) {
+            E = s_base[0];
+            M = s_base[1];
+            total_C += s_c[511];
+            last_C = (uint32_t)s_e[511];
+            last_levels = (uint32_t)s_m[511];
+        }
+    }
+    cl.sync();   // results read and commits done before anything is reused
+    return cut;
 }
 
 // Leader: announce a team phase, then start it with the cluster barrier.
@@ -182,7 +497,52 @@ __device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_gro
         last_levels = ctl->last_levels;
         sh.dE = 0;
     }
+    // burst policy (thread 0 decides, the CTA follows): bursts run while the
+    // recent clusters are small; a cluster too big for a burst pauses them
+    unsigned int cooldown = 0, fail_streak = 0, skip_next = 0;
+    unsigned long long bursts_done = 0, burst_calls = 0;
     for (unsigned long long u = 0; u < p.n; ++u) {
+        if (p.burst && p.n - u >= 2) {
+            // a burst cut short by an update too big for it leaves that update
+            // to the ordinary path directly
+            if (t0) sh.bflag = (cooldown == 0 && !skip_next) ? 1u : 0u;
+            __syncthreads();
+            if (sh.bflag) {
+                const uint32_t W = min((uint32_t)(blockDim.x >> 5), (uint32_t)kBurstMaxWarps);
+                const uint32_t nb =
+                    (uint32_t)min((unsigned long long)(W * cl.num_blocks()), p.n - u);
+                if (t0) sh.bcut = nb;
+                if (has_team)
+                    announce(sh, cl, kTeamBurst, (uint32_t)u, (uint32_t)(u >> 32), nb, 0, 0);
+                else
+                    __syncthreads();
+                const uint32_t c = team_burst<DIM>(p, sh, cl, u, nb, E, M, total_C, last_C,
+                                                   last_levels);
+                if (t0) {
+                    bursts_done += c;
+                    ++burst_calls;
+                    if (c > 0 && c < nb) {
+                        const TeamShared *src = cl.map_shared_rank(&sh, c / W);
+                        skip_next = src->bres[c % W][0] < 0 ? 1u : 0u;
+                    }
+                    // back off only while bursts keep failing at their first
+                    // update (the large-cluster regime): 0, 1, 3, ..., 63
+                    if (c == 0) {
+                        fail_streak = min(fail_streak + 1u, 7u);
+                        cooldown = (1u << (fail_streak - 1u)) - 1u;
+                    } else {
+                        fail_streak = 0;
+                    }
+                }
+                if (c > 0) {
+                    u += c - 1;
+                    continue;
+                }
+            } else if (t0) {
+                if (skip_next) skip_next = 0;
+                else --cooldown;
+            }
+        }
         const unsigned long long t = p.t0 + u;
         const uint32_t tlo = (uint32_t)t, thi = (uint32_t)(t >> 32);
         unsigned long long clk = 0;
@@ -326,6 +686,8 @@ __device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_gro
         ctl->st_ns_finish += ns_finish;
         ctl->st_handoffs += handoffs;
         ctl->st_grid_finishes += team_fin;
+        ctl->st_burst_updates += bursts_done;
+        ctl->st_bursts += burst_calls;
         ctl->st_end_ns = global_ns();
     }
     if (has_team) {

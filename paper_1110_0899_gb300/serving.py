@@ -80,6 +80,9 @@ class WolffServer:
             q = self.first_quota
         else:
             q = int(self.epoch_seconds * 1e9 / max(r.ns_per_update, 1.0))
+            # grow at most 4x per epoch: a young lattice's updates get dearer
+            # as it orders, faster than one epoch's estimate can follow
+            q = min(q, 4 * max(r.quota, 1))
         return max(1, min(q, self.epoch_updates, r.remaining))
 
     def _epoch(self, active):

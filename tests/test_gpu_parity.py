@@ -285,3 +285,28 @@ def test_batched_replicas_match_each_alone():
         assert t == total and np.array_equal(spins, s_ref)
         lat.close()
     batch.close()
+
+
+@pytest.mark.parametrize("dim,L,T,n", [(2, 200, 5.0, 600), (2, 64, TC2, 600), (3, 16, 8.0, 600),
+                                       (2, 4096, TC2, 300), (2, 12, 3.0, 400), (3, 5, 6.0, 400)])
+def test_burst_mode_matches_oracle(dim, L, T, n):
+    """Speculative bursts (many small updates grown at once, committed in
+    order while they do not interact) give the serial chain exactly, on
+    lattices where they mostly commit (high T, large L) and where conflicts
+    and oversized clusters cut them short (small L, T_c)."""
+    torch, w = require_cuda()
+    seed = 123 + L
+    ref, s_ref = oracle_trajectory(dim, L, T, seed, n)
+    for threads in (256, 512):
+        lat = w.WolffLattice(dim, L, T, seed=seed, schedule=w.SCHED_CLUSTER, grid_blocks=4,
+                             block_threads=threads)
+        lat.set_burst(True)
+        rec = lat.step(n)
+        st = lat.stats()
+        spins, _ = lat.get_state()
+        assert lat.measure()[:2] == lat.measure_full()
+        lat.close()
+        assert_records_equal(rec, ref, "burst %dD L=%d T=%g threads %d" % (dim, L, T, threads))
+        assert np.array_equal(spins, s_ref)
+        if T > 4.0 and L ** dim > 1000:
+            assert st["burst_updates"] > n // 2

@@ -279,6 +279,16 @@ wolff_status wolff_batch_run(wolff_batch *b, wolff_ctx *const *ctxs, int n,
                              const uint64_t *n_updates, void *const *d_records,
                              int cluster_size, int block_threads);
 
+/* As wolff_batch_run, but every lattice stops at the first update boundary
+ * after budget_ns nanoseconds of device time from the start of its work
+ * (0 = no limit), so a lattice whose updates suddenly get dearer cannot hold
+ * a batch for long.  How many updates each lattice ran is known after the
+ * next synchronising call on its context (wolff_get_stats().updates,
+ * wolff_get_info().t); its records fill a prefix of d_records[i]. */
+wolff_status wolff_batch_run_timed(wolff_batch *b, wolff_ctx *const *ctxs, int n,
+                                   const uint64_t *n_updates, void *const *d_records,
+                                   int cluster_size, int block_threads, uint64_t budget_ns);
+
 wolff_status wolff_batch_free(wolff_batch *b);
 
 /* Releases the context (and the workspace if the library allocated it).

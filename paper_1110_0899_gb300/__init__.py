@@ -87,6 +87,7 @@ def load_library():
         "wolff_set_burst": (i, [v, i]),
         "wolff_batch_create": (i, [P(v), i, v]),
         "wolff_batch_run": (i, [v, v, i, v, v, i, i]),
+        "wolff_batch_run_timed": (i, [v, v, i, v, v, i, i, u64]),
         "wolff_batch_free": (i, [v]),
         "wolff_step_static": (i, [i, i, d, d, u64, u64, u64, v, v, v]),
         "wolff_bond_threshold": (u64, [d, d]),
@@ -309,9 +310,12 @@ class WolffBatch:
                                                  _stream_handle(stream)))
         self.capacity = int(capacity)
 
-    def run(self, lattices, n_updates, records=None, cluster_size=1, block_threads=256):
+    def run(self, lattices, n_updates, records=None, cluster_size=1, block_threads=256,
+            budget_ns=0):
         """lattices: list of WolffLattice; n_updates: int or per-lattice list;
-        records: None or a list of device uint8 tensors (or None entries)."""
+        records: None or a list of device uint8 tensors (or None entries);
+        budget_ns: device-time limit per lattice (0 = none; the updates done
+        are then read back through each lattice's stats()["updates"])."""
         n = len(lattices)
         if isinstance(n_updates, int):
             n_updates = [n_updates] * n
@@ -320,8 +324,9 @@ class WolffBatch:
         recs = None
         if records is not None:
             recs = (ctypes.c_void_p * n)(*[None if r is None else r.data_ptr() for r in records])
-        _check(load_library().wolff_batch_run(self.handle, ctxs, n, nu, recs, int(cluster_size),
-                                              int(block_threads)))
+        _check(load_library().wolff_batch_run_timed(self.handle, ctxs, n, nu, recs,
+                                                    int(cluster_size), int(block_threads),
+                                                    int(budget_ns)))
 
     def close(self):
         if self.handle is not None and self.handle.value:

@@ -104,6 +104,7 @@ StepParams make_params(const wolff_ctx *c) {
     p.t_up = c->t_up;
     p.t_down = c->t_down;
     p.burst = c->burst ? 1u : 0u;
+    p.budget_ns = 0;
     return p;
 }
 
@@ -114,6 +115,7 @@ wolff_status sync_and_check(wolff_ctx *c, DevCtl *host_copy) {
     cudaError_t e = cudaMemcpyAsync(dst, c->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "synchronise");
+    c->t_host = dst->t;   // the device's count (a time-budgeted run may stop early)
     if (dst->status != 0) {
         char buf[160];
         snprintf(buf, sizeof buf, "device reported %s (detail %u)",
@@ -539,6 +541,12 @@ wolff_status wolff_batch_create(wolff_batch **out, int capacity, void *stream) {
 wolff_status wolff_batch_run(wolff_batch *b, wolff_ctx *const *ctxs, int n,
                              const uint64_t *n_updates, void *const *d_records, int cluster_size,
                              int block_threads) {
+    return wolff_batch_run_timed(b, ctxs, n, n_updates, d_records, cluster_size, block_threads, 0);
+}
+
+wolff_status wolff_batch_run_timed(wolff_batch *b, wolff_ctx *const *ctxs, int n,
+                                   const uint64_t *n_updates, void *const *d_records,
+                                   int cluster_size, int block_threads, uint64_t budget_ns) {
     if (!b || n < 0 || n > b->capacity || (n && (!ctxs || !n_updates))) return WOLFF_EINVAL;
     if (cluster_size != 1 && cluster_size != 2 && cluster_size != 4 && cluster_size != 8 &&
         cluster_size != 16)
@@ -562,6 +570,7 @@ wolff_status wolff_batch_run(wolff_batch *b, wolff_ctx *const *ctxs, int n,
         StepParams p = make_params(c);
         p.records = d_records ? reinterpret_cast<wolff_record *>(d_records[i]) : nullptr;
         p.n = n_updates[i];
+        p.budget_ns = budget_ns;
         b->h_table[c->dim == 2 ? k2++ : k3++] = p;
     }
     auto by_size = [](const StepParams &a, const StepParams &c) { return a.g.N > c.g.N; };

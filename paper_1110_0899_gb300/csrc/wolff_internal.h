@@ -102,6 +102,7 @@ struct StepParams {
     uint32_t t_up;              // leader hands a frontier larger than this to the grid
     uint32_t t_down;            // grid hands a frontier this small back to the leader
     uint32_t burst;             // cluster schedule: speculative bursts of small updates
+    unsigned long long budget_ns;   // cluster schedule: stop after this much device time (0 = none)
 };
 
 // Leader-local frontier capacity (shared memory) and the cluster-list prefix

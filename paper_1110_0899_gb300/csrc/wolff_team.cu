@@ -60,6 +60,7 @@ struct TeamShared {
     int bres[kBurstMaxWarps][4];  // |C| (or -1 when too big), levels, dE_bond, sig0bit
     unsigned int bcut;
     unsigned int bflag;
+    unsigned int bstop;
 };
 
 // All CTAs of the team: expand level after level from list[lo, hi) until the
@@ -501,7 +502,14 @@ __device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_gro
     // recent clusters are small; a cluster too big for a burst pauses them
     unsigned int cooldown = 0, fail_streak = 0, skip_next = 0;
     unsigned long long bursts_done = 0, burst_calls = 0;
-    for (unsigned long long u = 0; u < p.n; ++u) {
+    const unsigned long long launch_t0 = global_ns();
+    unsigned long long u = 0;
+    for (; u < p.n; ++u) {
+        if (p.budget_ns && u > 0) {   // a time-budgeted job stops at an update boundary
+            if (t0) sh.bstop = (global_ns() - launch_t0 > p.budget_ns) ? 1u : 0u;
+            __syncthreads();
+            if (sh.bstop) break;
+        }
         if (p.burst && p.n - u >= 2) {
             // a burst cut short by an update too big for it leaves that update
             // to the ordinary path directly
@@ -677,8 +685,8 @@ __device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_gro
         ctl->total_C = total_C;
         ctl->last_C = last_C;
         ctl->last_levels = last_levels;
-        ctl->t = p.t0 + p.n;
-        ctl->st_updates += p.n;
+        ctl->t = p.t0 + u;
+        ctl->st_updates += u;
         ctl->st_levels_local += st_local;
         ctl->st_levels_grid += st_team;
         ctl->st_ns_local += ns_local;

@@ -5,9 +5,11 @@ back its per-update records (|C|, levels, E_bond, M) and final E, M.  The
 server keeps every admitted lattice resident on the device and works in
 epochs: at each epoch boundary it admits the requests that have arrived, as
 long as their memory (workspace + record buffer) fits the budget, then runs
-up to `epoch_updates` updates of every active request in shared batched
-launches (one thread-block cluster per lattice; large lattices get larger
-teams on a second stream), and retires the requests that are done.
+updates of every active request in shared batched launches (one
+thread-block cluster per lattice; large lattices get larger teams on a second
+stream) -- each request's share sized from its measured cost per update and
+capped on the device by a time budget -- and retires the requests that are
+done.
 Requests that arrive while others are on the GPU therefore join at the next
 epoch and their work overlaps on the device.  A request's chain does not
 depend on what it shares the GPU with: its records equal those of the same
@@ -23,7 +25,7 @@ from . import RECORD_BYTES, WolffBatch, WolffLattice, records_to_numpy, wolff_wo
 
 class Request:
     __slots__ = ("spec", "lattice", "records", "done", "admitted_s", "finished_s", "result",
-                 "ns_per_update", "quota")
+                 "ns_per_update", "quota", "updates_seen")
 
     def __init__(self, spec):
         self.spec = spec
@@ -35,6 +37,7 @@ class Request:
         self.result = None
         self.ns_per_update = None
         self.quota = 0
+        self.updates_seen = 0
 
     @property
     def remaining(self):
@@ -99,17 +102,23 @@ class WolffServer:
             for r in g:
                 r.quota = self._quota(r)
             recs = [r.records[r.done * RECORD_BYTES:] for r in g]
+            # the device stops each lattice at the first update boundary past
+            # twice the epoch target, whatever its quota said
             b.run([r.lattice for r in g], [r.quota for r in g], recs, cluster_size=cs,
-                  block_threads=th)
+                  block_threads=th, budget_ns=int(2 * self.epoch_seconds * 1e9))
         for st in self.streams:
             cur.wait_stream(st)
         torch.cuda.synchronize()
         for r in active:
             st = r.lattice.stats()
+            ran = st["updates"] - r.updates_seen
+            r.updates_seen = st["updates"]
             dt = max(1, st["end_ns"] - st["start_ns"])
-            per = dt / r.quota
-            r.ns_per_update = per if r.ns_per_update is None else 0.5 * (r.ns_per_update + per)
-            r.done += r.quota
+            if ran > 0:
+                per = dt / ran
+                r.ns_per_update = per if r.ns_per_update is None else 0.5 * (r.ns_per_update + per)
+            r.quota = max(ran, 1)
+            r.done += ran
 
     def _retire(self, req, now):
         E, M, C = req.lattice.measure()

@@ -95,3 +95,34 @@ def test_served_requests_equal_their_runs_alone():
         if k < 3:
             orc, _ = oracle_trajectory(s["dim"], s["L"], s["T"], s["seed"], s["n_updates"])
             assert_records_equal(r.result["records"], orc, "request %d vs oracle" % s["id"])
+
+
+def test_time_budget_stops_at_update_boundaries():
+    """A batch with a device-time budget runs a prefix of each lattice's
+    updates; the chain continues exactly where it stopped."""
+    torch, w = require_cuda()
+    specs = [(2, 96, 2.0, 5), (3, 12, 4.0, 6), (2, 40, 2.3, 7)]
+    lats = [w.WolffLattice(d, L, T, seed=s) for d, L, T, s in specs]
+    for lat in lats:
+        lat.set_state(np.ones(lat.N, np.int8), 0)   # ordered: large clusters, slow updates
+    batch = w.WolffBatch(len(lats))
+    got = [[] for _ in lats]
+    seen = [0] * len(lats)
+    for call in range(6):
+        bufs = [lat.record_buffer(400) for lat in lats]
+        batch.run(lats, 400, bufs, cluster_size=2, block_threads=256, budget_ns=30_000)
+        torch.cuda.synchronize()
+        for k, lat in enumerate(lats):
+            ran = lat.stats()["updates"] - seen[k]
+            seen[k] += ran
+            assert 1 <= ran <= 400
+            got[k].append(w.records_to_numpy(bufs[k], ran))
+    assert any(sum(len(x) for x in g) < 6 * 400 for g in got)   # the budget did stop some
+    for k, (dim, L, T, seed) in enumerate(specs):
+        rec = np.concatenate(got[k])
+        ref, s_ref = oracle_trajectory(dim, L, T, seed, len(rec), s=np.ones(L ** dim, np.int8))
+        assert_records_equal(rec, ref, "budgeted lattice %d" % k)
+        spins, t = lats[k].get_state()
+        assert t == len(rec) and np.array_equal(spins, s_ref)
+        lats[k].close()
+    batch.close()

@@ -75,7 +75,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS) + ["batched", "served"])
+    ap.add_argument("--workload", default="2d",
+                    choices=sorted(WORKLOADS) + ["batched", "served", "binder"])
     ap.add_argument("--updates-per-step", type=int, default=1000)
     ap.add_argument("--equil", type=int, default=None)
     ap.add_argument("--schedule", default="auto",
@@ -318,6 +319,32 @@ def run_served(args, n_requests=200, embed=False):
                       "config": {"workload": summary["workload"]}, "served": summary}), flush=True)
 
 
+def run_binder(args):
+    """Temperature sweep of the Binder ratio on the batched form (section 5,
+    Fig. 2 of the paper): 2D L in {64, 128, 256} with 5000 discarded and 50000
+    measured updates per point, 3D L in {16, 32} with 10000 + 100000."""
+    import time as _time
+
+    import torch
+
+    from paper_1110_0899_gb300 import binder, workloads
+    torch.cuda.set_device(0)
+    out = {}
+    for dim, Ls, tc, disc, meas in ((2, [64, 128, 256], workloads.TC_2D, 5000, 50_000),
+                                    (3, [16, 32], workloads.TC_3D, 10_000, 100_000)):
+        Ts = [tc * f for f in (0.97, 0.98, 0.99, 1.0, 1.01, 1.02, 1.03)]
+        t0 = _time.perf_counter()
+        pts = binder.sweep(dim, Ls, Ts, disc, meas, chunk=5000)
+        wall = _time.perf_counter() - t0
+        flips = sum(p["mean_cluster"] * p["updates"] for p in pts)
+        out["%dd" % dim] = {
+            "points": pts, "wall_s": wall, "flips_per_s": flips / wall,
+            "crossings": {"%d-%d" % (a, b): binder.crossing(pts, a, b)
+                          for a, b in zip(Ls, Ls[1:])},
+            "tc": tc}
+    print(json.dumps({"metric": "Binder ratio sweep", "binder": out}), flush=True)
+
+
 def cpu_baseline(dim, L, T, seed, spins, t, seconds):
     """The oracle (single-threaded C) from the GPU's equilibrated lattice, a
     few updates at a time until `seconds` of CPU work have run."""
@@ -346,6 +373,8 @@ def main():
         return run_batched(args)
     if args.workload == "served":
         return run_served(args)
+    if args.workload == "binder":
+        return run_binder(args)
     import numpy as np
     import torch
 
@@ -454,8 +483,8 @@ def main():
     lat.close()
     batched_out = served_out = None
     if world == 1 and args.workload in ("2d", "3d") and not args.no_batched:
-        class _A:   # a short batched comparison beside the headline
-            steps, updates_per_step = 3, 100
+        class _A:   # a batched comparison beside the headline: 2 x 1000 updates per replica
+            steps, updates_per_step = 2, 1000
         batched_out = run_batched(_A, embed=True)
         batched_out.pop("autotune", None)
     if world == 1 and args.workload in ("2d", "3d") and not args.no_served:

@@ -50,6 +50,20 @@ def _load():
     lib.orc_run.restype = i32
     lib.orc_enumerate.argtypes = [i32, u32, p]
     lib.orc_enumerate.restype = i32
+    lib.orc_potts_init.argtypes = [i32, u32, u32, u64, p]
+    lib.orc_potts_init.restype = None
+    lib.orc_potts_energy_bond.argtypes = [i32, u32, p]
+    lib.orc_potts_energy_bond.restype = i64
+    lib.orc_potts_count0.argtypes = [i32, u32, p]
+    lib.orc_potts_count0.restype = i64
+    lib.orc_potts_cluster.argtypes = [i32, u32, u32, u64, u64, u64, p, p, p, p, p]
+    lib.orc_potts_cluster.restype = u32
+    lib.orc_potts_run.argtypes = [i32, u32, u32, u64, u64, u64, u64, p, p]
+    lib.orc_potts_run.restype = i32
+    lib.orc_potts_enumerate.argtypes = [i32, u32, u32, p]
+    lib.orc_potts_enumerate.restype = i32
+    lib.orc_potts_threshold.argtypes = [ctypes.c_double, ctypes.c_double]
+    lib.orc_potts_threshold.restype = u64
     _lib = lib
     return lib
 
@@ -174,3 +188,83 @@ def exact_moments(dim, L, J, T, g=None):
         "M4": float((pm * Mf ** 4).sum()),
         "P": P, "E_values": E, "M_values": M,
     }
+
+
+# ---- q-state Potts (section 6 names it as the straightforward extension) ----
+
+def potts_threshold(J, T):
+    """floor(p * 2^32), p = 1 - exp(-J/T) (Potts bond probability)."""
+    return int(_load().orc_potts_threshold(float(J), float(T)))
+
+
+def potts_init(dim, L, q, seed):
+    c = np.zeros(n_sites(dim, L), dtype=np.int8)
+    _load().orc_potts_init(dim, L, q, seed, _ptr(c))
+    return c
+
+
+def potts_energy_bond(dim, L, c):
+    c = np.ascontiguousarray(c, dtype=np.int8)
+    return int(_load().orc_potts_energy_bond(dim, L, _ptr(c)))
+
+
+def potts_count0(dim, L, c):
+    c = np.ascontiguousarray(c, dtype=np.int8)
+    return int(_load().orc_potts_count0(dim, L, _ptr(c)))
+
+
+def potts_cluster(dim, L, q, thr, seed, t, c):
+    """(member bool array, list, levels, new colour) of Potts update t on c."""
+    c = np.ascontiguousarray(c, dtype=np.int8)
+    n = n_sites(dim, L)
+    member = np.zeros(n, dtype=np.uint8)
+    lst = np.zeros(n, dtype=np.uint32)
+    levels = np.zeros(1, dtype=np.uint32)
+    nc = np.zeros(1, dtype=np.int32)
+    k = _load().orc_potts_cluster(dim, L, q, thr, seed, t, _ptr(c), _ptr(member), _ptr(lst),
+                                  _ptr(levels), _ptr(nc))
+    return member.astype(bool), lst[:k].copy(), int(levels[0]), int(nc[0])
+
+
+def potts_run(dim, L, q, thr, seed, t0, n, c, records=True):
+    """Potts updates t0..t0+n-1 on c (int8 colours, in place); records hold
+    |C|, levels, E_bond (satisfied bonds) and N0 (in the M field)."""
+    if c.dtype != np.int8 or not c.flags.c_contiguous:
+        raise ValueError("c must be a contiguous int8 array")
+    rec = np.zeros(int(n), dtype=RECORD_DTYPE) if records else None
+    rc = _load().orc_potts_run(dim, L, q, thr, seed, t0, n, _ptr(c),
+                               _ptr(rec) if rec is not None else None)
+    if rc != 0:
+        raise MemoryError("oracle could not allocate its scratch arrays (or q < 2)")
+    return rec
+
+
+def potts_density_of_states(dim, L, q):
+    """g(E_bond, N0) over all q^N colourings.  Returns (g, E values, N0 values)."""
+    n = n_sites(dim, L)
+    hist = np.zeros((dim * n + 1) * (n + 1), dtype=np.uint64)
+    if _load().orc_potts_enumerate(dim, L, q, _ptr(hist)) != 0:
+        raise ValueError("too many states to enumerate")
+    return hist.reshape(dim * n + 1, n + 1), np.arange(dim * n + 1), np.arange(n + 1)
+
+
+def potts_exact_moments(dim, L, q, J, T, g=None):
+    """Boltzmann averages <E_bond>, <N0>, <N0^2> from the enumeration."""
+    if g is None:
+        g, E, Z0 = potts_density_of_states(dim, L, q)
+    else:
+        n = n_sites(dim, L)
+        E, Z0 = np.arange(dim * n + 1), np.arange(n + 1)
+    K = float(J) / float(T)
+    gf = g.astype(np.float64)
+    occ = gf > 0
+    logw = np.full(gf.shape, -np.inf)
+    logw[occ] = np.log(gf[occ]) + (K * E[:, None].repeat(gf.shape[1], 1))[occ]
+    logw -= logw[occ].max()
+    w = np.exp(logw)
+    P = w / w.sum()
+    pe, pz = P.sum(axis=1), P.sum(axis=0)
+    Ef, Zf = E.astype(np.float64), Z0.astype(np.float64)
+    return {"E": float((pe * Ef).sum()), "N0": float((pz * Zf).sum()),
+            "N0_2": float((pz * Zf ** 2).sum()), "P": P}
+

@@ -286,3 +286,144 @@ int orc_enumerate(int dim, uint32_t L, uint64_t *hist)
     free(s);
     return 0;
 }
+
+/* ==== q-state Potts model (the extension named in section 6) ==============
+ *
+ * H = -J sum_<ij> delta(c_i, c_j), colours c in {0 .. q-1}.  One Wolff
+ * update t: seed site i0 and a new colour c' != c0, both from the seed draw
+ * (lane 0 -> site, lane 1 -> c' = (c0 + 1 + floor(x1 (q-1) / 2^32)) mod q);
+ * the cluster grows through bonds to neighbours of colour c0 that are active
+ * with probability p = 1 - exp(-J/T) (the same bond words as the Ising
+ * update); every member then takes colour c'.  With q = 2 this is the Ising
+ * update of coupling J/2, colour 1 <-> spin -1.
+ * Observables: the satisfied-bond count E_bond = sum_{i,d} delta(c_i, c_nb)
+ * (energy -J E_bond) and N0, the number of sites of colour 0.
+ * Initial colour of site i: floor(x q / 2^32), x = lane 0 of Philox(i, 0, 0, 2). */
+
+void orc_potts_init(int dim, uint32_t L, uint32_t q, uint64_t seed, int8_t *c)
+{
+    uint32_t n = orc_sites(dim, L);
+    for (uint32_t i = 0; i < n; ++i) {
+        uint32_t r[4];
+        orc_draw(seed, i, 0, ORC_TAG_INIT, r);
+        c[i] = (int8_t)(((uint64_t)r[0] * q) >> 32);
+    }
+}
+
+int64_t orc_potts_energy_bond(int dim, uint32_t L, const int8_t *c)
+{
+    uint32_t n = orc_sites(dim, L);
+    int64_t e = 0;
+    for (uint32_t i = 0; i < n; ++i)
+        for (int d = 0; d < dim; ++d)
+            e += c[i] == c[orc_neighbour(dim, L, i, d, +1)];
+    return e;
+}
+
+int64_t orc_potts_count0(int dim, uint32_t L, const int8_t *c)
+{
+    uint32_t n = orc_sites(dim, L);
+    int64_t k = 0;
+    for (uint32_t i = 0; i < n; ++i) k += c[i] == 0;
+    return k;
+}
+
+/* Cluster of Potts update t on c (c unchanged); member[] zero on entry.
+ * Writes the new colour to *new_colour.  Returns |C|. */
+uint32_t orc_potts_cluster(int dim, uint32_t L, uint32_t q, uint64_t thr, uint64_t seed,
+                           uint64_t t, const int8_t *c, uint8_t *member, uint32_t *list,
+                           uint32_t *levels, int *new_colour)
+{
+    uint32_t n = orc_sites(dim, L);
+    uint32_t r[4];
+    orc_draw(seed, 0, t, ORC_TAG_SEED, r);
+    uint32_t i0 = (uint32_t)(((uint64_t)r[0] * n) >> 32);
+    int c0 = c[i0];
+    *new_colour = (int)((c0 + 1 + (((uint64_t)r[1] * (q - 1)) >> 32)) % q);
+    uint32_t ic = 0, in = 0;
+    list[ic++] = i0;
+    member[i0] = 1;
+    uint32_t generation_end = ic, generations = 1;
+    while (in < ic) {
+        if (in == generation_end) {
+            generation_end = ic;
+            ++generations;
+        }
+        uint32_t i = list[in++];
+        for (int d = 0; d < dim; ++d) {
+            for (int sign = +1; sign >= -1; sign -= 2) {
+                uint32_t j = orc_neighbour(dim, L, i, d, sign);
+                uint32_t owner = sign > 0 ? i : j;
+                if (member[j] || c[j] != c0) continue;
+                if ((uint64_t)orc_bond_random(seed, t, owner, d) < thr) {
+                    member[j] = 1;
+                    list[ic++] = j;
+                }
+            }
+        }
+    }
+    if (levels) *levels = generations;
+    return ic;
+}
+
+/* Potts updates t0 .. t0+n-1 on c in place; records (nullable) hold |C|,
+ * levels, E_bond (satisfied bonds) and N0 in the M field. */
+int orc_potts_run(int dim, uint32_t L, uint32_t q, uint64_t thr, uint64_t seed, uint64_t t0,
+                  uint64_t n, int8_t *c, orc_record *rec)
+{
+    uint32_t sites = orc_sites(dim, L);
+    uint8_t *member = (uint8_t *)calloc(sites, 1);
+    uint32_t *list = (uint32_t *)malloc((size_t)sites * sizeof(uint32_t));
+    if (!member || !list || q < 2) { free(member); free(list); return -1; }
+    for (uint64_t u = 0; u < n; ++u) {
+        uint32_t levels = 0;
+        int nc = 0;
+        uint32_t k = orc_potts_cluster(dim, L, q, thr, seed, t0 + u, c, member, list, &levels,
+                                       &nc);
+        for (uint32_t m = 0; m < k; ++m) {
+            c[list[m]] = (int8_t)nc;
+            member[list[m]] = 0;
+        }
+        if (rec) {
+            rec[u].C = k;
+            rec[u].levels = levels;
+            rec[u].E_bond = orc_potts_energy_bond(dim, L, c);
+            rec[u].M = orc_potts_count0(dim, L, c);
+        }
+    }
+    free(member);
+    free(list);
+    return 0;
+}
+
+/* Exact enumeration of all q^N colourings (N small): hist[E_bond * (N+1) + N0]
+ * counts, E_bond in 0..D*N.  Colourings are visited as base-q numbers. */
+int orc_potts_enumerate(int dim, uint32_t L, uint32_t q, uint64_t *hist)
+{
+    uint32_t n = orc_sites(dim, L);
+    double states = 1.0;
+    for (uint32_t i = 0; i < n; ++i) states *= q;
+    if (states > 1.0e9) return -1;
+    int8_t *c = (int8_t *)calloc(n, 1);
+    if (!c) return -1;
+    uint64_t total = (uint64_t)states;
+    for (uint64_t k = 0; k < total; ++k) {
+        int64_t e = orc_potts_energy_bond(dim, L, c);
+        int64_t z = orc_potts_count0(dim, L, c);
+        hist[e * (n + 1) + z] += 1;
+        for (uint32_t i = 0; i < n; ++i) {   /* next base-q colouring */
+            if (++c[i] < (int8_t)q) break;
+            c[i] = 0;
+        }
+    }
+    free(c);
+    return 0;
+}
+
+uint64_t orc_potts_threshold(double J, double T)
+{
+    double p = 1.0 - exp(-J / T);
+    if (!(p > 0.0)) return 0;
+    if (p >= 1.0) return (uint64_t)1 << 32;
+    return (uint64_t)floor(ldexp(p, 32));
+}

@@ -66,6 +66,10 @@ WORKLOADS = {
     # update equilibrates quickly at T_c), where clusters are large
     "2d-eq": dict(dim=2, L=4096, T=TC2, seed=2, equil=1000, start="ordered"),
     "3d-eq": dict(dim=3, L=256, T=4.5115, seed=3, equil=1000, start="ordered"),
+    # q = 3 Potts (the extension named in section 6) at its exact 2D critical
+    # point T_c = 1 / ln(1 + sqrt 3), J = 1
+    "potts3-2d": dict(dim=2, L=2048, T=1.0 / math.log(1.0 + math.sqrt(3.0)), seed=4, equil=1000,
+                      start="ordered", q=3),
 }
 
 
@@ -345,18 +349,19 @@ def run_binder(args):
     print(json.dumps({"metric": "Binder ratio sweep", "binder": out}), flush=True)
 
 
-def cpu_baseline(dim, L, T, seed, spins, t, seconds):
+def cpu_baseline(dim, L, T, seed, spins, t, seconds, q=None):
     """The oracle (single-threaded C) from the GPU's equilibrated lattice, a
     few updates at a time until `seconds` of CPU work have run."""
     import numpy as np
 
     import oracle
-    thr = oracle.bond_threshold(1.0, T)
+    thr = oracle.bond_threshold(1.0, T) if q is None else oracle.potts_threshold(1.0, T)
     s = np.array(spins, dtype=np.int8, copy=True)
     flips, spent, n = 0, 0.0, 0
     while spent < seconds and n < 1000:
         t0 = time.perf_counter()
-        rec = oracle.run(dim, L, thr, seed, t + n, 1, s)
+        rec = (oracle.run(dim, L, thr, seed, t + n, 1, s) if q is None else
+               oracle.potts_run(dim, L, q, thr, seed, t + n, 1, s))
         spent += time.perf_counter() - t0
         flips += int(rec["C"][0])
         n += 1
@@ -397,14 +402,15 @@ def main():
 
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        lat = w.WolffLattice(dim, L, T, seed=seed, stream=stream)
+        lat = w.WolffLattice(dim, L, T, seed=seed, stream=stream, q=wl.get("q"))
         lat.set_schedule(sched, args.blocks, args.threads)
         if args.t_up is not None:
             lat.set_local_thresholds(args.t_up, args.t_down if args.t_down is not None
                                      else args.t_up // 2)
         info = lat.info()
         if wl["start"] == "ordered":
-            lat.set_state(np.ones(lat.N, dtype=np.int8), 0)
+            lat.set_state(np.zeros(lat.N, dtype=np.int8) if wl.get("q") else
+                          np.ones(lat.N, dtype=np.int8), 0)
         rec_buf = lat.record_buffer(U)
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
         # equilibration (untimed)
@@ -493,7 +499,7 @@ def main():
         served_out = run_served(_S, embed=True)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline(dim, L, T, seed, snap, t_snap, args.cpu_seconds)
+        cpu = cpu_baseline(dim, L, T, seed, snap, t_snap, args.cpu_seconds, q=wl.get("q"))
     # kernels per step: an L2 warm-up for lattices of 2^22 sites or more, the
     # persistent schedule's pre-launch reset, the update kernel (or, for the
     # graph schedule, one call kernel and levels + 3 nodes per update)
@@ -509,9 +515,10 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
         "data": "synthetic",
-        "config": {"workload": "%dD L=%d T=%.6g J=1 seed %d, %s start, %d equilibration + %d x %d "
+        "config": {"workload": "%s%dD L=%d T=%.6g J=1 seed %d, %s start, %d equilibration + %d x %d "
                                "recorded updates, one lattice per launch"
-                               % (dim, L, T, seed, wl["start"], equil, args.steps, U),
+                               % ("q=%d Potts, " % wl["q"] if wl.get("q") else "", dim, L, T, seed,
+                                  wl["start"], equil, args.steps, U),
                    "dim": dim, "L": L, "T": T, "seed": seed, "updates_per_step": U,
                    "schedule": args.schedule, "grid_blocks": info["grid_blocks"],
                    "t_up": args.t_up, "t_down": args.t_down,

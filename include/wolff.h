@@ -127,6 +127,29 @@ wolff_status ising_init(wolff_ctx **out, int dim, int L, double J, double T,
                         uint64_t seed, int layout, void *d_workspace,
                         size_t workspace_bytes, void *stream);
 
+/* ---- q-state Potts model ------------------------------------------------
+ * The extension section 6 of the paper names as straightforward:
+ * H = -J sum_<ij> delta(c_i, c_j), colours c in 0..q-1, 2 <= q <= 64.  One
+ * update t: seed site from lane 0 of the seed draw and a new colour
+ * c' = (c0 + 1 + floor(x1 (q-1) / 2^32)) mod q from lane 1; the cluster grows
+ * through bonds to neighbours of colour c0 that are active with
+ * p = 1 - exp(-J/T), tested on the same bond words as the Ising update; every
+ * member takes c'.  With q = 2 the chain equals the Ising chain of coupling
+ * J/2 (colour 1 <-> spin -1).  Initial colour of site i:
+ * floor(x q / 2^32), x = lane 0 of Philox(i, 0, 0, 2).
+ * A Potts context is used through the same entry points as an Ising one:
+ *   - records and measure() report E_bond = the number of satisfied forward
+ *     bonds (energy -J E_bond) and, in place of M, N0 = the number of sites
+ *     of colour 0;
+ *   - wolff_get_state / wolff_set_state exchange colours (int8 0..q-1);
+ *     set_state rejects other values with WOLFF_EINVAL;
+ *   - only the CLUSTER schedule runs it (no bursts); wolff_batch_run
+ *     returns WOLFF_EUNSUPPORTED for Potts contexts.
+ * Other arguments and ownership as for ising_init. */
+wolff_status potts_init(wolff_ctx **out, int dim, int L, int q, double J, double T,
+                        uint64_t seed, void *d_workspace, size_t workspace_bytes,
+                        void *stream);
+
 /* Enqueues n_updates single-cluster updates (t .. t+n-1), each: seed site,
  * level-synchronous growth with atomic claims and warp-aggregated appends to
  * the cluster list, boundary-bond energy change, unmark, record.  d_records

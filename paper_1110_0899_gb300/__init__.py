@@ -74,6 +74,7 @@ def load_library():
     sigs = {
         "wolff_workspace_bytes": (sz, [i, i, i]),
         "ising_init": (i, [P(v), i, i, d, d, u64, i, v, sz, v]),
+        "potts_init": (i, [P(v), i, i, i, d, d, u64, v, sz, v]),
         "wolff_step": (i, [v, u64, v]),
         "wolff_run_host": (i, [v, v, u64, u64, v, v]),
         "measure": (i, [v, P(i64), P(i64), P(u64)]),
@@ -153,6 +154,23 @@ def ising_init(dim, L, J, T, seed, layout=LAYOUT_INT8, workspace=None, stream=No
     return handle, workspace
 
 
+def potts_init(dim, L, q, J, T, seed, workspace=None, stream=None):
+    """Creates a q-state Potts context; returns (handle, workspace tensor)."""
+    torch = _torch()
+    lib = load_library()
+    nbytes = lib.wolff_workspace_bytes(dim, L, LAYOUT_INT8)
+    if nbytes == 0:
+        raise WolffError(WOLFF_EINVAL, "invalid lattice shape dim=%r L=%r" % (dim, L))
+    if workspace is None:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    handle = ctypes.c_void_p()
+    st = lib.potts_init(ctypes.byref(handle), int(dim), int(L), int(q), float(J), float(T),
+                        int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.c_void_p(workspace.data_ptr()),
+                        workspace.numel(), _stream_handle(stream))
+    _check(st)
+    return handle, workspace
+
+
 def wolff_step(handle, n_updates, d_records=None):
     """Enqueues n_updates updates; d_records: torch uint8 CUDA tensor of
     n_updates * 24 bytes (or None)."""
@@ -216,13 +234,18 @@ def records_to_numpy(d_records, n):
 
 
 class WolffLattice:
-    """One Ising lattice and its Wolff chain on the current CUDA device."""
+    """One Ising lattice (or, with q, a q-state Potts lattice) and its Wolff
+    chain on the current CUDA device."""
 
     def __init__(self, dim, L, T, J=1.0, seed=0, layout=LAYOUT_INT8, schedule=None,
-                 grid_blocks=0, block_threads=0, stream=None):
+                 grid_blocks=0, block_threads=0, stream=None, q=None):
         self.dim, self.L, self.J, self.T, self.seed = int(dim), int(L), float(J), float(T), int(seed)
         self.N = self.L ** self.dim
-        self.handle, self.workspace = ising_init(dim, L, J, T, seed, layout, stream=stream)
+        self.q = q
+        if q is None:
+            self.handle, self.workspace = ising_init(dim, L, J, T, seed, layout, stream=stream)
+        else:
+            self.handle, self.workspace = potts_init(dim, L, q, J, T, seed, stream=stream)
         self._records = None
         if schedule is not None or grid_blocks or block_threads:
             self.set_schedule(schedule or SCHED_AUTO, grid_blocks, block_threads)

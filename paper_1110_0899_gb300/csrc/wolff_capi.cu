@@ -26,6 +26,8 @@ cudaError_t launch_selftest_wait(DevCtl *scratch, unsigned long long wait_ns, cu
 struct wolff_ctx {
     int dim = 0, L = 0;
     uint32_t N = 0;
+    int potts = 0;         // 0 = Ising, 1 = q-state Potts
+    uint32_t q = 2;
     double J = 0, T = 0;
     uint64_t seed = 0, thr = 0;
     int layout = 0;
@@ -105,6 +107,7 @@ StepParams make_params(const wolff_ctx *c) {
     p.t_down = c->t_down;
     p.burst = c->burst ? 1u : 0u;
     p.budget_ns = 0;
+    p.q = c->q;
     return p;
 }
 
@@ -193,8 +196,25 @@ size_t wolff_workspace_bytes(int dim, int L, int layout) {
     return 2 * sizeof(DevCtl) + round_up(n, kAlign) + round_up(n * sizeof(uint32_t), kAlign);
 }
 
+static wolff_status init_common(wolff_ctx **out, int dim, int L, double J, double T,
+                                uint64_t seed, int layout, void *d_workspace,
+                                size_t workspace_bytes, void *stream, int potts, uint32_t q);
+
 wolff_status ising_init(wolff_ctx **out, int dim, int L, double J, double T, uint64_t seed,
                         int layout, void *d_workspace, size_t workspace_bytes, void *stream) {
+    return init_common(out, dim, L, J, T, seed, layout, d_workspace, workspace_bytes, stream, 0, 2);
+}
+
+wolff_status potts_init(wolff_ctx **out, int dim, int L, int q, double J, double T, uint64_t seed,
+                        void *d_workspace, size_t workspace_bytes, void *stream) {
+    if (q < 2 || q > 64) return WOLFF_EINVAL;
+    return init_common(out, dim, L, J, T, seed, WOLFF_LAYOUT_INT8, d_workspace, workspace_bytes,
+                       stream, 1, (uint32_t)q);
+}
+
+static wolff_status init_common(wolff_ctx **out, int dim, int L, double J, double T,
+                                uint64_t seed, int layout, void *d_workspace,
+                                size_t workspace_bytes, void *stream, int potts, uint32_t q) {
     if (!out) return WOLFF_EINVAL;
     *out = nullptr;
     if (!shape_ok(dim, L) || layout != WOLFF_LAYOUT_INT8) return WOLFF_EINVAL;
@@ -212,7 +232,10 @@ wolff_status ising_init(wolff_ctx **out, int dim, int L, double J, double T, uin
     c->J = J;
     c->T = T;
     c->seed = seed;
-    c->thr = wolff_bond_threshold(J, T);
+    c->potts = potts;
+    c->q = q;
+    // Ising: p = 1 - exp(-2J/T); Potts: p = 1 - exp(-J/T)
+    c->thr = potts ? wolff_bond_threshold(0.5 * J, T) : wolff_bond_threshold(J, T);
     c->layout = layout;
     c->stream = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaGetDevice(&c->device);
@@ -248,8 +271,12 @@ wolff_status ising_init(wolff_ctx **out, int dim, int L, double J, double T, uin
     e = cudaMemsetAsync(c->ws, 0, 2 * sizeof(DevCtl) + round_up(c->N, kAlign), c->stream);
     if (e == cudaSuccess) e = empty_list(c);
     if (e == cudaSuccess) e = launch_reset_ctl(c->ctl, 0, c->stream);
-    if (e == cudaSuccess) e = launch_init(c->spins, p.g, p.key0, p.key1, c->stream);
-    if (e == cudaSuccess) e = launch_measure_full(dim, c->spins, p.g, c->ctl, 1, c->stream);
+    if (e == cudaSuccess)
+        e = potts ? launch_potts_init(c->spins, p.g, q, p.key0, p.key1, c->stream)
+                  : launch_init(c->spins, p.g, p.key0, p.key1, c->stream);
+    if (e == cudaSuccess)
+        e = potts ? launch_potts_measure(dim, c->spins, p.g, c->ctl, 1, c->stream)
+                  : launch_measure_full(dim, c->spins, p.g, c->ctl, 1, c->stream);
     if (e != cudaSuccess) {
         cuda_fail(c, e, "ising_init");
         ising_free(c);
@@ -275,6 +302,8 @@ wolff_status wolff_set_schedule(wolff_ctx *c, int schedule, int grid_blocks, int
         return fail(c, WOLFF_EINVAL, "block_threads must be a multiple of 32 in [32, 1024]");
     if (grid_blocks < 0) return fail(c, WOLFF_EINVAL, "grid_blocks must be >= 0");
     const int sched_eff = schedule == WOLFF_SCHED_AUTO ? WOLFF_SCHED_CLUSTER : schedule;
+    if (c->potts && sched_eff != WOLFF_SCHED_CLUSTER)
+        return fail(c, WOLFF_EUNSUPPORTED, "the Potts update runs on the cluster schedule only");
     if (sched_eff != WOLFF_SCHED_GRAPH && (block_threads ? block_threads : c->threads) > 512)
         return fail(c, WOLFF_EINVAL, "persistent and cluster schedules take at most 512 threads");
     c->schedule = sched_eff;
@@ -325,7 +354,10 @@ wolff_status wolff_step(wolff_ctx *c, uint64_t n_updates, void *d_records) {
         e = launch_prefetch_l2(c->spins, c->N, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "prefetch");
     }
-    if (c->schedule == WOLFF_SCHED_CLUSTER) {
+    if (c->potts) {
+        e = launch_potts_team(c->dim, p, c->cluster, c->threads, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "potts launch");
+    } else if (c->schedule == WOLFF_SCHED_CLUSTER) {
         e = launch_team(c->dim, p, nullptr, 1, c->cluster, c->threads, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "cluster launch");
     } else if (c->schedule == WOLFF_SCHED_GRAPH) {
@@ -370,7 +402,8 @@ wolff_status measure(wolff_ctx *c, int64_t *E_bond, int64_t *M, uint64_t *last_C
 wolff_status measure_full(wolff_ctx *c, int64_t *E_bond, int64_t *M) {
     if (!c) return WOLFF_EINVAL;
     const StepParams p = make_params(c);
-    cudaError_t e = launch_measure_full(c->dim, c->spins, p.g, c->ctl, 0, c->stream);
+    cudaError_t e = c->potts ? launch_potts_measure(c->dim, c->spins, p.g, c->ctl, 0, c->stream)
+                             : launch_measure_full(c->dim, c->spins, p.g, c->ctl, 0, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "measure_full");
     DevCtl h;
     wolff_status s = sync_and_check(c, &h);
@@ -382,7 +415,10 @@ wolff_status measure_full(wolff_ctx *c, int64_t *E_bond, int64_t *M) {
 
 wolff_status wolff_get_state(wolff_ctx *c, int8_t *h_spins, uint64_t *t) {
     if (!c) return WOLFF_EINVAL;
-    if (h_spins) {
+    if (h_spins && c->potts) {   // a Potts site's byte at rest is its colour
+        cudaError_t e = cudaMemcpyAsync(h_spins, c->spins, c->N, cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "get_state");
+    } else if (h_spins) {
         int8_t *scratch = reinterpret_cast<int8_t *>(c->list);
         cudaError_t e = launch_to_pm1(scratch, c->spins, c->N, c->stream);
         if (e == cudaSuccess)
@@ -399,6 +435,24 @@ wolff_status wolff_get_state(wolff_ctx *c, int8_t *h_spins, uint64_t *t) {
 
 wolff_status wolff_set_state(wolff_ctx *c, const int8_t *h_spins, uint64_t t) {
     if (!c || !h_spins) return WOLFF_EINVAL;
+    if (c->potts) {
+        const StepParams p = make_params(c);
+        cudaError_t e = cudaMemcpyAsync(c->spins, h_spins, c->N, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = launch_reset_ctl(c->ctl, t, c->stream);
+        if (e == cudaSuccess) e = launch_potts_check(c->spins, c->N, c->q, c->ctl, c->stream);
+        if (e == cudaSuccess) e = launch_potts_measure(c->dim, c->spins, p.g, c->ctl, 1, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "set_state");
+        c->t_host = t;
+        wolff_status st = sync_and_check(c, nullptr);
+        if (st != WOLFF_OK) {   // leave a valid lattice behind a rejected one
+            launch_potts_init(c->spins, p.g, c->q, p.key0, p.key1, c->stream);
+            launch_reset_ctl(c->ctl, 0, c->stream);
+            launch_potts_measure(c->dim, c->spins, p.g, c->ctl, 1, c->stream);
+            cudaStreamSynchronize(c->stream);
+            c->t_host = 0;
+        }
+        return st;
+    }
     int8_t *scratch = reinterpret_cast<int8_t *>(c->list);
     const StepParams p = make_params(c);
     cudaError_t e = cudaMemcpyAsync(scratch, h_spins, c->N, cudaMemcpyHostToDevice, c->stream);
@@ -560,6 +614,7 @@ wolff_status wolff_batch_run_timed(wolff_batch *b, wolff_ctx *const *ctxs, int n
     int n2 = 0, n3 = 0;
     for (int i = 0; i < n; ++i) {
         if (!ctxs[i]) return WOLFF_EINVAL;
+        if (ctxs[i]->potts) return WOLFF_EUNSUPPORTED;
         if (n_updates[i] == 0) continue;
         (ctxs[i]->dim == 2 ? n2 : n3) += 1;
     }

@@ -103,6 +103,7 @@ struct StepParams {
     uint32_t t_down;            // grid hands a frontier this small back to the leader
     uint32_t burst;             // cluster schedule: speculative bursts of small updates
     unsigned long long budget_ns;   // cluster schedule: stop after this much device time (0 = none)
+    uint32_t q;                 // Potts: number of colours (the Ising kernels ignore it)
 };
 
 // Leader-local frontier capacity (shared memory) and the cluster-list prefix
@@ -135,6 +136,16 @@ int persistent_max_blocks_per_sm(int dim, int threads, int *err);
 const void *team_kernel(int dim);
 cudaError_t launch_team(int dim, const StepParams &single, const StepParams *d_table, int njobs,
                         int cluster_size, int threads, cudaStream_t s);
+
+// q-state Potts (wolff_potts.cu).
+cudaError_t launch_potts_init(uint8_t *spins, Geometry g, uint32_t q, uint32_t k0, uint32_t k1,
+                              cudaStream_t s);
+cudaError_t launch_potts_measure(int dim, const uint8_t *spins, Geometry g, DevCtl *ctl,
+                                 int set_chain, cudaStream_t s);
+cudaError_t launch_potts_check(const uint8_t *spins, uint32_t N, uint32_t q, DevCtl *ctl,
+                               cudaStream_t s);
+cudaError_t launch_potts_team(int dim, const StepParams &p, int cluster_size, int threads,
+                              cudaStream_t s);
 
 // Graph schedule: builds the nested-WHILE graph; returns its executable.
 cudaError_t build_update_graph(int dim, const StepParams &p, int blocks,

@@ -94,6 +94,7 @@ extern "C" wolff_status wolff_step_static(int dim, int L, double J, double T, ui
     p.t_down = 256;
     p.burst = 0;
     p.budget_ns = 0;
+    p.q = 2;
 
     // every call starts from a cleared control block: the array keeps the
     // previous call's contents

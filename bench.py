@@ -43,7 +43,7 @@ TC2 = 2.0 / math.log(1.0 + math.sqrt(2.0))
 # committed ncu capture (profiles/k_team_2d_L4096_random_start.md), valid only
 # while the kernel sources hash to the captured value.
 TRAFFIC_CAPTURES = {
-    ("2d", 100): {"src": "1566f913e7cc", "bytes_per_launch": 120064 + 0},   # superseded kernel
+    ("2d", 1000): {"src": "d471d1d61b18", "bytes_per_launch": 676608 + 0},
 }
 
 
@@ -489,8 +489,8 @@ def main():
     lat.close()
     batched_out = served_out = None
     if world == 1 and args.workload in ("2d", "3d") and not args.no_batched:
-        class _A:   # a batched comparison beside the headline: 2 x 1000 updates per replica
-            steps, updates_per_step = 2, 1000
+        class _A:   # a batched comparison beside the headline: 1000 updates per replica
+            steps, updates_per_step = 1, 1000
         batched_out = run_batched(_A, embed=True)
         batched_out.pop("autotune", None)
     if world == 1 and args.workload in ("2d", "3d") and not args.no_served:

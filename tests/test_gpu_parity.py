@@ -310,3 +310,36 @@ def test_burst_mode_matches_oracle(dim, L, T, n):
         assert np.array_equal(spins, s_ref)
         if T > 4.0 and L ** dim > 1000:
             assert st["burst_updates"] > n // 2
+
+
+@pytest.mark.parametrize("dim,L,T,seed,equil,sample", [(2, 4096, TC2, 2, 2000, 40),
+                                                      (3, 256, 4.5115, 3, 2000, 8)])
+def test_full_size_in_bench_configuration(dim, L, T, seed, equil, sample):
+    """The workloads bench.py times, at full size and in its launch
+    configuration (default schedule: one 16-CTA cluster, 512 threads, bursts):
+    after the specified equilibration the GPU runs one bench step of 1000
+    recorded updates.  The oracle replays the first `sample` updates from the
+    GPU's snapshot and must match them bit for bit; all 1000 records must obey
+    the update's invariants; the incremental E and M must equal a full
+    recount of the final lattice."""
+    torch, w = require_cuda()
+    lat = w.WolffLattice(dim, L, T, seed=seed)
+    lat.step(equil, records=False)
+    snap, t0 = lat.get_state()
+    assert t0 == equil
+    rec = lat.step(1000)
+    ref, _ = oracle_trajectory(dim, L, T, seed, sample, t0=t0, s=snap)
+    assert_records_equal(rec[:sample], ref, "full size %dD L=%d" % (dim, L))
+    N = L ** dim
+    E_prev, M_prev = oracle.energy_bond(dim, L, snap), oracle.magnetisation(dim, L, snap)
+    for r in rec:
+        C = int(r["C"])
+        assert 1 <= C <= N and r["levels"] >= 1
+        assert abs(int(r["M"]) - M_prev) == 2 * C
+        assert (int(r["E"]) - E_prev) % 2 == 0 and abs(int(r["E"])) <= dim * N
+        E_prev, M_prev = int(r["E"]), int(r["M"])
+    E, M, C = lat.measure()
+    assert (E, M) == lat.measure_full() == (int(rec["E"][-1]), int(rec["M"][-1]))
+    st = lat.stats()
+    assert st["burst_updates"] > 0   # the bench's burst path is the one exercised
+    lat.close()

@@ -71,7 +71,7 @@ enum { WOLFF_LAYOUT_INT8 = 0 };
  *               cluster with the hardware cluster barrier between levels;
  *   AUTO        the library's choice: CLUSTER with the largest cluster the
  *               GPU launches (16 where non-portable sizes are allowed, else
- *               8), 512 threads, t_up = 128, t_down = 64, bursts on (the
+ *               8), 512 threads, t_up = 128, t_down = 64, window mode on (the
  *               default). */
 enum {
     WOLFF_SCHED_AUTO = 0,
@@ -143,7 +143,7 @@ wolff_status ising_init(wolff_ctx **out, int dim, int L, double J, double T,
  *     of colour 0;
  *   - wolff_get_state / wolff_set_state exchange colours (int8 0..q-1);
  *     set_state rejects other values with WOLFF_EINVAL;
- *   - only the CLUSTER schedule runs it (no bursts); wolff_batch_run
+ *   - only the CLUSTER schedule runs it (no window mode); wolff_batch_run
  *     returns WOLFF_EUNSUPPORTED for Potts contexts.
  * Other arguments and ownership as for ising_init. */
 wolff_status potts_init(wolff_ctx **out, int dim, int L, int q, double J, double T,
@@ -200,12 +200,18 @@ wolff_status wolff_set_schedule(wolff_ctx *ctx, int schedule, int grid_blocks,
  * t_down <= t_up <= 2048.  Results do not depend on the values. */
 wolff_status wolff_set_local_thresholds(wolff_ctx *ctx, uint32_t t_up, uint32_t t_down);
 
-/* Cluster schedule and batched runs: burst mode (on by default).  While the
- * recent clusters are small the leader CTA grows up to one update per warp at
- * once on the same lattice, then commits in order the longest prefix whose
- * updates read no site flipped by an earlier update of the prefix; the rest
- * run the ordinary way.  A committed update is exactly the serial one, so
- * results do not depend on the setting. */
+/* Cluster schedule and batched runs: window mode (on by default).  While the
+ * recent clusters are small, all warps of the team grow consecutive updates
+ * speculatively on the current lattice, one update per warp at a time, each
+ * taking the next free update of a window of up to 2048 when done.  Rounds
+ * of `levels` growth levels alternate with commits: the prefix of finished
+ * updates that read no site flipped by an earlier one is applied in order,
+ * and an uncommitted update that read a committed flip is grown again.  A
+ * committed update is exactly the serial one (section 2's cluster depends
+ * only on the spins it reads and on the counter-based bond draws), so results
+ * do not depend on the setting.  enable: 0 = off, 1 = on with 32 levels per
+ * round, k >= 2 = on with k levels per round (at most 64).  EINVAL if
+ * enable < 0. */
 wolff_status wolff_set_burst(wolff_ctx *ctx, int enable);
 
 wolff_status wolff_get_info(wolff_ctx *ctx, wolff_info *info);
@@ -224,8 +230,13 @@ typedef struct {
     uint64_t grid_finishes;    /* updates closed by all CTAs */
     uint64_t start_ns;         /* device globaltimer when the last launch began this lattice */
     uint64_t end_ns;           /* ... and when it finished it */
-    uint64_t burst_updates;    /* updates committed by burst mode (cluster schedule) */
-    uint64_t bursts;           /* bursts attempted */
+    uint64_t burst_updates;    /* updates committed by window mode (cluster schedule) */
+    uint64_t bursts;           /* window-mode commit rounds */
+    uint64_t ns_win_grow;      /* window mode, leader's view: growth phases */
+    uint64_t ns_win_map;       /*   flattening and recording the flips */
+    uint64_t ns_win_check;     /*   conflict checks and the cut */
+    uint64_t ns_win_commit;    /*   commits, records, regrowth queue */
+    uint64_t win_levels;       /* growth levels run by all warps, discarded ones included */
 } wolff_stats;
 
 /* Reads the counters above.  Synchronises. */

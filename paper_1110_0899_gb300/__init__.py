@@ -48,7 +48,8 @@ class _Info(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in
                 ("updates", "levels_local", "levels_grid", "ns_local", "ns_grid", "ns_finish",
-                 "handoffs", "grid_finishes", "start_ns", "end_ns", "burst_updates", "bursts")]
+                 "handoffs", "grid_finishes", "start_ns", "end_ns", "burst_updates", "bursts",
+                 "ns_win_grow", "ns_win_map", "ns_win_check", "ns_win_commit", "win_levels")]
 
 
 _lib = None
@@ -264,7 +265,10 @@ class WolffLattice:
         return {k: getattr(inf, k) for k, _ in _Info._fields_}
 
     def set_burst(self, enable):
-        _check(load_library().wolff_set_burst(self.handle, 1 if enable else 0), self.handle)
+        """Window mode: False/0 off, True/1 on, k >= 2 on with k growth levels
+        per commit round."""
+        level = int(enable) if not isinstance(enable, bool) else (1 if enable else 0)
+        _check(load_library().wolff_set_burst(self.handle, level), self.handle)
 
     def stats(self):
         st = _Stats()

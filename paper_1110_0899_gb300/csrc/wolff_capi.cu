@@ -52,7 +52,7 @@ struct wolff_ctx {
     unsigned long long wait_ns = 2000000000ull;
     uint32_t t_up = 128, t_down = 64;
     bool thresholds_set = false;
-    bool burst = true;
+    int burst = kDefaultWindowLevels;   // window mode: growth levels per round (0 = off)
     int cluster = 8;
     int max_cluster = 8;
     std::string err;
@@ -61,6 +61,10 @@ struct wolff_ctx {
 namespace {
 
 constexpr size_t kAlign = 256;
+// window slots per CTA: one lattice per launch gets a 2048-update window at
+// cluster size 16; the batched form keeps its CTAs small
+constexpr int kPlainWindowSlots = 128;
+constexpr int kBatchWindowSlots = 64;
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -105,7 +109,7 @@ StepParams make_params(const wolff_ctx *c) {
     p.wait_ns = c->wait_ns;
     p.t_up = c->t_up;
     p.t_down = c->t_down;
-    p.burst = c->burst ? 1u : 0u;
+    p.burst = (uint32_t)c->burst;
     p.budget_ns = 0;
     p.q = c->q;
     return p;
@@ -140,6 +144,12 @@ int max_cluster_size(int dim, int threads) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(16);
     cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = window_smem_bytes(threads, kPlainWindowSlots);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cfg.dynamicSmemBytes) != cudaSuccess) {
+        cudaGetLastError();
+        return 8;
+    }
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 16;
@@ -338,7 +348,8 @@ wolff_status wolff_set_local_thresholds(wolff_ctx *c, uint32_t t_up, uint32_t t_
 
 wolff_status wolff_set_burst(wolff_ctx *c, int enable) {
     if (!c) return WOLFF_EINVAL;
-    c->burst = enable != 0;
+    if (enable < 0) return fail(c, WOLFF_EINVAL, "enable must be >= 0");
+    c->burst = enable == 0 ? 0 : enable == 1 ? kDefaultWindowLevels : (enable > 64 ? 64 : enable);
     return WOLFF_OK;
 }
 
@@ -358,7 +369,8 @@ wolff_status wolff_step(wolff_ctx *c, uint64_t n_updates, void *d_records) {
         e = launch_potts_team(c->dim, p, c->cluster, c->threads, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "potts launch");
     } else if (c->schedule == WOLFF_SCHED_CLUSTER) {
-        e = launch_team(c->dim, p, nullptr, 1, c->cluster, c->threads, c->stream);
+        e = launch_team(c->dim, p, nullptr, 1, c->cluster, c->threads, kPlainWindowSlots,
+                        c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "cluster launch");
     } else if (c->schedule == WOLFF_SCHED_GRAPH) {
         if (!c->gexec) {
@@ -538,6 +550,11 @@ wolff_status wolff_get_stats(wolff_ctx *c, wolff_stats *st) {
     st->end_ns = h.st_end_ns;
     st->burst_updates = h.st_burst_updates;
     st->bursts = h.st_bursts;
+    st->ns_win_grow = h.st_ns_win[0];
+    st->ns_win_map = h.st_ns_win[1];
+    st->ns_win_check = h.st_ns_win[2];
+    st->ns_win_commit = h.st_ns_win[3];
+    st->win_levels = h.st_win_levels;
     return WOLFF_OK;
 }
 
@@ -639,9 +656,12 @@ wolff_status wolff_batch_run_timed(wolff_batch *b, wolff_ctx *const *ctxs, int n
     if (e != cudaSuccess) return WOLFF_ECUDA;
     b->pending = true;
     StepParams none = {};
-    if (n2) e = launch_team(2, none, b->d_table, n2, cluster_size, block_threads, b->stream);
+    if (n2)
+        e = launch_team(2, none, b->d_table, n2, cluster_size, block_threads, kBatchWindowSlots,
+                        b->stream);
     if (e == cudaSuccess && n3)
-        e = launch_team(3, none, b->d_table + n2, n3, cluster_size, block_threads, b->stream);
+        e = launch_team(3, none, b->d_table + n2, n3, cluster_size, block_threads,
+                        kBatchWindowSlots, b->stream);
     if (e != cudaSuccess) return WOLFF_ECUDA;
     for (int i = 0; i < n; ++i) ctxs[i]->t_host += n_updates[i];
     return WOLFF_OK;

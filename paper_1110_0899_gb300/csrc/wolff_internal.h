@@ -77,8 +77,11 @@ struct alignas(256) DevCtl {
     unsigned long long st_ns_local, st_ns_grid, st_ns_finish;
     unsigned long long st_handoffs, st_grid_finishes;
     unsigned long long st_start_ns, st_end_ns;   // globaltimer at the last launch's start/end
-    unsigned long long st_burst_updates;         // updates committed by burst mode
-    unsigned long long st_bursts;                // bursts attempted
+    unsigned long long st_burst_updates;         // updates committed by window mode
+    unsigned long long st_bursts;                // window-mode commit rounds
+    // line 6: window-mode phase times (leader thread 0) and growth work
+    alignas(128) unsigned long long st_ns_win[4];   // growth, map, check, commit
+    unsigned long long st_win_levels;            // growth levels of all warps (incl. discarded)
 };
 static_assert(sizeof(DevCtl) % 256 == 0 && sizeof(DevCtl) <= 1024, "control block layout");
 
@@ -101,7 +104,7 @@ struct StepParams {
     unsigned long long wait_ns; // bound of every device-side wait
     uint32_t t_up;              // leader hands a frontier larger than this to the grid
     uint32_t t_down;            // grid hands a frontier this small back to the leader
-    uint32_t burst;             // cluster schedule: speculative bursts of small updates
+    uint32_t burst;             // cluster schedule: window mode, growth levels per round (0 = off)
     unsigned long long budget_ns;   // cluster schedule: stop after this much device time (0 = none)
     uint32_t q;                 // Potts: number of colours (the Ising kernels ignore it)
 };
@@ -133,9 +136,17 @@ int persistent_max_blocks_per_sm(int dim, int threads, int *err);
 // Team schedule (wolff_team.cu): one thread-block cluster per job; the jobs
 // come from d_table (device array of njobs StepParams) or, when d_table is
 // null, the single job `single` (njobs must be 1).
+// Window mode (speculative growth of many small updates at once) needs
+// window_slots (a power of two, 0 = off) slots per CTA of dynamic shared memory.
+struct WinCfg {
+    uint32_t slots;   // window slots per CTA (0: no window area, window mode off)
+    uint32_t cap;     // members per speculative update
+};
+constexpr int kDefaultWindowLevels = 32;  // growth levels per warp between commit rounds
 const void *team_kernel(int dim);
+size_t window_smem_bytes(int threads, int window_slots);
 cudaError_t launch_team(int dim, const StepParams &single, const StepParams *d_table, int njobs,
-                        int cluster_size, int threads, cudaStream_t s);
+                        int cluster_size, int threads, int window_slots, cudaStream_t s);
 
 // q-state Potts (wolff_potts.cu).
 cudaError_t launch_potts_init(uint8_t *spins, Geometry g, uint32_t q, uint32_t k0, uint32_t k1,

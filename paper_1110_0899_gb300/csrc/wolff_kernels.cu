@@ -198,6 +198,8 @@ __global__ void k_reset_ctl(DevCtl *ctl, unsigned long long t) {
     ctl->st_start_ns = ctl->st_end_ns = 0;
     ctl->st_burst_updates = 0;
     ctl->st_bursts = 0;
+    for (int k = 0; k < 4; ++k) ctl->st_ns_win[k] = 0;
+    ctl->st_win_levels = 0;
 }
 
 // Before every persistent launch: command sequence, barrier word and

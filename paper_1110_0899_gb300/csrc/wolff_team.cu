@@ -33,21 +33,36 @@ namespace {
 
 enum : unsigned int { kTeamLevels = 1, kTeamFinish = 2, kTeamExit = 3, kTeamBurst = 4 };
 
-// ---- burst mode --------------------------------------------------------------
+// ---- window mode -------------------------------------------------------------
 // While clusters are small, consecutive updates rarely touch the same sites.
-// The leader then grows up to one update per warp at once, all on the same
-// lattice, without claiming anything (each warp keeps its cluster in a
-// shared-memory hash set), and afterwards commits, in order, the longest
-// prefix whose updates read no site that an earlier update of the prefix
-// flips.  Update t+j reads its members and their neighbours; if none of them
-// was flipped by updates t..t+j-1, it sees exactly the lattice the serial
-// chain would show it, so every committed update is the serial one -- the
-// same component, level count, boundary sum and record.  The first update that
-// conflicts, or whose cluster outgrows kBurstCap, is left for the ordinary path.
-constexpr int kBurstMaxWarps = 16;
-constexpr uint32_t kBurstCap = 64;          // members per speculative update (128 at <= 8 warps)
-constexpr uint32_t kBurstMapSlots = 2048;   // flipped-site map of the whole burst
+// Window mode then grows many consecutive updates at once, all on the current
+// lattice, without claiming anything: each warp grows one update at a time
+// (its cluster in a shared-memory hash set) and, when done, takes the next
+// free update of its CTA.  The window holds updates [c, c + P), P = S slots
+// per CTA times the cluster size; update j lives in CTA j mod CS, slot
+// (j / CS) mod S.  Rounds of K levels of growth alternate with commits:
+//   - every finished update records the sites it flips in a map "lowest
+//     update index that flips this site", spread over the CTAs' shared
+//     memory (each site has an owner CTA, reached through distributed shared
+//     memory);
+//   - update j conflicts if it reads (its members and their neighbours) a
+//     site that an earlier finished update of the window flips;
+//   - the round commits [c, cut), cut = the first update that is unfinished
+//     or conflicts: it flips their members and writes their records;
+//   - every uncommitted update, finished or still growing, that read a site
+//     the committed ones flip is grown again from its seed; the others keep
+//     their clusters, which the new lattice leaves unchanged.
+// An update that read no site flipped by an earlier one sees exactly the
+// lattice the serial chain shows it, so every committed update is the serial
+// one: the same component, level count, boundary sum and record.  An update
+// whose cluster outgrows the cap (or whose flips do not fit the map) stops the
+// window; it runs the ordinary way.
+constexpr int kWinMaxWarps = 16;
+constexpr uint32_t kWinCap = 64;            // members per speculative update (128 at <= 8 warps)
 constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint32_t kWinMaxStall = 4096;     // rounds without a commit before giving up
+enum : uint32_t { kSlotFree = 0, kSlotGrowing = 1, kSlotDone = 2, kSlotTooBig = 3, kSlotRegrow = 4 };
 
 struct TeamShared {
     uint32_t front[2][kLocalFrontierCap];
@@ -56,11 +71,16 @@ struct TeamShared {
     unsigned int sig0bit;
     unsigned int cmd[8];        // kind, lo, hi, level, sig0bit, t_lo, t_hi
     unsigned long long dE;      // team boundary sum (leader's copy)
-    // burst mode (leader only): per-warp results and the commit cut
-    int bres[kBurstMaxWarps][4];  // |C| (or -1 when too big), levels, dE_bond, sig0bit
-    unsigned int bcut;
+    // window mode (the leader's copies are the team's)
+    unsigned int wcut;          // lowest update of the window that cannot commit (atomic)
+    unsigned int wlimit;        // lowest update found too big (atomic)
+    unsigned int wstop;         // time budget spent
     unsigned int bflag;
     unsigned int bstop;
+    unsigned int wlast[2];      // |C| and levels of the last committed update
+    unsigned long long wlevels; // growth levels of all warps (atomic)
+    long long wsum[3][kWinMaxWarps];  // per-warp totals of the record scan
+    long long wbase[3];         // E_bond, M and sum of |C| before the scanned block
 };
 
 // All CTAs of the team: expand level after level from list[lo, hi) until the
@@ -143,13 +163,17 @@ __device__ __forceinline__ long long team_finish(const StepParams &p, TeamShared
 }
 
 template <int DIM>
-__device__ uint32_t team_burst(const StepParams &p, TeamShared &sh, cg::cluster_group &cl,
-                               unsigned long long u0, uint32_t nb, long long &E, long long &M,
-                               unsigned long long &total_C, uint32_t &last_C,
-                               uint32_t &last_levels);
+__device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster_group &cl,
+                                const WinCfg &wc, unsigned long long u0, uint32_t n_rem,
+                                unsigned long long launch_t0, long long &E, long long &M,
+                                unsigned long long &total_C, uint32_t &last_C,
+                                uint32_t &last_levels, unsigned long long &rounds,
+                                unsigned long long *win_ns, uint32_t c_start, bool resume,
+                                bool &resumable);
 
 template <int DIM>
-__device__ void team_worker(const StepParams &p, TeamShared &sh, cg::cluster_group &cl) {
+__device__ void team_worker(const StepParams &p, TeamShared &sh, cg::cluster_group &cl,
+                            const WinCfg &wc) {
     TeamShared *lead = cl.map_shared_rank(&sh, 0);
     while (true) {
         cl.sync();   // the leader has announced the next phase
@@ -164,10 +188,11 @@ __device__ void team_worker(const StepParams &p, TeamShared &sh, cg::cluster_gro
             team_finish<DIM>(p, sh, cl, hi, sig0bit);
         } else if (kind == kTeamBurst) {
             long long E = 0, M = 0;
-            unsigned long long tc = 0;
+            unsigned long long tc = 0, rounds = 0;
             uint32_t lc = 0, ll = 0;
-            team_burst<DIM>(p, sh, cl, ((unsigned long long)hi << 32) | lo, level, E, M, tc, lc,
-                            ll);
+            bool resumable = false;
+            team_window<DIM>(p, sh, cl, wc, ((unsigned long long)hi << 32) | lo, level, 0, E, M,
+                             tc, lc, ll, rounds, nullptr, tlo, sig0bit != 0, resumable);
         } else {
             // the leader's shared memory (read above) must outlive every
             // remote access: leave together, after one more cluster barrier
@@ -206,258 +231,601 @@ __device__ __forceinline__ bool burst_contains(const uint32_t *set, uint32_t slo
     return false;
 }
 
-// Owner CTA of a site in the team's distributed flipped-site map.
-__device__ __forceinline__ uint32_t burst_owner(uint32_t site, uint32_t cs) {
-    return ((site * 0x85EBCA6Bu) >> 16) & (cs - 1u);
+
+// The window's per-CTA state in dynamic shared memory: S slots of `cap`
+// members (packed coordinates), each slot's result (|C|, levels, dE_bond / 2,
+// seed spin) as one 16-byte word, then the slot's update index, state and
+// lowest conflicting update, the regrowth queue, the slot offsets of the
+// flattened member list, a few counters, and per member the alignment of
+// its 2 DIM neighbours with the seed spin as the growth read them (bit s =
+// neighbour s parallel), which revalidates a finished update after a change
+// of the lattice made outside the window.
+struct WinView {
+    uint32_t *members, *j, *state, *cmin, *rg, *off, *scal;
+    uint4 *meta;
+    uint8_t *amask;
+};
+enum : uint32_t { kScNextQ = 0, kScRgCount = 1, kScRgTake = 2, kScQEnd = 3, kScMin = 4 };
+constexpr uint32_t kWinScalars = 8;
+
+__device__ __forceinline__ WinView win_view(uint32_t *base, uint32_t S, uint32_t cap) {
+    WinView v;
+    v.members = base;
+    v.meta = reinterpret_cast<uint4 *>(base + S * cap);
+    uint32_t *m = base + S * cap + 4 * S;
+    v.j = m;
+    v.state = m + S;
+    v.cmin = m + 2 * S;
+    v.rg = m + 3 * S;
+    v.off = m + 4 * S;          // S + 1 entries
+    v.scal = m + 5 * S + 1;     // kWinScalars
+    v.amask = reinterpret_cast<uint8_t *>(m + 5 * S + 1 + kWinScalars);   // S * cap bytes
+    return v;
 }
 
-// All CTAs of the team: grow, check and commit up to nb consecutive updates
-// starting at p.t0 + u0, update u0 + g on warp g % W of CTA g / W (W warps per
-// CTA).  The map "lowest update index that flips a site" is spread over the
-// CTAs' shared memory (each site has an owner CTA) and reached through
-// distributed shared memory; cluster barriers separate growth, insertion,
-// checking and commit.  Returns how many updates were committed (0 when the
-// first one is too big); the leader's thread 0 advances the chain state and
-// writes their records.
+__device__ __forceinline__ void win_tick(unsigned long long &acc, unsigned long long &tick) {
+    const unsigned long long now = global_ns();
+    acc += now - tick;
+    tick = now;
+}
+
+// Warp 0: off[s] = members of the finished slots before slot s, off[S] = all.
+__device__ __forceinline__ void win_flatten(const WinView &v, uint32_t S, uint32_t lane) {
+    uint32_t carry = 0;
+    for (uint32_t k0 = 0; k0 < S; k0 += 32) {
+        const uint32_t s = k0 + lane;
+        const uint32_t x = (s < S && v.state[s] == kSlotDone) ? v.meta[s].x : 0;
+        uint32_t incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFullMask, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
+        }
+        if (s < S) v.off[s] = carry + incl - x;
+        carry += __shfl_sync(kFullMask, incl, 31);
+    }
+    if (lane == 0) v.off[S] = carry;
+}
+
+// Warp 0: the regrowth queue, lowest update first (window starts at c).
+__device__ __forceinline__ void win_queue(const WinView &v, uint32_t S, uint32_t c, uint32_t rank,
+                                          uint32_t cs, uint32_t lane) {
+    const uint32_t qlo = c > rank ? (c - rank + cs - 1) / cs : 0;
+    uint32_t count = 0;
+    for (uint32_t k0 = 0; k0 < S; k0 += 32) {
+        const uint32_t s = (qlo + k0 + lane) & (S - 1);
+        const bool want = k0 + lane < S && v.state[s] == kSlotRegrow;
+        const uint32_t mask = __ballot_sync(kFullMask, want);
+        if (want) v.rg[count + __popc(mask & ((1u << lane) - 1u))] = s;
+        count += __popc(mask);
+    }
+    if (lane == 0) {
+        v.scal[kScRgCount] = count;
+        v.scal[kScRgTake] = 0;
+    }
+}
+
+// Slot s holding update j of the flattened list entry f: off[s] <= f < off[s+1].
+__device__ __forceinline__ uint32_t flat_slot(const uint32_t *off, uint32_t S, uint32_t f) {
+    uint32_t lo = 0, hi = S;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (off[mid] <= f) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Warp: a fresh speculative growth of update t (seed claimed in the hash set).
 template <int DIM>
-__device__ uint32_t team_burst(const StepParams &p, TeamShared &sh, cg::cluster_group &cl,
-                               unsigned long long u0, uint32_t nb, long long &E, long long &M,
-                               unsigned long long &total_C, uint32_t &last_C,
-                               uint32_t &last_levels) {
-    const uint32_t W = min((uint32_t)(blockDim.x >> 5), (uint32_t)kBurstMaxWarps);
-    const uint32_t rank = cl.block_rank(), cs = cl.num_blocks();
-    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t g = rank * W + warp;
-    const bool active = warp < W && g < nb;
-    TeamShared *lead = cl.map_shared_rank(&sh, 0);
-    uint32_t *raw = &sh.front[0][0];                 // 8192 words, free outside growth
-    uint32_t *map_key = raw;                         // kBurstMapSlots
-    uint32_t *map_val = raw + kBurstMapSlots;        // kBurstMapSlots
-    // a CTA with 8 warps or fewer gives each of them room for 128 members
-    const uint32_t cap = W <= 8 ? 2 * kBurstCap : kBurstCap, hslots = 2 * cap;
-    uint32_t *mine = raw + 2 * kBurstMapSlots + (warp % kBurstMaxWarps) * (cap + hslots);
-    uint32_t *members = mine, *hset = mine + cap;
-    for (uint32_t k = threadIdx.x; k < kBurstMapSlots; k += blockDim.x) {
-        map_key[k] = kEmptyKey;
-        map_val[k] = 0xFFFFFFFFu;
+__device__ __forceinline__ void win_start(const StepParams &p, unsigned long long t,
+                                          uint32_t *members, uint32_t *hset, uint32_t hslots,
+                                          uint32_t lane, uint32_t &n, uint32_t &lo,
+                                          uint32_t &levels, uint32_t &sig0bit) {
+    for (uint32_t k = lane; k < hslots; k += 32) hset[k] = kEmptyKey;
+    __syncwarp();
+    const uint32_t i0 = seed_site(p, t);
+    sig0bit = __ldca(p.spins + i0) & 1u;
+    if (lane == 0) {
+        burst_insert(hset, hslots, i0);
+        members[0] = pack_index<DIM>(p.g, i0);
     }
+    __syncwarp();
+    n = 1;
+    lo = 0;
+    levels = 0;
+}
+
+// Warp: one level of speculative growth, members[lo, n) -> new members
+// appended.  Returns true when the cluster outgrew cap.
+template <int DIM>
+__device__ __forceinline__ bool win_level(const StepParams &p, uint32_t *members, uint8_t *amask,
+                                          uint32_t *hset, uint32_t hslots, uint32_t cap,
+                                          uint32_t lane, uint32_t &lo, uint32_t &n,
+                                          uint32_t sig0bit, uint32_t tlo, uint32_t thi) {
+    const uint32_t hi = n;
     bool too_big = false;
-    uint32_t n = 0;
-    // ---- grow
-    if (active) {
-        for (uint32_t k = lane; k < hslots; k += 32) hset[k] = kEmptyKey;
-        __syncwarp();
-        const unsigned long long t = p.t0 + u0 + g;
-        const uint32_t tlo = (uint32_t)t, thi = (uint32_t)(t >> 32);
-        const uint32_t i0 = seed_site(p, t);
-        const uint32_t sig0bit = __ldcg(p.spins + i0) & 1u;
-        if (lane == 0) {
-            burst_insert(hset, hslots, i0);
-            members[0] = pack_index<DIM>(p.g, i0);
-        }
-        __syncwarp();
-        n = 1;
-        uint32_t lo = 0, levels = 0;
-        while (lo < n && !too_big) {
-            const uint32_t hi = n;
-            for (uint32_t b = lo; b < hi; b += 32) {
-                const uint32_t k = b + lane;
-                Neighbours<DIM> nb2;
-                uint32_t fresh = 0;
-                bool full = false;
-                if (k < hi) {
-                    uint32_t i;
-                    neighbours<DIM>(p.g, members[k], &i, nb2);
-                    uint8_t v[2 * DIM];
-#pragma unroll
-                    for (int s = 0; s < 2 * DIM; ++s) v[s] = __ldcg(p.spins + nb2.idx[s]);
-                    uint32_t owners[DIM + 1];
-                    owners[0] = i;
-#pragma unroll
-                    for (int d = 0; d < DIM; ++d) owners[d + 1] = nb2.idx[2 * d + 1];
-                    Philox4 draw[DIM + 1];
-                    philox4x32_10_lanes<DIM + 1>(owners, tlo, thi, kTagBond, p.key0, p.key1, draw);
-#pragma unroll
-                    for (int s = 0; s < 2 * DIM; ++s) {
-                        const int d = s >> 1;
-                        const uint32_t r = (s & 1) ? draw[d + 1].v[d] : draw[0].v[d];
-                        if ((uint32_t)(v[s] & 1u) == sig0bit && (unsigned long long)r < p.thr) {
-                            const int ins = burst_insert(hset, hslots, nb2.idx[s]);
-                            if (ins > 0) fresh |= 1u << s;
-                            if (ins < 0) full = true;
-                        }
-                    }
-                }
-                const uint32_t cnt = __popc(fresh);
-                uint32_t incl = cnt;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(kFullMask, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                const uint32_t total = __shfl_sync(kFullMask, incl, 31);
-                uint32_t pos = n + incl - cnt;
-#pragma unroll
-                for (int s = 0; s < 2 * DIM; ++s) {
-                    if (fresh & (1u << s)) {
-                        if (pos < cap) members[pos] = nb2.packed[s];
-                        ++pos;
-                    }
-                }
-                n += total;
-                if (__any_sync(kFullMask, full) || n > cap) too_big = true;
-            }
-            __syncwarp();
-            ++levels;
-            lo = hi;
-        }
-        int dE = 0;
-        if (!too_big) {
-            for (uint32_t k = lane; k < n; k += 32) {
-                uint32_t i;
-                Neighbours<DIM> nb2;
-                neighbours<DIM>(p.g, members[k], &i, nb2);
-#pragma unroll
-                for (int s = 0; s < 2 * DIM; ++s) {
-                    if (burst_contains(hset, hslots, nb2.idx[s])) continue;
-                    const uint32_t cur = __ldcg(p.spins + nb2.idx[s]) & 1u;
-                    dE += (cur == sig0bit) ? -1 : 1;
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) dE += __shfl_down_sync(kFullMask, dE, o);
-        }
-        if (lane == 0) {
-            sh.bres[warp][0] = too_big ? -1 : (int)n;
-            sh.bres[warp][1] = (int)levels;
-            sh.bres[warp][2] = dE;
-            sh.bres[warp][3] = (int)sig0bit;
-            if (too_big) atomicMin(&lead->bcut, g);
-        }
-    }
-    cl.sync();   // every CTA has grown its updates and cleared its part of the map
-    // ---- the lowest update index that flips each site, in the owner CTA's map
-    if (active && !too_big) {
-        bool lost = false;
-        for (uint32_t k = lane; k < n; k += 32) {
-            uint32_t c[DIM];
-            unpack<DIM>(members[k], c);
-            const uint32_t site = site_index<DIM>(p.g, c);
-            uint32_t *rraw = cl.map_shared_rank(raw, burst_owner(site, cs));
-            uint32_t h = burst_hash(site * 0x9E3779B1u + 0x7F4A7C15u, kBurstMapSlots);
-            bool placed = false;
-            for (uint32_t probe = 0; probe < kBurstMapSlots; ++probe) {
-                const uint32_t prev = atomicCAS(rraw + h, kEmptyKey, site);
-                if (prev == kEmptyKey || prev == site) {
-                    atomicMin(rraw + kBurstMapSlots + h, g);
-                    placed = true;
-                    break;
-                }
-                h = (h + 1) & (kBurstMapSlots - 1);
-            }
-            if (!placed) lost = true;
-        }
-        // a map too full to record a flip makes the update unsafe to commit
-        if (__any_sync(kFullMask, lost) && lane == 0) atomicMin(&lead->bcut, g);
-    }
-    cl.sync();
-    // ---- update g conflicts if it read a site flipped by an earlier update
-    if (active && !too_big) {
-        bool conflict = false;
-        for (uint32_t k = lane; k < n && !conflict; k += 32) {
+    for (uint32_t b = lo; b < hi && !too_big; b += 32) {
+        const uint32_t k = b + lane;
+        Neighbours<DIM> nb2;
+        uint32_t fresh = 0;
+        bool full = false;
+        if (k < hi) {
             uint32_t i;
-            Neighbours<DIM> nb2;
             neighbours<DIM>(p.g, members[k], &i, nb2);
-            uint32_t probe_sites[2 * DIM + 1];
-            probe_sites[0] = i;
+            uint8_t v[2 * DIM];
 #pragma unroll
-            for (int s = 0; s < 2 * DIM; ++s) probe_sites[s + 1] = nb2.idx[s];
+            for (int s = 0; s < 2 * DIM; ++s) v[s] = __ldca(p.spins + nb2.idx[s]);
+            uint32_t par = 0;
 #pragma unroll
-            for (int q = 0; q < 2 * DIM + 1; ++q) {
-                const uint32_t site = probe_sites[q];
-                const uint32_t *rraw = cl.map_shared_rank(raw, burst_owner(site, cs));
-                uint32_t h = burst_hash(site * 0x9E3779B1u + 0x7F4A7C15u, kBurstMapSlots);
-                for (uint32_t probe = 0; probe < kBurstMapSlots; ++probe) {
-                    const uint32_t key = rraw[h];
-                    if (key == site) {
-                        if (rraw[kBurstMapSlots + h] < g) conflict = true;
-                        break;
-                    }
-                    if (key == kEmptyKey) break;
-                    h = (h + 1) & (kBurstMapSlots - 1);
+            for (int s = 0; s < 2 * DIM; ++s) par |= (uint32_t)((v[s] & 1u) == sig0bit) << s;
+            amask[k] = (uint8_t)par;
+            uint32_t owners[DIM + 1];
+            owners[0] = i;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) owners[d + 1] = nb2.idx[2 * d + 1];
+            Philox4 draw[DIM + 1];
+            philox4x32_10_lanes<DIM + 1>(owners, tlo, thi, kTagBond, p.key0, p.key1, draw);
+#pragma unroll
+            for (int s = 0; s < 2 * DIM; ++s) {
+                const int d = s >> 1;
+                const uint32_t r = (s & 1) ? draw[d + 1].v[d] : draw[0].v[d];
+                if (((par >> s) & 1u) && (unsigned long long)r < p.thr) {
+                    const int ins = burst_insert(hset, hslots, nb2.idx[s]);
+                    if (ins > 0) fresh |= 1u << s;
+                    if (ins < 0) full = true;
                 }
             }
         }
-        if (__any_sync(kFullMask, conflict) && lane == 0) atomicMin(&lead->bcut, g);
-    }
-    cl.sync();
-    const uint32_t cut = *reinterpret_cast<volatile unsigned int *>(&lead->bcut);
-    // ---- commit updates [0, cut): flip their members (both bits)
-    if (active && g < cut) {
-        const uint8_t v = sh.bres[warp][3] ? 0x00 : 0x03;
-        for (uint32_t k = lane; k < n; k += 32) {
-            uint32_t c[DIM];
-            unpack<DIM>(members[k], c);
-            p.spins[site_index<DIM>(p.g, c)] = v;
-        }
-    }
-    if (rank == 0 && cut > 0) {
-        // records of the committed updates in parallel: a scan of the energy
-        // and magnetisation steps over the leader CTA
-        __shared__ long long s_e[512], s_m[512];
-        __shared__ unsigned long long s_c[512];
-        __shared__ long long s_base[2];
-        const uint32_t j = threadIdx.x;
-        int res[4] = {0, 0, 0, 0};
-        if (j < cut) {
-            const TeamShared *src = cl.map_shared_rank(&sh, j / W);
+        const uint32_t cnt = __popc(fresh);
+        uint32_t incl = cnt;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) res[q] = src->bres[j % W][q];
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFullMask, incl, o);
+            if (lane >= o) incl += y;
         }
-        s_e[j] = j < cut ? 2LL * res[2] : 0;
-        s_m[j] = j < cut ? (res[3] ? -2LL : 2LL) * res[0] : 0;
-        s_c[j] = j < cut ? (unsigned long long)res[0] : 0;
-        if (j == 0) {
-            s_base[0] = E;
-            s_base[1] = M;
+        const uint32_t total = __shfl_sync(kFullMask, incl, 31);
+        uint32_t pos = n + incl - cnt;
+#pragma unroll
+        for (int s = 0; s < 2 * DIM; ++s) {
+            if (fresh & (1u << s)) {
+                if (pos < cap) members[pos] = nb2.packed[s];
+                ++pos;
+            }
         }
-        __syncthreads();
-        for (uint32_t off = 1; off < cut; off <<= 1) {
-            const long long ve = j >= off ? s_e[j - off] : 0;
-            const long long vm = j >= off ? s_m[j - off] : 0;
-            const unsigned long long vc = j >= off ? s_c[j - off] : 0;
-            __syncthreads();
-            s_e[j] += ve;
-            s_m[j] += vm;
-            s_c[j] += vc;
-            __syncthreads();
+        n += total;
+        if (__any_sync(kFullMask, full) || n > cap) too_big = true;
+    }
+    __syncwarp();
+    lo = hi;
+    return too_big;
+}
+
+// Warp: sum over the boundary bonds of the grown cluster of (the neighbour is
+// parallel ? -1 : +1), i.e. dE_bond / 2 of flipping it (every lane gets it).
+template <int DIM>
+__device__ __forceinline__ int win_boundary(const StepParams &p, const uint32_t *members,
+                                            const uint32_t *hset, uint32_t hslots, uint32_t n,
+                                            uint32_t sig0bit, uint32_t lane) {
+    int dE = 0;
+    for (uint32_t k = lane; k < n; k += 32) {
+        uint32_t i;
+        Neighbours<DIM> nb2;
+        neighbours<DIM>(p.g, members[k], &i, nb2);
+#pragma unroll
+        for (int s = 0; s < 2 * DIM; ++s) {
+            if (burst_contains(hset, hslots, nb2.idx[s])) continue;
+            const uint32_t cur = __ldca(p.spins + nb2.idx[s]) & 1u;
+            dE += (cur == sig0bit) ? -1 : 1;
         }
-        if (j < cut && p.records) {
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dE += __shfl_xor_sync(kFullMask, dE, o);
+    return dE;
+}
+
+// Lowest update index below `below` that flips a site of the closed
+// neighbourhood of the member `packed` (kNone if none).  The flips of the
+// finished updates are stamped into the cluster-list array, which window mode
+// uses as a site-indexed map: list[i] = lowest finished update that flips i.
+template <int DIM>
+__device__ __forceinline__ uint32_t read_conflict(const StepParams &p, uint32_t packed,
+                                                  uint32_t below) {
+    uint32_t i;
+    Neighbours<DIM> nb2;
+    neighbours<DIM>(p.g, packed, &i, nb2);
+    uint32_t v[2 * DIM + 1];
+    v[0] = __ldcg(p.list + i);
+#pragma unroll
+    for (int s = 0; s < 2 * DIM; ++s) v[s + 1] = __ldcg(p.list + nb2.idx[s]);
+    uint32_t best = kNone;
+#pragma unroll
+    for (int q = 0; q < 2 * DIM + 1; ++q)
+        if (v[q] < below && v[q] < best) best = v[q];
+    return best;
+}
+
+// Block: inclusive scan of three 64-bit sums (blockDim.x <= 512); also
+// returns the block totals.
+__device__ __forceinline__ void block_scan3(TeamShared &sh, long long &a, long long &b,
+                                            long long &c, long long tot[3]) {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long ya = __shfl_up_sync(kFullMask, a, o);
+        const long long yb = __shfl_up_sync(kFullMask, b, o);
+        const long long yc = __shfl_up_sync(kFullMask, c, o);
+        if (lane >= (uint32_t)o) {
+            a += ya;
+            b += yb;
+            c += yc;
+        }
+    }
+    if (lane == 31) {
+        sh.wsum[0][warp] = a;
+        sh.wsum[1][warp] = b;
+        sh.wsum[2][warp] = c;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        long long x[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) x[q] = lane < nw ? sh.wsum[q][lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const long long y = __shfl_up_sync(kFullMask, x[q], o);
+                if (lane >= (uint32_t)o) x[q] += y;
+            }
+        }
+        if (lane < nw) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) sh.wsum[q][lane] = x[q];
+        }
+    }
+    __syncthreads();
+    if (warp > 0) {
+        a += sh.wsum[0][warp - 1];
+        b += sh.wsum[1][warp - 1];
+        c += sh.wsum[2][warp - 1];
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) tot[q] = sh.wsum[q][nw - 1];
+    __syncthreads();
+}
+
+// Leader CTA: records of the committed updates [c, cut) (relative to u0),
+// E_bond and M by a scan of their steps; advances the chain state held by
+// thread 0.  Reads the per-slot results of their CTAs remotely.
+__device__ void win_records(const StepParams &p, TeamShared &sh, cg::cluster_group &cl,
+                            const WinView &v, uint32_t S, uint32_t cs, unsigned long long u0,
+                            uint32_t c, uint32_t cut, long long &E, long long &M,
+                            unsigned long long &total_C, uint32_t &last_C,
+                            uint32_t &last_levels) {
+    if (threadIdx.x == 0) {
+        sh.wbase[0] = E;
+        sh.wbase[1] = M;
+        sh.wbase[2] = (long long)total_C;
+    }
+    __syncthreads();
+    for (uint32_t base = c; base < cut; base += blockDim.x) {
+        const uint32_t j = base + threadIdx.x;
+        const bool valid = j < cut;
+        uint4 m = make_uint4(0, 0, 0, 0);
+        if (valid) m = cl.map_shared_rank(v.meta, j % cs)[(j / cs) & (S - 1)];
+        const uint32_t n = m.x, lev = m.y, sig = m.w;
+        const int dE = (int)m.z;
+        long long de = valid ? 2LL * dE : 0;
+        long long dm = valid ? (sig ? -2LL : 2LL) * (long long)n : 0;
+        long long dc = valid ? (long long)n : 0;
+        long long tot[3];
+        const long long e0 = sh.wbase[0], m0 = sh.wbase[1];
+        block_scan3(sh, de, dm, dc, tot);
+        if (valid && p.records) {
             wolff_record r;
-            r.C = (uint32_t)res[0];
-            r.levels = (uint32_t)res[1];
-            r.E_bond = s_base[0] + s_e[j];
-            r.M = s_base[1] + s_m[j];
+            r.C = n;
+            r.levels = lev;
+            r.E_bond = e0 + de;
+            r.M = m0 + dm;
             p.records[u0 + j] = r;
         }
         if (j == cut - 1) {
-            s_base[0] += s_e[j];
-            s_base[1] += s_m[j];
-            s_c[511] = s_c[j];
-            s_e[511] = res[0];
-            s_m[511] = res[1];
+            sh.wlast[0] = n;
+            sh.wlast[1] = lev;
         }
         __syncthreads();
-        if (j == 0) {
-            E = s_base[0];
-            M = s_base[1];
-            total_C += s_c[511];
-            last_C = (uint32_t)s_e[511];
-            last_levels = (uint32_t)s_m[511];
+        if (threadIdx.x == 0) {
+            sh.wbase[0] += tot[0];
+            sh.wbase[1] += tot[1];
+            sh.wbase[2] += tot[2];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        E = sh.wbase[0];
+        M = sh.wbase[1];
+        total_C = (unsigned long long)sh.wbase[2];
+        last_C = sh.wlast[0];
+        last_levels = sh.wlast[1];
+    }
+}
+
+// All CTAs of the team: window mode over updates u0 .. u0 + n_rem - 1 of the
+// launch (see the comment at kWinCap).  Returns how many updates it
+// committed; the leader's thread 0 holds the advanced chain state.  The
+// leader sets wcut = min(n_rem, P), wlimit = kNone and wstop = 0 before the
+// phase starts.  The cluster list is the flipped-site map: every slot holds
+// kEmptySlot on entry, and again when this returns.
+template <int DIM>
+__device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster_group &cl,
+                                const WinCfg &wc, unsigned long long u0, uint32_t n_rem,
+                                unsigned long long launch_t0, long long &E, long long &M,
+                                unsigned long long &total_C, uint32_t &last_C,
+                                uint32_t &last_levels, unsigned long long &rounds,
+                                unsigned long long *win_ns, uint32_t c_start, bool resume,
+                                bool &resumable) {
+    extern __shared__ __align__(16) uint32_t win_dyn[];
+    const uint32_t rank = cl.block_rank(), cs = cl.num_blocks();
+    const uint32_t W = min((uint32_t)(blockDim.x >> 5), (uint32_t)kWinMaxWarps);
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t S = wc.slots, cap = wc.cap, hslots = 2 * cap, K = p.burst;
+    const uint32_t P = S * cs;
+    TeamShared *lead = cl.map_shared_rank(&sh, 0);
+    uint32_t *hset = &sh.front[0][0] + (warp % kWinMaxWarps) * hslots;
+    const WinView v = win_view(win_dyn, S, cap);
+    uint32_t c = resume ? c_start : 0;
+    if (!resume) {
+        for (uint32_t k = threadIdx.x; k < S; k += blockDim.x) v.state[k] = kSlotFree;
+        if (threadIdx.x == 0) {
+            v.scal[kScNextQ] = 0;
+            v.scal[kScRgCount] = 0;
+            v.scal[kScRgTake] = 0;
+        }
+    } else {
+        // the window was left for an update too big for it, which has since
+        // run the ordinary way: a finished update whose read set (members and
+        // their neighbours) changed grows again, the others keep their
+        // clusters
+        for (uint32_t k = threadIdx.x; k < S; k += blockDim.x) v.cmin[k] = kNone;
+        if (warp == 0) win_flatten(v, S, lane);
+        __syncthreads();
+        const uint32_t total = v.off[S];
+        for (uint32_t f = threadIdx.x; f < total; f += blockDim.x) {
+            const uint32_t s = flat_slot(v.off, S, f);
+            const uint32_t k = s * cap + (f - v.off[s]);
+            const uint32_t sig = v.meta[s].w;
+            uint32_t i;
+            Neighbours<DIM> nb2;
+            neighbours<DIM>(p.g, v.members[k], &i, nb2);
+            uint32_t par = 0;
+#pragma unroll
+            for (int q = 0; q < 2 * DIM; ++q)
+                par |= (uint32_t)((__ldcg(p.spins + nb2.idx[q]) & 1u) == sig) << q;
+            if ((__ldcg(p.spins + i) & 1u) != sig || par != v.amask[k]) v.cmin[s] = 0;
+        }
+        __syncthreads();
+        for (uint32_t k = threadIdx.x; k < S; k += blockDim.x)
+            if (v.state[k] == kSlotDone && v.cmin[k] != kNone) v.state[k] = kSlotRegrow;
+        __syncthreads();
+        if (warp == 0) win_queue(v, S, c, rank, cs, lane);
+    }
+    if (threadIdx.x == 0) v.off[S] = 0;   // no stamps to clear before the first round
+    __syncthreads();
+    // this warp's update in progress (registers, kept across rounds)
+    bool have = false, restart = false;
+    uint32_t g_slot = 0, g_j = 0, g_lo = 0, g_n = 0, g_levels = 0, g_sig = 0;
+    const bool timer = win_ns != nullptr && rank == 0 && threadIdx.x == 0;
+    unsigned long long tick = timer ? global_ns() : 0;
+    uint32_t stall = 0;
+    resumable = false;
+    while (true) {
+        const uint32_t lim = min(n_rem, c + P);
+        // ---- clear the previous round's stamps (every read of them ended at
+        // the last cluster barrier; the slots keep their members until taken)
+        {
+            const uint32_t total = v.off[S];
+            for (uint32_t f = threadIdx.x; f < total; f += blockDim.x) {
+                const uint32_t s = flat_slot(v.off, S, f);
+                uint32_t cc[DIM];
+                unpack<DIM>(v.members[s * cap + (f - v.off[s])], cc);
+                p.list[site_index<DIM>(p.g, cc)] = kEmptySlot;
+            }
+        }
+        // ---- growth: K levels per warp; fresh updates stop at the first
+        // one found too big
+        if (threadIdx.x == 0) {
+            const uint32_t wl = ld_volatile_u32(&lead->wlimit);
+            const uint32_t l2 = min(lim, wl);
+            v.scal[kScQEnd] = l2 > rank ? (l2 - rank + cs - 1) / cs : 0;
+            v.scal[kScMin] = kNone;
+            if (rank == 0) sh.wcut = lim;
+        }
+        __syncthreads();
+        if (warp < W) {
+            uint32_t steps = 0;
+            while (steps < K) {
+                if (!have) {
+                    uint32_t took = kNone;
+                    if (lane == 0) {
+                        const uint32_t r = atomicAdd(&v.scal[kScRgTake], 1u);
+                        if (r < v.scal[kScRgCount]) {
+                            took = v.rg[r];
+                        } else {
+                            // the next fresh update, if below the window's
+                            // end (never handed out twice: next_q only grows)
+                            const uint32_t q_end = v.scal[kScQEnd];
+                            uint32_t q = ld_volatile_u32(&v.scal[kScNextQ]);
+                            while (q < q_end) {
+                                const uint32_t prev = atomicCAS(&v.scal[kScNextQ], q, q + 1);
+                                if (prev == q) {
+                                    took = q & (S - 1);
+                                    v.j[took] = q * cs + rank;
+                                    break;
+                                }
+                                q = prev;
+                            }
+                        }
+                        if (took != kNone) v.state[took] = kSlotGrowing;
+                    }
+                    took = __shfl_sync(kFullMask, took, 0);
+                    if (took == kNone) break;
+                    __syncwarp();
+                    g_slot = took;
+                    g_j = v.j[took];
+                    have = true;
+                    restart = true;
+                }
+                const unsigned long long t = p.t0 + u0 + g_j;
+                uint32_t *members = v.members + g_slot * cap;
+                if (restart) {
+                    win_start<DIM>(p, t, members, hset, hslots, lane, g_n, g_lo, g_levels, g_sig);
+                    restart = false;
+                }
+                const bool big =
+                    win_level<DIM>(p, members, v.amask + g_slot * cap, hset, hslots, cap, lane,
+                                   g_lo, g_n, g_sig, (uint32_t)t, (uint32_t)(t >> 32));
+                ++g_levels;
+                ++steps;
+                if (big) {
+                    if (lane == 0) {
+                        v.state[g_slot] = kSlotTooBig;
+                        atomicMin(&lead->wlimit, g_j);
+                    }
+                    have = false;
+                } else if (g_lo == g_n) {
+                    const int dE = win_boundary<DIM>(p, members, hset, hslots, g_n, g_sig, lane);
+                    if (lane == 0) {
+                        v.meta[g_slot] = make_uint4(g_n, g_levels, (uint32_t)dE, g_sig);
+                        v.state[g_slot] = kSlotDone;
+                    }
+                    have = false;
+                    ++steps;
+                }
+            }
+            if (lane == 0 && steps) atomicAdd(&lead->wlevels, (unsigned long long)steps);
+        }
+        __syncthreads();
+        // ---- flatten this CTA's finished updates: off[s] = members before slot s
+        if (warp == 0) win_flatten(v, S, lane);
+        for (uint32_t k = threadIdx.x; k < S; k += blockDim.x) v.cmin[k] = kNone;
+        cl.sync();   // every stamp is clear, every CTA has grown and flattened
+        if (timer) win_tick(win_ns[0], tick);
+        // ---- stamp the flips of the finished updates: list[i] = lowest one
+        const uint32_t total = v.off[S];
+        for (uint32_t f = threadIdx.x; f < total; f += blockDim.x) {
+            const uint32_t s = flat_slot(v.off, S, f);
+            uint32_t cc[DIM];
+            unpack<DIM>(v.members[s * cap + (f - v.off[s])], cc);
+            atomicMin(p.list + site_index<DIM>(p.g, cc), v.j[s]);
+        }
+        cl.sync();
+        if (timer) win_tick(win_ns[1], tick);
+        // ---- conflicts: lowest earlier update flipping a site each one read
+        for (uint32_t f = threadIdx.x; f < total; f += blockDim.x) {
+            const uint32_t s = flat_slot(v.off, S, f);
+            const uint32_t jj = v.j[s];
+            const uint32_t best = read_conflict<DIM>(p, v.members[s * cap + (f - v.off[s])], jj);
+            if (best != kNone) atomicMin(&v.cmin[s], best);
+        }
+        __syncthreads();
+        {
+            // the lowest update of this CTA in [c, lim) that cannot commit
+            const uint32_t qlo = c > rank ? (c - rank + cs - 1) / cs : 0;
+            uint32_t blk = kNone;
+            for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) {
+                const uint32_t q = qlo + ((s - qlo) & (S - 1));
+                const uint32_t jj = q * cs + rank;
+                if (jj < lim) {
+                    const bool ok =
+                        v.state[s] == kSlotDone && v.j[s] == jj && v.cmin[s] == kNone;
+                    if (!ok) blk = min(blk, jj);
+                }
+            }
+            blk = __reduce_min_sync(kFullMask, blk);
+            if (lane == 0 && blk != kNone) atomicMin(&v.scal[kScMin], blk);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (v.scal[kScMin] != kNone) atomicMin(&lead->wcut, v.scal[kScMin]);
+            if (rank == 0 && p.budget_ns)
+                sh.wstop = (global_ns() - launch_t0 > p.budget_ns) ? 1u : 0u;
+        }
+        cl.sync();
+        if (timer) win_tick(win_ns[2], tick);
+        const uint32_t cut = ld_volatile_u32(&lead->wcut);
+        const uint32_t wl = ld_volatile_u32(&lead->wlimit);
+        const uint32_t stop = ld_volatile_u32(&lead->wstop);
+        // ---- commit [c, cut): flip the members (both bits), write records
+        for (uint32_t f = threadIdx.x; f < total; f += blockDim.x) {
+            const uint32_t s = flat_slot(v.off, S, f);
+            if (v.j[s] < cut) {
+                uint32_t cc[DIM];
+                unpack<DIM>(v.members[s * cap + (f - v.off[s])], cc);
+                p.spins[site_index<DIM>(p.g, cc)] = v.meta[s].w ? 0x00 : 0x03;
+            }
+        }
+        if (rank == 0 && cut > c)
+            win_records(p, sh, cl, v, S, cs, u0, c, cut, E, M, total_C, last_C, last_levels);
+        // the committed slots are free; a finished update that read a
+        // committed flip grows again
+        for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) {
+            if (v.state[s] == kSlotDone) {
+                if (v.j[s] < cut) v.state[s] = kSlotFree;
+                else if (v.cmin[s] < cut) v.state[s] = kSlotRegrow;
+            }
+        }
+        // an update still growing that read a committed flip starts again
+        if (warp < W && have && !restart && cut > c) {
+            bool hit = false;
+            const uint32_t *members = v.members + g_slot * cap;
+            for (uint32_t k = lane; k < g_n && k < cap; k += 32)
+                if (read_conflict<DIM>(p, members[k], cut) != kNone) hit = true;
+            if (__any_sync(kFullMask, hit)) restart = true;
+        }
+        __syncthreads();
+        if (warp == 0) win_queue(v, S, cut, rank, cs, lane);
+        ++rounds;
+        // the update at the cut finishes within cap / K rounds of its last
+        // (re)start, and nothing restarts the lowest uncommitted update
+        // twice; a window that stops advancing anyway hands it over and
+        // reports the fault
+        stall = cut == c ? stall + 1 : 0;
+        const bool stuck = stall > kWinMaxStall;
+        if (stuck && rank == 0 && threadIdx.x == 0) raise_status(p.ctl, WOLFF_EINVAL, 0xD4u);
+        const bool finished = cut >= n_rem;
+        const bool blocked = !finished && (cut == wl || stuck);
+        const bool stopped = stop != 0 && u0 + cut > 0;
+        cl.sync();   // commits visible, every read of the stamps done
+        if (timer) win_tick(win_ns[3], tick);
+        c = cut;
+        if (finished || blocked || stopped) {
+            resumable = blocked && !stuck && !stopped;
+            break;
         }
     }
-    cl.sync();   // results read and commits done before anything is reused
-    return cut;
+    if (resumable) {
+        // the update at the cut runs the ordinary way; the window keeps its
+        // finished updates and regrows the rest when it resumes
+        if (warp < W && have && lane == 0) v.state[g_slot] = kSlotRegrow;
+        __syncthreads();
+        for (uint32_t k = threadIdx.x; k < S; k += blockDim.x)
+            if (v.state[k] == kSlotTooBig) v.state[k] = v.j[k] == c ? kSlotFree : kSlotRegrow;
+    }
+    // leave the cluster list empty, and ordered before whatever uses it next
+    {
+        const uint32_t total = v.off[S];
+        for (uint32_t f = threadIdx.x; f < total; f += blockDim.x) {
+            const uint32_t s = flat_slot(v.off, S, f);
+            uint32_t cc[DIM];
+            unpack<DIM>(v.members[s * cap + (f - v.off[s])], cc);
+            p.list[site_index<DIM>(p.g, cc)] = kEmptySlot;
+        }
+    }
+    cl.sync();
+    if (timer) win_ns[4] += sh.wlevels;
+    return c;
 }
 
 // Leader: announce a team phase, then start it with the cluster barrier.
@@ -478,7 +846,8 @@ __device__ __forceinline__ void announce(TeamShared &sh, cg::cluster_group &cl, 
 }
 
 template <int DIM>
-__device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_group &cl) {
+__device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_group &cl,
+                            const WinCfg &wc) {
     DevCtl *ctl = p.ctl;
     const bool t0 = threadIdx.x == 0;
     const bool has_team = cl.num_blocks() > 1;
@@ -498,10 +867,16 @@ __device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_gro
         last_levels = ctl->last_levels;
         sh.dE = 0;
     }
-    // burst policy (thread 0 decides, the CTA follows): bursts run while the
-    // recent clusters are small; a cluster too big for a burst pauses them
+    // window policy (thread 0 decides, the CTA follows): windows run while the
+    // recent clusters are small; a cluster too big for one pauses them
     unsigned int cooldown = 0, fail_streak = 0, skip_next = 0;
     unsigned long long bursts_done = 0, burst_calls = 0;
+    unsigned long long win_ns[5] = {0, 0, 0, 0, 0};
+    // an open window (left for an update too big for it) resumes at
+    // update win_u0 + win_next
+    bool win_open = false;
+    unsigned long long win_u0 = 0;
+    uint32_t win_nrem = 0, win_next = 0;
     const unsigned long long launch_t0 = global_ns();
     unsigned long long u = 0;
     for (; u < p.n; ++u) {
@@ -510,40 +885,52 @@ __device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_gro
             __syncthreads();
             if (sh.bstop) break;
         }
-        if (p.burst && p.n - u >= 2) {
-            // a burst cut short by an update too big for it leaves that update
-            // to the ordinary path directly
-            if (t0) sh.bflag = (cooldown == 0 && !skip_next) ? 1u : 0u;
+        if (p.burst && wc.slots && p.n - u >= 2) {
+            // a window stopped by an update too big for it leaves that update
+            // to the ordinary path directly, then resumes with what it holds
+            const bool resume = win_open && u == win_u0 + win_next;
+            if (t0) sh.bflag = (resume || (cooldown == 0 && !skip_next)) ? 1u : 0u;
             __syncthreads();
             if (sh.bflag) {
-                const uint32_t W = min((uint32_t)(blockDim.x >> 5), (uint32_t)kBurstMaxWarps);
-                const uint32_t nb =
-                    (uint32_t)min((unsigned long long)(W * cl.num_blocks()), p.n - u);
-                if (t0) sh.bcut = nb;
+                const unsigned long long u0w = resume ? win_u0 : u;
+                const uint32_t n_rem =
+                    resume ? win_nrem : (uint32_t)min(p.n - u, 0x7FFFFFFFull);
+                const uint32_t c_start = resume ? win_next : 0;
+                if (t0) {
+                    sh.wlimit = kNone;
+                    sh.wstop = 0;
+                    sh.wlevels = 0;
+                }
                 if (has_team)
-                    announce(sh, cl, kTeamBurst, (uint32_t)u, (uint32_t)(u >> 32), nb, 0, 0);
+                    announce(sh, cl, kTeamBurst, (uint32_t)u0w, (uint32_t)(u0w >> 32), n_rem,
+                             resume ? 1u : 0u, c_start);
                 else
                     __syncthreads();
-                const uint32_t c = team_burst<DIM>(p, sh, cl, u, nb, E, M, total_C, last_C,
-                                                   last_levels);
+                bool resumable = false;
+                const uint32_t c =
+                    team_window<DIM>(p, sh, cl, wc, u0w, n_rem, launch_t0, E, M, total_C, last_C,
+                                     last_levels, burst_calls, win_ns, c_start, resume,
+                                     resumable);
+                const uint32_t done = c - c_start;
+                // a resumed window that commits nothing is closed
+                win_open = resumable && !(resume && done == 0);
+                win_u0 = u0w;
+                win_nrem = n_rem;
+                win_next = c + 1;
                 if (t0) {
-                    bursts_done += c;
-                    ++burst_calls;
-                    if (c > 0 && c < nb) {
-                        const TeamShared *src = cl.map_shared_rank(&sh, c / W);
-                        skip_next = src->bres[c % W][0] < 0 ? 1u : 0u;
-                    }
-                    // back off only while bursts keep failing at their first
-                    // update (the large-cluster regime): 0, 1, 3, ..., 63
-                    if (c == 0) {
+                    bursts_done += done;
+                    if (done > 0 && c < n_rem && !sh.wstop) skip_next = 1;
+                    // back off only while fresh windows keep failing at their
+                    // first update (the large-cluster regime): 0, 1, 3, ..., 63
+                    if (done == 0 && !resume) {
                         fail_streak = min(fail_streak + 1u, 7u);
                         cooldown = (1u << (fail_streak - 1u)) - 1u;
-                    } else {
+                    } else if (done > 0) {
                         fail_streak = 0;
                     }
                 }
-                if (c > 0) {
-                    u += c - 1;
+                if (done > 0) {
+                    u = u0w + c - 1;
                     continue;
                 }
             } else if (t0) {
@@ -696,6 +1083,8 @@ __device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_gro
         ctl->st_grid_finishes += team_fin;
         ctl->st_burst_updates += bursts_done;
         ctl->st_bursts += burst_calls;
+        for (int k = 0; k < 4; ++k) ctl->st_ns_win[k] += win_ns[k];
+        ctl->st_win_levels += win_ns[4];
         ctl->st_end_ns = global_ns();
     }
     if (has_team) {
@@ -705,16 +1094,17 @@ __device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_gro
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(512, 1) k_team(StepParams single, const StepParams *table) {
+__global__ void __launch_bounds__(512, 1) k_team(StepParams single, const StepParams *table,
+                                                 WinCfg wc) {
     cg::cluster_group cl = cg::this_cluster();
     __shared__ TeamShared sh;
     const unsigned int job = blockIdx.x / cl.num_blocks();
     const StepParams p = table ? table[job] : single;
     if (cl.block_rank() != 0) {
-        team_worker<DIM>(p, sh, cl);
+        team_worker<DIM>(p, sh, cl, wc);
         return;
     }
-    team_leader<DIM>(p, sh, cl);
+    team_leader<DIM>(p, sh, cl, wc);
 }
 
 }  // namespace
@@ -724,18 +1114,40 @@ const void *team_kernel(int dim) {
                     : reinterpret_cast<const void *>(&k_team<3>);
 }
 
+size_t window_smem_bytes(int threads, int window_slots) {
+    if (window_slots <= 0) return 0;
+    const uint32_t W = min((uint32_t)threads / 32u, (uint32_t)kWinMaxWarps);
+    const uint32_t cap = W <= 8 ? 2 * kWinCap : kWinCap;
+    const size_t S = (size_t)window_slots;
+    return (S * cap + 9 * S + 1 + kWinScalars) * sizeof(uint32_t) + S * cap;
+}
+
 cudaError_t launch_team(int dim, const StepParams &single, const StepParams *d_table, int njobs,
-                        int cluster_size, int threads, cudaStream_t s) {
+                        int cluster_size, int threads, int window_slots, cudaStream_t s) {
     if (njobs <= 0) return cudaSuccess;
+    if (window_slots < 0 || (window_slots & (window_slots - 1)) != 0 || window_slots > 1024)
+        return cudaErrorInvalidValue;
     const void *fn = team_kernel(dim);
     if (cluster_size > 8) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
     }
+    WinCfg wc;
+    wc.slots = (uint32_t)window_slots;
+    {
+        const uint32_t W = min((uint32_t)threads / 32u, (uint32_t)kWinMaxWarps);
+        wc.cap = W <= 8 ? 2 * kWinCap : kWinCap;
+    }
+    const size_t dyn = window_smem_bytes(threads, window_slots);
+    if (dyn > 0) {
+        cudaError_t e =
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) return e;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(njobs * cluster_size));
     cfg.blockDim = dim3((unsigned)threads);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = dyn;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -744,7 +1156,7 @@ cudaError_t launch_team(int dim, const StepParams &single, const StepParams *d_t
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    void *args[] = {const_cast<StepParams *>(&single), const_cast<StepParams **>(&d_table)};
+    void *args[] = {const_cast<StepParams *>(&single), const_cast<StepParams **>(&d_table), &wc};
     return cudaLaunchKernelExC(&cfg, fn, args);
 }
 

@@ -312,6 +312,51 @@ def test_burst_mode_matches_oracle(dim, L, T, n):
             assert st["burst_updates"] > n // 2
 
 
+@pytest.mark.parametrize("dim,L,T,n", [(2, 32, 5.0, 1500), (2, 20, 3.2, 1200),
+                                       (3, 8, 9.0, 1200), (3, 12, 6.0, 800)])
+@pytest.mark.parametrize("levels,cs,threads", [(1, 16, 512), (2, 4, 256), (3, 1, 128),
+                                               (6, 2, 512)])
+def test_window_rounds_and_regrowth(dim, L, T, n, levels, cs, threads):
+    """Window mode on small hot lattices, where the updates of a window often
+    read each other's flips: short rounds (1-3 growth levels) make updates
+    span several commits, so finished and half-grown updates are grown again,
+    and the chain must still be the serial one, lattice included."""
+    torch, w = require_cuda()
+    seed = 900 + L + levels
+    ref, s_ref = oracle_trajectory(dim, L, T, seed, n)
+    check_run_window(w, dim, L, T, n, levels, cs, threads, seed, ref, s_ref)
+
+
+@pytest.mark.parametrize("dim,L,T,n", [(2, 96, 2.5, 1500), (3, 20, 4.8, 1200)])
+@pytest.mark.parametrize("levels,cs,threads", [(4, 16, 512), (32, 4, 256), (64, 1, 512)])
+def test_window_resumes_after_oversized_update(dim, L, T, n, levels, cs, threads):
+    """Near T_c some clusters outgrow a window update's member cap (64 at 512
+    threads, 128 at 256).  The window then hands that update to the ordinary
+    path and resumes with the updates it had finished, each revalidated
+    against the lattice the big flip left; the chain must stay the serial one."""
+    torch, w = require_cuda()
+    seed = 4200 + L + levels
+    ref, s_ref = oracle_trajectory(dim, L, T, seed, n)
+    cap = 64 if threads > 256 else 128
+    assert int((ref["C"] > cap).sum()) >= 3   # the resume path is exercised
+    check_run_window(w, dim, L, T, n, levels, cs, threads, seed, ref, s_ref)
+
+
+def check_run_window(w, dim, L, T, n, levels, cs, threads, seed, ref, s_ref):
+    lat = w.WolffLattice(dim, L, T, seed=seed, schedule=w.SCHED_CLUSTER, grid_blocks=cs,
+                         block_threads=threads)
+    lat.set_burst(levels)
+    rec = np.concatenate([lat.step(k) for k in (n // 3, n - n // 3)])
+    st = lat.stats()
+    spins, t = lat.get_state()
+    assert lat.measure()[:2] == lat.measure_full()
+    lat.close()
+    tag = "window %dD L=%d T=%g levels %d cs %d threads %d" % (dim, L, T, levels, cs, threads)
+    assert_records_equal(rec, ref, tag)
+    assert t == n and np.array_equal(spins, s_ref)
+    assert st["burst_updates"] > n // 4, (tag, st)
+
+
 @pytest.mark.parametrize("dim,L,T,seed,equil,sample", [(2, 4096, TC2, 2, 2000, 40),
                                                       (3, 256, 4.5115, 3, 2000, 8)])
 def test_full_size_in_bench_configuration(dim, L, T, seed, equil, sample):

@@ -43,7 +43,7 @@ TC2 = 2.0 / math.log(1.0 + math.sqrt(2.0))
 # committed ncu capture (profiles/k_team_2d_L4096_random_start.md), valid only
 # while the kernel sources hash to the captured value.
 TRAFFIC_CAPTURES = {
-    ("2d", 1000): {"src": "d471d1d61b18", "bytes_per_launch": 676608 + 0},
+    ("2d", 1000): {"src": "a82fc47d1cc9", "bytes_per_launch": 1327104 + 0},
 }
 
 

@@ -64,6 +64,27 @@ def _load():
     lib.orc_potts_enumerate.restype = i32
     lib.orc_potts_threshold.argtypes = [ctypes.c_double, ctypes.c_double]
     lib.orc_potts_threshold.restype = u64
+    f64 = ctypes.c_double
+    lib.orc_xy_table.argtypes = [p]
+    lib.orc_xy_table.restype = None
+    lib.orc_xy_cos_at.argtypes = [u32]
+    lib.orc_xy_cos_at.restype = ctypes.c_int32
+    lib.orc_xy_exp_neg.argtypes = [f64]
+    lib.orc_xy_exp_neg.restype = f64
+    lib.orc_xy_coupling.argtypes = [f64, f64]
+    lib.orc_xy_coupling.restype = f64
+    lib.orc_xy_threshold.argtypes = [i64, f64]
+    lib.orc_xy_threshold.restype = u64
+    lib.orc_xy_init.argtypes = [i32, u32, i32, u64, p]
+    lib.orc_xy_init.restype = None
+    lib.orc_xy_observables.argtypes = [i32, u32, p, p]
+    lib.orc_xy_observables.restype = None
+    lib.orc_xy_phi.argtypes = [u64, u64, i32]
+    lib.orc_xy_phi.restype = u32
+    lib.orc_xy_cluster.argtypes = [i32, u32, i32, f64, u64, u64, p, p, p, p, p]
+    lib.orc_xy_cluster.restype = u32
+    lib.orc_xy_run.argtypes = [i32, u32, i32, f64, u64, u64, u64, p, p]
+    lib.orc_xy_run.restype = i32
     _lib = lib
     return lib
 
@@ -268,3 +289,80 @@ def potts_exact_moments(dim, L, q, J, T, g=None):
     return {"E": float((pe * Ef).sum()), "N0": float((pz * Zf).sum()),
             "N0_2": float((pz * Zf ** 2).sum()), "P": P}
 
+
+
+# ---- XY model (embedded-cluster Wolff update, the extension section 6 names) ----
+
+XY_RECORD_DTYPE = np.dtype([("C", "<u4"), ("levels", "<u4"), ("E", "<i8"),
+                            ("Mx", "<i8"), ("My", "<i8")])
+XY_ONE = 1 << 30          # fixed-point unit of the cosine table
+XY_ANGLE_BITS = 15        # production angle resolution (units of 2 pi / 65536)
+
+
+def xy_table():
+    """I[k] = round(cos(pi k / 32768) 2^30), k = 0..16384."""
+    t = np.zeros(16385, dtype=np.int32)
+    _load().orc_xy_table(_ptr(t))
+    return t
+
+
+def xy_cos(a):
+    """Fixed-point cos of angle a (units of 2 pi / 65536)."""
+    return int(_load().orc_xy_cos_at(int(a) & 0xFFFF))
+
+
+def xy_exp_neg(y):
+    return float(_load().orc_xy_exp_neg(float(y)))
+
+
+def xy_coupling(J, T):
+    """2 J / T * 2^-60: y = coupling * (product of two fixed-point projections)."""
+    return float(_load().orc_xy_coupling(float(J), float(T)))
+
+
+def xy_threshold(prod, kk):
+    """floor(2^32 (1 - exp(-kk prod))) for prod > 0, else 0."""
+    return int(_load().orc_xy_threshold(int(prod), float(kk)))
+
+
+def xy_init(dim, L, bits, seed):
+    th = np.zeros(n_sites(dim, L), dtype=np.uint16)
+    _load().orc_xy_init(dim, L, bits, seed, _ptr(th))
+    return th
+
+
+def xy_observables(dim, L, theta):
+    """(E_fix, Mx, My) by their definitions."""
+    theta = np.ascontiguousarray(theta, dtype=np.uint16)
+    out = np.zeros(3, dtype=np.int64)
+    _load().orc_xy_observables(dim, L, _ptr(theta), _ptr(out))
+    return int(out[0]), int(out[1]), int(out[2])
+
+
+def xy_phi(seed, t, bits):
+    return int(_load().orc_xy_phi(seed, t, bits))
+
+
+def xy_cluster(dim, L, bits, kk, seed, t, theta):
+    """(member bool array, list, levels, phi) of XY update t on theta."""
+    theta = np.ascontiguousarray(theta, dtype=np.uint16)
+    n = n_sites(dim, L)
+    member = np.zeros(n, dtype=np.uint8)
+    lst = np.zeros(n, dtype=np.uint32)
+    levels = np.zeros(1, dtype=np.uint32)
+    phi = np.zeros(1, dtype=np.uint32)
+    k = _load().orc_xy_cluster(dim, L, bits, kk, seed, t, _ptr(theta), _ptr(member), _ptr(lst),
+                               _ptr(levels), _ptr(phi))
+    return member.astype(bool), lst[:k].copy(), int(levels[0]), int(phi[0])
+
+
+def xy_run(dim, L, bits, kk, seed, t0, n, theta, records=True):
+    """XY updates t0..t0+n-1 on theta (uint16 angles, in place)."""
+    if theta.dtype != np.uint16 or not theta.flags.c_contiguous:
+        raise ValueError("theta must be a contiguous uint16 array")
+    rec = np.zeros(int(n), dtype=XY_RECORD_DTYPE) if records else None
+    rc = _load().orc_xy_run(dim, L, bits, kk, seed, t0, n, _ptr(theta),
+                            _ptr(rec) if rec is not None else None)
+    if rc != 0:
+        raise MemoryError("oracle could not allocate its scratch arrays (or bad angle bits)")
+    return rec

@@ -427,3 +427,213 @@ uint64_t orc_potts_threshold(double J, double T)
     if (p >= 1.0) return (uint64_t)1 << 32;
     return (uint64_t)floor(ldexp(p, 32));
 }
+
+/* ---- XY model (section 6 names it as the next extension) -----------------
+ *
+ * H = -J sum_<ij> cos(theta_i - theta_j).  Wolff's embedded-cluster update
+ * (Wolff, PRL 62 (1989) 361): draw a unit vector r at angle phi and a seed
+ * site; a bond <ij> is active with probability
+ *     p_ij = 1 - exp(-2K (r.s_i)(r.s_j))  when (r.s_i)(r.s_j) > 0, else 0,
+ * K = J/T, judged on the pre-update spins; the cluster is the seed's
+ * connected component of active bonds, and every member is reflected in the
+ * line perpendicular to r: theta -> pi + 2 phi - theta.
+ *
+ * Readings (exact integer arithmetic, so that CPU and GPU agree bit for bit):
+ *   - Angles are integers in units of 2 pi / 65536.  With angle_bits b
+ *     (1..15) spins are multiples of 2^(16-b) and phi a multiple of
+ *     2^(15-b), so the reflection 32768 + 2 phi - theta (mod 65536) stays on
+ *     the grid; b = 15 is the production resolution, small b gives a
+ *     2^b-state clock model whose Boltzmann averages can be enumerated.
+ *   - cos is the fixed-point table I[k] = round(cos(pi k / 32768) 2^30),
+ *     k = 0..16384 (C library cos in double), extended by symmetry.  The
+ *     projection r.s_i is I(theta_i - phi); E_fix = sum_{i,d} I(theta_i -
+ *     theta_nb(i,d)) (energy -J E_fix 2^-30); Mx = sum I(theta_i),
+ *     My = sum I(theta_i - 16384).
+ *   - p_ij: y = (2K 2^-60) * (double)(I_i I_j) and p = 1 - e^-y, with e^-y
+ *     computed by Cody-Waite range reduction (y = k ln2 + r) and the Taylor
+ *     series of e^-r to degree 16 (Cody & Waite, Software Manual for the
+ *     Elementary Functions, 1980) in IEEE double basic operations in a fixed
+ *     order (no contraction), so that any platform following the same steps
+ *     gets the same double; thr = floor(p 2^32) and the bond is active when
+ *     its random word is below thr.
+ *   - Randomness: the seed site as in the Ising update (lane 0 of the seed
+ *     draw), phi from lane 1 of the same draw, the bond words as in the Ising
+ *     update; initial angle of site i from lane 0 of Philox(i, 0, 0, 2). */
+
+typedef struct {
+    uint32_t C;
+    uint32_t levels;
+    int64_t  E;    /* fixed-point bond sum E_fix after the flip */
+    int64_t  Mx;   /* fixed-point magnetisation after the flip */
+    int64_t  My;
+} orc_xy_record;
+
+#define ORC_XY_PI 3.141592653589793
+
+void orc_xy_table(int32_t *tab)
+{
+    for (int k = 0; k <= 16384; ++k)
+        tab[k] = (int32_t)llround(cos(ORC_XY_PI * (double)k / 32768.0) * 1073741824.0);
+}
+
+/* cos of angle a (units 2 pi / 65536) from the quarter-wave table. */
+static int32_t orc_xy_cos(const int32_t *tab, uint32_t a)
+{
+    a &= 0xFFFFu;
+    uint32_t q = a >> 14, r = a & 0x3FFFu;
+    if (q == 0) return tab[r];
+    if (q == 1) return -tab[16384 - r];
+    if (q == 2) return -tab[r];
+    return tab[16384 - r];
+}
+
+int32_t orc_xy_cos_at(uint32_t a)
+{
+    static int32_t tab[16385];
+    static int ready = 0;
+    if (!ready) { orc_xy_table(tab); ready = 1; }
+    return orc_xy_cos(tab, a);
+}
+
+/* e^-y for y >= 0 (see the readings above). */
+double orc_xy_exp_neg(double y)
+{
+    const double inv_ln2 = 0x1.71547652b82fep+0;
+    const double ln2_hi = 0x1.62e42feep-1;      /* ln 2 to 32 significant bits */
+    const double ln2_lo = 0x1.a39ef35793c76p-33; /* ln 2 - ln2_hi */
+    if (!(y < 1000.0)) return 0.0;
+    double coef[17];
+    coef[0] = 1.0;
+    for (int n = 1; n <= 16; ++n) coef[n] = coef[n - 1] / (double)n;
+    double t = y * inv_ln2;
+    double kd = floor(t + 0.5);
+    double r = (y - kd * ln2_hi) - kd * ln2_lo;
+    double m = -r;
+    double s = coef[16];
+    for (int n = 15; n >= 0; --n) s = s * m + coef[n];
+    return ldexp(s, -(int)kd);
+}
+
+/* 2K 2^-60, the factor that turns a product of two projections into y. */
+double orc_xy_coupling(double J, double T)
+{
+    return ldexp(2.0 * J / T, -60);
+}
+
+uint64_t orc_xy_threshold(int64_t prod, double kk)
+{
+    if (prod <= 0) return 0;
+    double y = kk * (double)prod;
+    double p = 1.0 - orc_xy_exp_neg(y);
+    if (!(p > 0.0)) return 0;
+    if (p >= 1.0) return (uint64_t)1 << 32;
+    return (uint64_t)floor(ldexp(p, 32));
+}
+
+void orc_xy_init(int dim, uint32_t L, int bits, uint64_t seed, uint16_t *theta)
+{
+    uint32_t n = orc_sites(dim, L);
+    for (uint32_t i = 0; i < n; ++i) {
+        uint32_t r[4];
+        orc_draw(seed, i, 0, ORC_TAG_INIT, r);
+        theta[i] = (uint16_t)((r[0] >> (32 - bits)) << (16 - bits));
+    }
+}
+
+void orc_xy_observables(int dim, uint32_t L, const uint16_t *theta, int64_t out[3])
+{
+    uint32_t n = orc_sites(dim, L);
+    int64_t e = 0, mx = 0, my = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        for (int d = 0; d < dim; ++d)
+            e += orc_xy_cos_at((uint32_t)theta[i] - theta[orc_neighbour(dim, L, i, d, +1)]);
+        mx += orc_xy_cos_at(theta[i]);
+        my += orc_xy_cos_at((uint32_t)theta[i] + 65536u - 16384u);
+    }
+    out[0] = e;
+    out[1] = mx;
+    out[2] = my;
+}
+
+/* Reflection angle of update t on the grid of angle_bits b. */
+uint32_t orc_xy_phi(uint64_t seed, uint64_t t, int bits)
+{
+    uint32_t r[4];
+    orc_draw(seed, 0, t, ORC_TAG_SEED, r);
+    return (r[1] >> (32 - (bits + 1))) << (15 - bits);
+}
+
+/* Cluster of XY update t on theta (unchanged); member[] zero on entry.
+ * Writes phi.  Returns |C|. */
+uint32_t orc_xy_cluster(int dim, uint32_t L, int bits, double kk, uint64_t seed, uint64_t t,
+                        const uint16_t *theta, uint8_t *member, uint32_t *list, uint32_t *levels,
+                        uint32_t *phi_out)
+{
+    uint32_t n = orc_sites(dim, L);
+    uint32_t r[4];
+    orc_draw(seed, 0, t, ORC_TAG_SEED, r);
+    uint32_t i0 = (uint32_t)(((uint64_t)r[0] * n) >> 32);
+    uint32_t phi = orc_xy_phi(seed, t, bits);
+    if (phi_out) *phi_out = phi;
+    uint32_t ic = 0, in = 0;
+    list[ic++] = i0;
+    member[i0] = 1;
+    uint32_t generation_end = ic, generations = 1;
+    while (in < ic) {
+        if (in == generation_end) {
+            generation_end = ic;
+            ++generations;
+        }
+        uint32_t i = list[in++];
+        int64_t si = orc_xy_cos_at((uint32_t)theta[i] + 65536u - phi);
+        for (int d = 0; d < dim; ++d) {
+            for (int sign = +1; sign >= -1; sign -= 2) {
+                uint32_t j = orc_neighbour(dim, L, i, d, sign);
+                uint32_t owner = sign > 0 ? i : j;
+                if (member[j]) continue;
+                int64_t sj = orc_xy_cos_at((uint32_t)theta[j] + 65536u - phi);
+                uint64_t thr = orc_xy_threshold(si * sj, kk);
+                if ((uint64_t)orc_bond_random(seed, t, owner, d) < thr) {
+                    member[j] = 1;
+                    list[ic++] = j;
+                }
+            }
+        }
+    }
+    if (levels) *levels = generations;
+    return ic;
+}
+
+/* XY updates t0 .. t0+n-1 on theta in place; records (nullable) recounted
+ * from their definitions after every update. */
+int orc_xy_run(int dim, uint32_t L, int bits, double kk, uint64_t seed, uint64_t t0, uint64_t n,
+               uint16_t *theta, orc_xy_record *rec)
+{
+    uint32_t sites = orc_sites(dim, L);
+    if (bits < 1 || bits > 15) return -1;
+    uint8_t *member = (uint8_t *)calloc(sites, 1);
+    uint32_t *list = (uint32_t *)malloc((size_t)sites * sizeof(uint32_t));
+    if (!member || !list) { free(member); free(list); return -1; }
+    for (uint64_t u = 0; u < n; ++u) {
+        uint32_t levels = 0, phi = 0;
+        uint32_t k = orc_xy_cluster(dim, L, bits, kk, seed, t0 + u, theta, member, list, &levels,
+                                    &phi);
+        for (uint32_t m = 0; m < k; ++m) {
+            uint32_t i = list[m];
+            theta[i] = (uint16_t)((32768u + 2u * phi - theta[i]) & 0xFFFFu);
+            member[i] = 0;
+        }
+        if (rec) {
+            int64_t obs[3];
+            orc_xy_observables(dim, L, theta, obs);
+            rec[u].C = k;
+            rec[u].levels = levels;
+            rec[u].E = obs[0];
+            rec[u].Mx = obs[1];
+            rec[u].My = obs[2];
+        }
+    }
+    free(member);
+    free(list);
+    return 0;
+}

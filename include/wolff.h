@@ -150,6 +150,65 @@ wolff_status potts_init(wolff_ctx **out, int dim, int L, int q, double J, double
                         uint64_t seed, void *d_workspace, size_t workspace_bytes,
                         void *stream);
 
+/* ---- XY model (embedded-cluster update) ---------------------------------
+ * The model section 6 of the paper names next: H = -J sum_<ij>
+ * cos(theta_i - theta_j), updated by Wolff's embedded Ising cluster (Wolff,
+ * PRL 62 (1989) 361).  Update t: seed site from lane 0 of the seed draw and
+ * a reflection angle phi from lane 1; a bond <ij> is active with probability
+ * 1 - exp(-2K (r.s_i)(r.s_j)) when (r.s_i)(r.s_j) > 0 (K = J/T, judged on
+ * the pre-update spins, the same bond words as the Ising update); every
+ * member of the seed's component is reflected: theta -> pi + 2 phi - theta.
+ * Exact integer arithmetic, so that results are reproducible bit for bit:
+ *   - angles are integers in units of 2 pi / 65536 on a grid of angle_bits
+ *     (1..15) bits: spins are multiples of 2^(16 - angle_bits) and phi of
+ *     2^(15 - angle_bits) (15 = the finest; small values give 2^bits-state
+ *     clock models);
+ *   - cos is the fixed-point table round(cos(pi k / 32768) 2^30), k =
+ *     0..16384, extended by symmetry; r.s_i = I(theta_i - phi);
+ *   - y = (2K 2^-60) (I_i I_j) in double, p = 1 - e^-y with e^-y from
+ *     Cody-Waite range reduction and a degree-16 Taylor series in a fixed
+ *     sequence of correctly rounded double operations; the bond is active
+ *     when its random word is below floor(p 2^32);
+ *   - initial angle of site i: the top angle_bits bits of lane 0 of
+ *     Philox(i, 0, 0, 2), shifted to the grid.
+ * Records and measurements are fixed point: E = sum_{i,d} I(theta_i -
+ * theta_nb(i,d)) (energy -J E 2^-30), Mx = sum I(theta_i), My = sum
+ * I(theta_i - 16384).  An XY context runs through wolff_step (d_records
+ * receives wolff_xy_record entries), wolff_set_schedule (CLUSTER only),
+ * wolff_get_info, wolff_get_stats and ising_free; the Ising state and
+ * measure entry points, wolff_run_host and the batched form return
+ * WOLFF_EUNSUPPORTED for it. */
+#define WOLFF_XY_ANGLE_BITS 15
+typedef struct {
+    uint32_t C;
+    uint32_t levels;
+    int64_t  E;     /* fixed-point bond sum after the flip */
+    int64_t  Mx;    /* fixed-point magnetisation after the flip */
+    int64_t  My;
+} wolff_xy_record;
+
+/* Bytes of device workspace an XY context of this shape needs (0 if
+ * invalid): 32-bit site words, the cluster list, the cosine table. */
+size_t wolff_xy_workspace_bytes(int dim, int L);
+
+/* As ising_init, for the XY model; angle_bits in 1..15 (EINVAL otherwise). */
+wolff_status xy_init(wolff_ctx **out, int dim, int L, int angle_bits, double J, double T,
+                     uint64_t seed, void *d_workspace, size_t workspace_bytes, void *stream);
+
+/* Incrementally tracked E, Mx, My and the last cluster size (outputs
+ * nullable).  Synchronises; reports latched device errors. */
+wolff_status xy_measure(wolff_ctx *ctx, int64_t *E, int64_t *Mx, int64_t *My,
+                        uint64_t *last_C);
+
+/* The same three sums by a full pass over the lattice.  Synchronises. */
+wolff_status xy_measure_full(wolff_ctx *ctx, int64_t *E, int64_t *Mx, int64_t *My);
+
+/* Checkpoint / restore of the angles (N uint16 entries) and the next update
+ * index.  set_state rejects, with EINVAL, angles off the context's grid and
+ * recomputes E, Mx, My.  Both synchronise. */
+wolff_status xy_get_state(wolff_ctx *ctx, uint16_t *h_theta, uint64_t *t);
+wolff_status xy_set_state(wolff_ctx *ctx, const uint16_t *h_theta, uint64_t t);
+
 /* Enqueues n_updates single-cluster updates (t .. t+n-1), each: seed site,
  * level-synchronous growth with atomic claims and warp-aggregated appends to
  * the cluster list, boundary-bond energy change, unmark, record.  d_records

@@ -25,6 +25,12 @@ SCHED_AUTO, SCHED_PERSISTENT, SCHED_GRAPH, SCHED_CLUSTER = 0, 1, 2, 3
 
 RECORD_DTYPE = np.dtype([("C", "<u4"), ("levels", "<u4"), ("E", "<i8"), ("M", "<i8")])
 RECORD_BYTES = RECORD_DTYPE.itemsize  # 24
+# XY model records: |C|, levels and the fixed-point E, Mx, My (units 2^-30)
+XY_RECORD_DTYPE = np.dtype([("C", "<u4"), ("levels", "<u4"), ("E", "<i8"),
+                            ("Mx", "<i8"), ("My", "<i8")])
+XY_RECORD_BYTES = XY_RECORD_DTYPE.itemsize  # 32
+XY_ANGLE_BITS = 15
+XY_ONE = 1 << 30
 
 TC_2D = 2.0 / math.log(1.0 + math.sqrt(2.0))   # Onsager: T_c/J = 2.2691...
 TC_3D = 4.5115                                  # simple cubic, J = 1
@@ -76,6 +82,12 @@ def load_library():
         "wolff_workspace_bytes": (sz, [i, i, i]),
         "ising_init": (i, [P(v), i, i, d, d, u64, i, v, sz, v]),
         "potts_init": (i, [P(v), i, i, i, d, d, u64, v, sz, v]),
+        "wolff_xy_workspace_bytes": (sz, [i, i]),
+        "xy_init": (i, [P(v), i, i, i, d, d, u64, v, sz, v]),
+        "xy_measure": (i, [v, P(i64), P(i64), P(i64), P(u64)]),
+        "xy_measure_full": (i, [v, P(i64), P(i64), P(i64)]),
+        "xy_get_state": (i, [v, v, P(u64)]),
+        "xy_set_state": (i, [v, v, u64]),
         "wolff_step": (i, [v, u64, v]),
         "wolff_run_host": (i, [v, v, u64, u64, v, v]),
         "measure": (i, [v, P(i64), P(i64), P(u64)]),
@@ -366,3 +378,107 @@ class WolffBatch:
         except Exception:
             pass
 
+
+
+def xy_init(dim, L, angle_bits, J, T, seed, workspace=None, stream=None):
+    """Creates an XY context; returns (handle, workspace tensor)."""
+    torch = _torch()
+    lib = load_library()
+    nbytes = lib.wolff_xy_workspace_bytes(dim, L)
+    if nbytes == 0:
+        raise WolffError(WOLFF_EINVAL, "invalid lattice shape dim=%r L=%r" % (dim, L))
+    if workspace is None:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    handle = ctypes.c_void_p()
+    st = lib.xy_init(ctypes.byref(handle), int(dim), int(L), int(angle_bits), float(J), float(T),
+                     int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.c_void_p(workspace.data_ptr()),
+                     workspace.numel(), _stream_handle(stream))
+    _check(st)
+    return handle, workspace
+
+
+class WolffXY:
+    """One XY lattice (angles in units of 2 pi / 65536 on a grid of
+    angle_bits bits) and its embedded-cluster Wolff chain on the current
+    CUDA device.  Energies and magnetisations are fixed point (units 2^-30)."""
+
+    def __init__(self, dim, L, T, J=1.0, seed=0, angle_bits=XY_ANGLE_BITS, grid_blocks=0,
+                 block_threads=0, stream=None):
+        self.dim, self.L, self.J, self.T, self.seed = int(dim), int(L), float(J), float(T), int(seed)
+        self.N = self.L ** self.dim
+        self.angle_bits = int(angle_bits)
+        self.handle, self.workspace = xy_init(dim, L, angle_bits, J, T, seed, stream=stream)
+        self._records = None
+        if grid_blocks or block_threads:
+            self.set_schedule(SCHED_CLUSTER, grid_blocks, block_threads)
+
+    def set_schedule(self, schedule=SCHED_CLUSTER, grid_blocks=0, block_threads=0):
+        _check(load_library().wolff_set_schedule(self.handle, int(schedule), int(grid_blocks),
+                                                 int(block_threads)), self.handle)
+
+    def record_buffer(self, n):
+        torch = _torch()
+        need = int(n) * XY_RECORD_BYTES
+        if self._records is None or self._records.numel() < need:
+            self._records = torch.empty(max(need, XY_RECORD_BYTES), dtype=torch.uint8,
+                                        device="cuda")
+        return self._records
+
+    def step(self, n, records=True):
+        """Runs n updates; returns the records as a numpy array (synchronising)
+        when records is True, the device buffer when records == "device", else None."""
+        buf = self.record_buffer(n) if records else None
+        wolff_step(self.handle, n, buf)
+        if records == "device":
+            return buf
+        if records:
+            host = buf[: int(n) * XY_RECORD_BYTES].cpu().numpy()
+            return host.view(XY_RECORD_DTYPE).copy()
+        return None
+
+    def measure(self):
+        E, Mx, My, C = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_uint64()
+        _check(load_library().xy_measure(self.handle, ctypes.byref(E), ctypes.byref(Mx),
+                                         ctypes.byref(My), ctypes.byref(C)), self.handle)
+        return E.value, Mx.value, My.value, C.value
+
+    def measure_full(self):
+        E, Mx, My = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load_library().xy_measure_full(self.handle, ctypes.byref(E), ctypes.byref(Mx),
+                                              ctypes.byref(My)), self.handle)
+        return E.value, Mx.value, My.value
+
+    def get_state(self):
+        theta = np.zeros(self.N, dtype=np.uint16)
+        t = ctypes.c_uint64()
+        _check(load_library().xy_get_state(self.handle, theta.ctypes.data_as(ctypes.c_void_p),
+                                           ctypes.byref(t)), self.handle)
+        return theta, t.value
+
+    def set_state(self, theta, t):
+        theta = np.ascontiguousarray(theta, dtype=np.uint16)
+        if theta.size != self.N:
+            raise ValueError("need %d angles" % self.N)
+        _check(load_library().xy_set_state(self.handle, theta.ctypes.data_as(ctypes.c_void_p),
+                                           int(t)), self.handle)
+
+    def stats(self):
+        st = _Stats()
+        _check(load_library().wolff_get_stats(self.handle, ctypes.byref(st)), self.handle)
+        return {k: int(getattr(st, k)) for k, _ in _Stats._fields_}
+
+    def info(self):
+        inf = _Info()
+        _check(load_library().wolff_get_info(self.handle, ctypes.byref(inf)), self.handle)
+        return {k: getattr(inf, k) for k, _ in _Info._fields_}
+
+    def close(self):
+        if self.handle is not None:
+            ising_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "wolff.h"
 #include "wolff_internal.h"
@@ -28,6 +29,13 @@ struct wolff_ctx {
     uint32_t N = 0;
     int potts = 0;         // 0 = Ising, 1 = q-state Potts
     uint32_t q = 2;
+    int xy = 0;            // 1 = XY model (32-bit site words)
+    uint32_t angle_bits = 15;
+    double xy_kk = 0;
+    int32_t *xy_tab = nullptr;     // device copies in the workspace
+    double *xy_coef = nullptr;
+    std::vector<int32_t> h_xy_tab; // host copies (kept for the async uploads)
+    std::vector<double> h_xy_coef;
     double J = 0, T = 0;
     uint64_t seed = 0, thr = 0;
     int layout = 0;
@@ -112,6 +120,11 @@ StepParams make_params(const wolff_ctx *c) {
     p.burst = (uint32_t)c->burst;
     p.budget_ns = 0;
     p.q = c->q;
+    p.xy_tab = c->xy_tab;
+    p.xy_coef = c->xy_coef;
+    p.xy_kk = c->xy_kk;
+    p.xy_bits = c->angle_bits;
+    p.xy_records = nullptr;
     return p;
 }
 
@@ -206,9 +219,17 @@ size_t wolff_workspace_bytes(int dim, int L, int layout) {
     return 2 * sizeof(DevCtl) + round_up(n, kAlign) + round_up(n * sizeof(uint32_t), kAlign);
 }
 
+size_t wolff_xy_workspace_bytes(int dim, int L) {
+    if (!shape_ok(dim, L)) return 0;
+    const size_t n = sites(dim, L);
+    return 2 * sizeof(DevCtl) + 2 * round_up(n * sizeof(uint32_t), kAlign) +
+           round_up(kXyTableSize * sizeof(int32_t), kAlign) + round_up(17 * sizeof(double), kAlign);
+}
+
 static wolff_status init_common(wolff_ctx **out, int dim, int L, double J, double T,
                                 uint64_t seed, int layout, void *d_workspace,
-                                size_t workspace_bytes, void *stream, int potts, uint32_t q);
+                                size_t workspace_bytes, void *stream, int potts, uint32_t q,
+                                int xy_bits = 0);
 
 wolff_status ising_init(wolff_ctx **out, int dim, int L, double J, double T, uint64_t seed,
                         int layout, void *d_workspace, size_t workspace_bytes, void *stream) {
@@ -222,14 +243,25 @@ wolff_status potts_init(wolff_ctx **out, int dim, int L, int q, double J, double
                        stream, 1, (uint32_t)q);
 }
 
+wolff_status xy_init(wolff_ctx **out, int dim, int L, int angle_bits, double J, double T,
+                     uint64_t seed, void *d_workspace, size_t workspace_bytes, void *stream) {
+    if (!out) return WOLFF_EINVAL;
+    *out = nullptr;
+    if (angle_bits < 1 || angle_bits > WOLFF_XY_ANGLE_BITS) return WOLFF_EINVAL;
+    return init_common(out, dim, L, J, T, seed, WOLFF_LAYOUT_INT8, d_workspace, workspace_bytes,
+                       stream, 0, 2, angle_bits);
+}
+
 static wolff_status init_common(wolff_ctx **out, int dim, int L, double J, double T,
                                 uint64_t seed, int layout, void *d_workspace,
-                                size_t workspace_bytes, void *stream, int potts, uint32_t q) {
+                                size_t workspace_bytes, void *stream, int potts, uint32_t q,
+                                int xy_bits) {
     if (!out) return WOLFF_EINVAL;
     *out = nullptr;
     if (!shape_ok(dim, L) || layout != WOLFF_LAYOUT_INT8) return WOLFF_EINVAL;
     if (!(J >= 0.0) || !(T > 0.0)) return WOLFF_EINVAL;
-    const size_t need = wolff_workspace_bytes(dim, L, layout);
+    const bool xy = xy_bits > 0;
+    const size_t need = xy ? wolff_xy_workspace_bytes(dim, L) : wolff_workspace_bytes(dim, L, layout);
     if (d_workspace) {
         if (workspace_bytes < need) return WOLFF_ENOMEM;
         if (reinterpret_cast<uintptr_t>(d_workspace) % kAlign) return WOLFF_EINVAL;
@@ -244,6 +276,19 @@ static wolff_status init_common(wolff_ctx **out, int dim, int L, double J, doubl
     c->seed = seed;
     c->potts = potts;
     c->q = q;
+    c->xy = xy ? 1 : 0;
+    if (xy) {
+        c->angle_bits = (uint32_t)xy_bits;
+        c->xy_kk = ldexp(2.0 * J / T, -60);
+        // round(cos(pi k / 32768) 2^30), k = 0..16384, and 1/n!, n = 0..16
+        c->h_xy_tab.resize(kXyTableSize);
+        for (uint32_t k = 0; k < kXyTableSize; ++k)
+            c->h_xy_tab[k] = (int32_t)llround(cos(3.141592653589793 * (double)k / 32768.0) *
+                                              1073741824.0);
+        c->h_xy_coef.resize(17);
+        c->h_xy_coef[0] = 1.0;
+        for (int n = 1; n <= 16; ++n) c->h_xy_coef[n] = c->h_xy_coef[n - 1] / (double)n;
+    }
     // Ising: p = 1 - exp(-2J/T); Potts: p = 1 - exp(-J/T)
     c->thr = potts ? wolff_bond_threshold(0.5 * J, T) : wolff_bond_threshold(J, T);
     c->layout = layout;
@@ -271,22 +316,44 @@ static wolff_status init_common(wolff_ctx **out, int dim, int L, double J, doubl
     c->ctl = reinterpret_cast<DevCtl *>(base);
     c->scratch_ctl = reinterpret_cast<DevCtl *>(base + sizeof(DevCtl));
     c->spins = reinterpret_cast<uint8_t *>(base + 2 * sizeof(DevCtl));
-    c->list = reinterpret_cast<uint32_t *>(base + 2 * sizeof(DevCtl) + round_up(c->N, kAlign));
+    const size_t spin_bytes = round_up(xy ? (size_t)c->N * sizeof(uint32_t) : c->N, kAlign);
+    c->list = reinterpret_cast<uint32_t *>(base + 2 * sizeof(DevCtl) + spin_bytes);
+    if (xy) {
+        char *tail = base + 2 * sizeof(DevCtl) + spin_bytes +
+                     round_up((size_t)c->N * sizeof(uint32_t), kAlign);
+        c->xy_tab = reinterpret_cast<int32_t *>(tail);
+        c->xy_coef = reinterpret_cast<double *>(
+            tail + round_up(kXyTableSize * sizeof(int32_t), kAlign));
+    }
     c->blocks = default_blocks(c);
     c->threads = 512;
     c->max_cluster = max_cluster_size(dim, c->threads);
     c->cluster = c->max_cluster;
 
     const StepParams p = make_params(c);
-    e = cudaMemsetAsync(c->ws, 0, 2 * sizeof(DevCtl) + round_up(c->N, kAlign), c->stream);
+    e = cudaMemsetAsync(c->ws, 0, 2 * sizeof(DevCtl) + spin_bytes, c->stream);
     if (e == cudaSuccess) e = empty_list(c);
     if (e == cudaSuccess) e = launch_reset_ctl(c->ctl, 0, c->stream);
-    if (e == cudaSuccess)
-        e = potts ? launch_potts_init(c->spins, p.g, q, p.key0, p.key1, c->stream)
-                  : launch_init(c->spins, p.g, p.key0, p.key1, c->stream);
-    if (e == cudaSuccess)
-        e = potts ? launch_potts_measure(dim, c->spins, p.g, c->ctl, 1, c->stream)
-                  : launch_measure_full(dim, c->spins, p.g, c->ctl, 1, c->stream);
+    if (xy) {
+        uint32_t *words = reinterpret_cast<uint32_t *>(c->spins);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->xy_tab, c->h_xy_tab.data(), kXyTableSize * sizeof(int32_t),
+                                cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->xy_coef, c->h_xy_coef.data(), 17 * sizeof(double),
+                                cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = launch_xy_init(words, p.g, c->angle_bits, p.key0, p.key1, c->stream);
+        if (e == cudaSuccess)
+            e = launch_xy_measure(dim, words, p.g, c->xy_tab, c->ctl, 1, c->stream);
+    } else {
+        if (e == cudaSuccess)
+            e = potts ? launch_potts_init(c->spins, p.g, q, p.key0, p.key1, c->stream)
+                      : launch_init(c->spins, p.g, p.key0, p.key1, c->stream);
+        if (e == cudaSuccess)
+            e = potts ? launch_potts_measure(dim, c->spins, p.g, c->ctl, 1, c->stream)
+                      : launch_measure_full(dim, c->spins, p.g, c->ctl, 1, c->stream);
+    }
     if (e != cudaSuccess) {
         cuda_fail(c, e, "ising_init");
         ising_free(c);
@@ -314,6 +381,8 @@ wolff_status wolff_set_schedule(wolff_ctx *c, int schedule, int grid_blocks, int
     const int sched_eff = schedule == WOLFF_SCHED_AUTO ? WOLFF_SCHED_CLUSTER : schedule;
     if (c->potts && sched_eff != WOLFF_SCHED_CLUSTER)
         return fail(c, WOLFF_EUNSUPPORTED, "the Potts update runs on the cluster schedule only");
+    if (c->xy && sched_eff != WOLFF_SCHED_CLUSTER)
+        return fail(c, WOLFF_EUNSUPPORTED, "the XY update runs on the cluster schedule only");
     if (sched_eff != WOLFF_SCHED_GRAPH && (block_threads ? block_threads : c->threads) > 512)
         return fail(c, WOLFF_EINVAL, "persistent and cluster schedules take at most 512 threads");
     c->schedule = sched_eff;
@@ -365,7 +434,13 @@ wolff_status wolff_step(wolff_ctx *c, uint64_t n_updates, void *d_records) {
         e = launch_prefetch_l2(c->spins, c->N, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "prefetch");
     }
-    if (c->potts) {
+    if (c->xy) {
+        StepParams px = p;
+        px.records = nullptr;
+        px.xy_records = reinterpret_cast<wolff_xy_record *>(d_records);
+        e = launch_xy_team(c->dim, px, c->cluster, c->threads, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "xy launch");
+    } else if (c->potts) {
         e = launch_potts_team(c->dim, p, c->cluster, c->threads, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "potts launch");
     } else if (c->schedule == WOLFF_SCHED_CLUSTER) {
@@ -402,6 +477,7 @@ wolff_status wolff_step(wolff_ctx *c, uint64_t n_updates, void *d_records) {
 
 wolff_status measure(wolff_ctx *c, int64_t *E_bond, int64_t *M, uint64_t *last_C) {
     if (!c) return WOLFF_EINVAL;
+    if (c->xy) return fail(c, WOLFF_EUNSUPPORTED, "XY contexts use xy_measure");
     DevCtl h;
     wolff_status s = sync_and_check(c, &h);
     if (s != WOLFF_OK) return s;
@@ -413,6 +489,7 @@ wolff_status measure(wolff_ctx *c, int64_t *E_bond, int64_t *M, uint64_t *last_C
 
 wolff_status measure_full(wolff_ctx *c, int64_t *E_bond, int64_t *M) {
     if (!c) return WOLFF_EINVAL;
+    if (c->xy) return fail(c, WOLFF_EUNSUPPORTED, "XY contexts use xy_measure_full");
     const StepParams p = make_params(c);
     cudaError_t e = c->potts ? launch_potts_measure(c->dim, c->spins, p.g, c->ctl, 0, c->stream)
                              : launch_measure_full(c->dim, c->spins, p.g, c->ctl, 0, c->stream);
@@ -427,6 +504,7 @@ wolff_status measure_full(wolff_ctx *c, int64_t *E_bond, int64_t *M) {
 
 wolff_status wolff_get_state(wolff_ctx *c, int8_t *h_spins, uint64_t *t) {
     if (!c) return WOLFF_EINVAL;
+    if (c->xy) return fail(c, WOLFF_EUNSUPPORTED, "XY contexts use xy_get_state");
     if (h_spins && c->potts) {   // a Potts site's byte at rest is its colour
         cudaError_t e = cudaMemcpyAsync(h_spins, c->spins, c->N, cudaMemcpyDeviceToHost, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "get_state");
@@ -447,6 +525,7 @@ wolff_status wolff_get_state(wolff_ctx *c, int8_t *h_spins, uint64_t *t) {
 
 wolff_status wolff_set_state(wolff_ctx *c, const int8_t *h_spins, uint64_t t) {
     if (!c || !h_spins) return WOLFF_EINVAL;
+    if (c->xy) return fail(c, WOLFF_EUNSUPPORTED, "XY contexts use xy_set_state");
     if (c->potts) {
         const StepParams p = make_params(c);
         cudaError_t e = cudaMemcpyAsync(c->spins, h_spins, c->N, cudaMemcpyHostToDevice, c->stream);
@@ -480,6 +559,7 @@ wolff_status wolff_set_state(wolff_ctx *c, const int8_t *h_spins, uint64_t t) {
 wolff_status wolff_run_host(wolff_ctx *c, const int8_t *h_spins_in, uint64_t t_in,
                             uint64_t n_updates, wolff_record *h_records, int8_t *h_spins_out) {
     if (!c) return WOLFF_EINVAL;
+    if (c->xy) return fail(c, WOLFF_EUNSUPPORTED, "no host-buffer path for XY contexts");
     wolff_status s;
     if (h_spins_in) {
         s = wolff_set_state(c, h_spins_in, t_in);
@@ -515,6 +595,78 @@ wolff_status wolff_run_host(wolff_ctx *c, const int8_t *h_spins_in, uint64_t t_i
         s = sync_and_check(c, nullptr);
     }
     return s;
+}
+
+wolff_status xy_measure(wolff_ctx *c, int64_t *E, int64_t *Mx, int64_t *My, uint64_t *last_C) {
+    if (!c) return WOLFF_EINVAL;
+    if (!c->xy) return fail(c, WOLFF_EUNSUPPORTED, "not an XY context");
+    DevCtl h;
+    wolff_status s = sync_and_check(c, &h);
+    if (s != WOLFF_OK) return s;
+    if (E) *E = h.E;
+    if (Mx) *Mx = h.M;
+    if (My) *My = h.My;
+    if (last_C) *last_C = h.last_C;
+    return WOLFF_OK;
+}
+
+wolff_status xy_measure_full(wolff_ctx *c, int64_t *E, int64_t *Mx, int64_t *My) {
+    if (!c) return WOLFF_EINVAL;
+    if (!c->xy) return fail(c, WOLFF_EUNSUPPORTED, "not an XY context");
+    const StepParams p = make_params(c);
+    cudaError_t e = launch_xy_measure(c->dim, reinterpret_cast<const uint32_t *>(c->spins), p.g,
+                                      c->xy_tab, c->ctl, 0, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "xy_measure_full");
+    DevCtl h;
+    wolff_status s = sync_and_check(c, &h);
+    if (s != WOLFF_OK) return s;
+    if (E) *E = h.full_E;
+    if (Mx) *Mx = h.full_M;
+    if (My) *My = h.full_My;
+    return WOLFF_OK;
+}
+
+wolff_status xy_get_state(wolff_ctx *c, uint16_t *h_theta, uint64_t *t) {
+    if (!c) return WOLFF_EINVAL;
+    if (!c->xy) return fail(c, WOLFF_EUNSUPPORTED, "not an XY context");
+    if (h_theta) {
+        // between updates a site word is its angle (no claim bit): copy the
+        // low halves of the words, 2 bytes apart in a 4-byte stride
+        cudaError_t e = cudaMemcpy2DAsync(h_theta, sizeof(uint16_t), c->spins, sizeof(uint32_t),
+                                          sizeof(uint16_t), c->N, cudaMemcpyDeviceToHost,
+                                          c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "xy_get_state");
+    }
+    DevCtl h;
+    wolff_status s = sync_and_check(c, &h);
+    if (s != WOLFF_OK) return s;
+    if (t) *t = h.t;
+    return WOLFF_OK;
+}
+
+wolff_status xy_set_state(wolff_ctx *c, const uint16_t *h_theta, uint64_t t) {
+    if (!c || !h_theta) return WOLFF_EINVAL;
+    if (!c->xy) return fail(c, WOLFF_EUNSUPPORTED, "not an XY context");
+    const StepParams p = make_params(c);
+    uint32_t *words = reinterpret_cast<uint32_t *>(c->spins);
+    cudaError_t e = cudaMemsetAsync(words, 0, (size_t)c->N * sizeof(uint32_t), c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(words, sizeof(uint32_t), h_theta, sizeof(uint16_t),
+                              sizeof(uint16_t), c->N, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_reset_ctl(c->ctl, t, c->stream);
+    if (e == cudaSuccess) e = launch_xy_check(words, c->N, c->angle_bits, c->ctl, c->stream);
+    if (e == cudaSuccess) e = launch_xy_measure(c->dim, words, p.g, c->xy_tab, c->ctl, 1, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "xy_set_state");
+    c->t_host = t;
+    wolff_status st = sync_and_check(c, nullptr);
+    if (st != WOLFF_OK) {   // leave a valid lattice behind a rejected one
+        launch_xy_init(words, p.g, c->angle_bits, p.key0, p.key1, c->stream);
+        launch_reset_ctl(c->ctl, 0, c->stream);
+        launch_xy_measure(c->dim, words, p.g, c->xy_tab, c->ctl, 1, c->stream);
+        cudaStreamSynchronize(c->stream);
+        c->t_host = 0;
+    }
+    return st;
 }
 
 wolff_status wolff_get_info(wolff_ctx *c, wolff_info *info) {
@@ -631,7 +783,7 @@ wolff_status wolff_batch_run_timed(wolff_batch *b, wolff_ctx *const *ctxs, int n
     int n2 = 0, n3 = 0;
     for (int i = 0; i < n; ++i) {
         if (!ctxs[i]) return WOLFF_EINVAL;
-        if (ctxs[i]->potts) return WOLFF_EUNSUPPORTED;
+        if (ctxs[i]->potts || ctxs[i]->xy) return WOLFF_EUNSUPPORTED;
         if (n_updates[i] == 0) continue;
         (ctxs[i]->dim == 2 ? n2 : n3) += 1;
     }

@@ -46,6 +46,8 @@ struct alignas(256) DevCtl {
     unsigned int err_detail;       // where a bounded wait gave up, etc.
     long long full_E;              // full recount results
     long long full_M;
+    long long My;                  // XY: second magnetisation component
+    long long full_My;
     // line 1: grid barrier
     // bar_word = arrivals << 32 | entries appended this level (atomic): the
     // warps reserve list slots and the CTAs arrive on the same word, so the
@@ -107,6 +109,13 @@ struct StepParams {
     uint32_t burst;             // cluster schedule: window mode, growth levels per round (0 = off)
     unsigned long long budget_ns;   // cluster schedule: stop after this much device time (0 = none)
     uint32_t q;                 // Potts: number of colours (the Ising kernels ignore it)
+    // XY (the other kernels ignore these): the sites are 32-bit words
+    // (angle | claim bit), spins points at them
+    const int32_t *xy_tab;      // fixed-point quarter-wave cosine table, 16385 entries
+    const double *xy_coef;      // 1/n!, n = 0..16, for e^-y
+    double xy_kk;               // 2 J / T * 2^-60
+    uint32_t xy_bits;           // angle grid: spins multiples of 2^(16-bits)
+    wolff_xy_record *xy_records;
 };
 
 // Leader-local frontier capacity (shared memory) and the cluster-list prefix
@@ -157,6 +166,17 @@ cudaError_t launch_potts_check(const uint8_t *spins, uint32_t N, uint32_t q, Dev
                                cudaStream_t s);
 cudaError_t launch_potts_team(int dim, const StepParams &p, int cluster_size, int threads,
                               cudaStream_t s);
+
+// XY embedded-cluster model (wolff_xy.cu).
+constexpr uint32_t kXyTableSize = 16385;
+cudaError_t launch_xy_init(uint32_t *words, Geometry g, uint32_t bits, uint32_t k0, uint32_t k1,
+                           cudaStream_t s);
+cudaError_t launch_xy_measure(int dim, const uint32_t *words, Geometry g, const int32_t *tab,
+                              DevCtl *ctl, int set_chain, cudaStream_t s);
+cudaError_t launch_xy_check(const uint32_t *words, uint32_t N, uint32_t bits, DevCtl *ctl,
+                            cudaStream_t s);
+cudaError_t launch_xy_team(int dim, const StepParams &p, int cluster_size, int threads,
+                           cudaStream_t s);
 
 // Graph schedule: builds the nested-WHILE graph; returns its executable.
 cudaError_t build_update_graph(int dim, const StepParams &p, int blocks,

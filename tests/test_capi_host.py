@@ -82,3 +82,23 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(w, "_lib", None)
     with pytest.raises(ImportError):
         w.load_library()
+
+
+def test_xy_workspace_and_argument_checks(lib):
+    import paper_1110_0899_gb300 as w
+    n = 1024 * 1024
+    b = lib.wolff_xy_workspace_bytes(2, 1024)
+    # two 32-bit arrays (site words, cluster list), the cosine table, 1/n!
+    assert 8 * n + 16385 * 4 <= b <= 8 * n + 16385 * 4 + 8192
+    assert lib.wolff_xy_workspace_bytes(2, 1) == 0 and lib.wolff_xy_workspace_bytes(4, 8) == 0
+    h = ctypes.c_void_p()
+    for bits in (0, 16, -1):
+        assert lib.xy_init(ctypes.byref(h), 2, 16, bits, 1.0, 1.0, 1, None, 0, None) == w.WOLFF_EINVAL
+    for dim, L, J, T in [(4, 16, 1.0, 1.0), (2, 1, 1.0, 1.0), (2, 16, 1.0, 0.0), (2, 16, -1.0, 1.0)]:
+        assert lib.xy_init(ctypes.byref(h), dim, L, 15, J, T, 1, None, 0, None) == w.WOLFF_EINVAL
+    assert lib.xy_init(None, 2, 16, 15, 1.0, 1.0, 1, None, 0, None) == w.WOLFF_EINVAL
+    assert lib.xy_measure(None, None, None, None, None) == w.WOLFF_EINVAL
+    assert lib.xy_measure_full(None, None, None, None) == w.WOLFF_EINVAL
+    assert lib.xy_get_state(None, None, None) == w.WOLFF_EINVAL
+    assert lib.xy_set_state(None, None, 0) == w.WOLFF_EINVAL
+    assert w.XY_RECORD_DTYPE.itemsize == 32 and w.XY_RECORD_DTYPE == oracle.XY_RECORD_DTYPE

@@ -70,7 +70,15 @@ WORKLOADS = {
     # point T_c = 1 / ln(1 + sqrt 3), J = 1
     "potts3-2d": dict(dim=2, L=2048, T=1.0 / math.log(1.0 + math.sqrt(3.0)), seed=4, equil=1000,
                       start="ordered", q=3),
+    # XY embedded-cluster update (the other extension section 6 names): 15-bit
+    # angles, 2D near the BKT temperature 0.8929, 3D near its critical 2.2017
+    "xy-2d": dict(dim=2, L=1024, T=0.89, seed=6, equil=200, start="ordered", model="xy"),
+    "xy-3d": dict(dim=3, L=128, T=2.2, seed=7, equil=200, start="ordered", model="xy"),
 }
+# algorithmic bytes per flipped XY site (32-bit words): own word 4, 2D
+# neighbour words, claim read-modify-write 8, list write + read 8, boundary
+# pass re-reading 2D neighbour words and the list entry 4, reflected word 4
+XY_ALGO_BYTES_PER_FLIP = {2: 60.0, 3: 76.0}
 
 
 def parse():
@@ -193,20 +201,41 @@ def run_reference(args):
     import oracle
     wl = WORKLOADS[args.workload]
     dim, L, T, seed = wl["dim"], wl["L"], wl["T"], wl["seed"]
-    thr = oracle.bond_threshold(1.0, T)
-    s = oracle.init_lattice(dim, L, seed)
-    if wl["start"] == "ordered":
-        s[:] = 1
+    q, ordered = wl.get("q"), wl["start"] == "ordered"
+    if wl.get("model") == "xy":
+        kk = oracle.xy_coupling(1.0, T)
+        s = oracle.xy_init(dim, L, oracle.XY_ANGLE_BITS, seed)
+        if ordered:
+            s[:] = 0
+
+        def run(t, n, records=True):
+            return oracle.xy_run(dim, L, oracle.XY_ANGLE_BITS, kk, seed, t, n, s, records)
+    elif q:
+        thr = oracle.potts_threshold(1.0, T)
+        s = oracle.potts_init(dim, L, q, seed)
+        if ordered:
+            s[:] = 0
+
+        def run(t, n, records=True):
+            return oracle.potts_run(dim, L, q, thr, seed, t, n, s, records)
+    else:
+        thr = oracle.bond_threshold(1.0, T)
+        s = oracle.init_lattice(dim, L, seed)
+        if ordered:
+            s[:] = 1
+
+        def run(t, n, records=True):
+            return oracle.run(dim, L, thr, seed, t, n, s, records)
     # the configuration's equilibration, unrecorded (the oracle skips its full
     # recount when no record is asked for)
     equil = wl["equil"] if args.equil is None else args.equil
-    oracle.run(dim, L, thr, seed, 0, equil, s, records=False)
+    run(0, equil, records=False)
     t = equil
     per_step = 4
     times, flips = [], []
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        rec = oracle.run(dim, L, thr, seed, t, per_step, s)
+        rec = run(t, per_step)
         dt = time.perf_counter() - t0
         t += per_step
         if k >= args.warmup:
@@ -370,10 +399,146 @@ def cpu_baseline(dim, L, T, seed, spins, t, seconds, q=None):
                       % (n, t, spent)}
 
 
+def run_xy(args):
+    """One XY lattice per launch: the same timing contract as the Ising
+    workloads (L2 flush between steps, CUDA events on the lattice's stream,
+    clocks sampled, e2e through host buffers, the oracle as CPU baseline)."""
+    import numpy as np
+    import torch
+
+    import paper_1110_0899_gb300 as w
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    wl = WORKLOADS[args.workload]
+    dim, L, T = wl["dim"], wl["L"], wl["T"]
+    seed = rank_seed(wl["seed"], rank)
+    equil = wl["equil"] if args.equil is None else args.equil
+    U = args.updates_per_step
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        lat = w.WolffXY(dim, L, T, seed=seed, stream=stream, grid_blocks=args.blocks,
+                        block_threads=args.threads)
+        info = lat.info()
+        lat.set_state(np.zeros(lat.N, np.uint16), 0)
+        done = 0
+        while done < equil:
+            k = min(100, equil - done)
+            lat.step(k, records=False)
+            done += k
+        snap, t_snap = lat.get_state()
+        rec_buf = lat.record_buffer(U)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        for _ in range(args.warmup):
+            w.wolff_step(lat.handle, U, rec_buf)
+        torch.cuda.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        recs = []
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            starts[k].record(stream)
+            w.wolff_step(lat.handle, U, rec_buf)
+            ends[k].record(stream)
+            recs.append(rec_buf[: U * w.XY_RECORD_BYTES].clone())
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        if world > 1:
+            torch.distributed.barrier()
+        total_ms = float(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
+        records = np.concatenate([r.cpu().numpy().view(w.XY_RECORD_DTYPE) for r in recs])
+        flips = int(records["C"].astype(np.int64).sum())
+        if world > 1:
+            total_ms_all, flips_all = aggregate_ranks(total_ms, flips, "cuda")
+        else:
+            total_ms_all, flips_all = total_ms, float(flips)
+        value = flips_all / (total_ms_all / 1000.0)
+        e2e = None
+        if not args.no_e2e:
+            # the public API end to end: upload the snapshot, run U recorded
+            # updates, read the records back
+            e_flips, e_s = 0, 0.0
+            for k in range(max(3, min(args.steps, 5))):
+                t0 = time.perf_counter()
+                lat.set_state(snap, t_snap)
+                r = lat.step(U)
+                e_s += time.perf_counter() - t0
+                e_flips += int(r["C"].astype(np.int64).sum())
+            e2e = {"value": e_flips / e_s, "unit": UNIT, "h2d_bytes_per_step": int(2 * lat.N),
+                   "d2h_bytes_per_step": int(U * w.XY_RECORD_BYTES)}
+    lat.close()
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    peaks, peak_kind = measured_peaks()
+    achieved = XY_ALGO_BYTES_PER_FLIP[dim] * (flips / args.steps) / (total_ms / args.steps / 1000.0) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_kind": peak_kind,
+            "kernel": "k_xy_team<%d>" % dim}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = xy_cpu_baseline(dim, L, T, seed, snap, t_snap, args.cpu_seconds)
+    warm = 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u16 angles, i64 fixed point, f64 bond test", "data": "synthetic",
+        "config": {"workload": "XY %dD L=%d T=%.6g J=1 seed %d, 15-bit angles, %s start, %d "
+                               "equilibration + %d x %d recorded updates, one lattice per launch"
+                               % (dim, L, T, seed, wl["start"], equil, args.steps, U),
+                   "dim": dim, "L": L, "T": T, "seed": seed, "updates_per_step": U,
+                   "schedule": "cluster", "grid_blocks": info["grid_blocks"],
+                   "block_threads": info["block_threads"],
+                   "l2": "256 MB buffer written between timed steps",
+                   "parallelism": "replicas x%d" % world},
+        "e2e": e2e, "gpu_launches": args.steps * (1 + warm), "roofline": roof,
+        "cpu_baseline": cpu, "clocks": clk,
+        "detail": {"mean_cluster": flips / len(records),
+                   "mean_levels": float(records["levels"].mean()),
+                   "max_levels": int(records["levels"].max()),
+                   "ms_per_update": total_ms / len(records)},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def xy_cpu_baseline(dim, L, T, seed, theta, t, seconds):
+    """The XY oracle from the GPU's equilibrated lattice, one update at a
+    time until `seconds` of CPU work have run."""
+    import numpy as np
+
+    import oracle
+    kk = oracle.xy_coupling(1.0, T)
+    th = np.array(theta, dtype=np.uint16, copy=True)
+    flips, spent, n = 0, 0.0, 0
+    while spent < seconds and n < 1000:
+        t0 = time.perf_counter()
+        rec = oracle.xy_run(dim, L, oracle.XY_ANGLE_BITS, kk, seed, t + n, 1, th)
+        spent += time.perf_counter() - t0
+        flips += int(rec["C"][0])
+        n += 1
+    return {"value": flips / spent, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d updates from the GPU's equilibrated lattice (t=%d), %.1f s of one core"
+                      % (n, t, spent)}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if WORKLOADS.get(args.workload, {}).get("model") == "xy":
+        return run_xy(args)
     if args.workload == "batched":
         return run_batched(args)
     if args.workload == "served":

@@ -85,6 +85,28 @@ __device__ __forceinline__ unsigned long long xy_threshold(long long prod, const
     return (unsigned long long)floor(__dmul_rn(pr, 4294967296.0));
 }
 
+// The bond test r < floor(2^32 (1 - e^-y)), decided first in single
+// precision.  p_f = 1 - expf(-y_f) with y_f = float(kk) * float(prod):
+// y_f = y (1 + e), |e| <= 3 * 2^-24, and expf is within 2 ulp (CUDA
+// programming guide, appendix on mathematical functions), so
+// |p_f - p| <= max_y (e^-y y 3 2^-24) + 2 * 2^-23 < 3.2e-7, and the exact
+// threshold x = p 2^32 lies within kXyMargin 2^32 of p_f 2^32.  Outside that
+// band the single-precision answer is the exact one (an integer r with
+// r + 1 <= x is below floor(x); r >= x is not); inside it (a few times 1e-6
+// of the tests) the double-precision path decides.
+constexpr double kXyMargin = 2.0e-6;
+
+__device__ __forceinline__ bool xy_bond_active(uint32_t r, long long prod, float kk_f,
+                                               const StepParams &p) {
+    if (prod <= 0) return false;
+    const float yf = __fmul_rn(kk_f, __ll2float_rn(prod));
+    const double pf = 1.0 - (double)expf(-yf);
+    const double ru = (double)r;
+    if (ru + 1.0 <= (pf - kXyMargin) * 4294967296.0) return true;
+    if (ru >= (pf + kXyMargin) * 4294967296.0) return false;
+    return (unsigned long long)r < xy_threshold(prod, p);
+}
+
 __device__ __forceinline__ uint32_t xy_reflect(uint32_t theta, uint32_t phi) {
     return (32768u + 2u * phi - theta) & kXyAngle;
 }
@@ -108,6 +130,7 @@ __device__ __forceinline__ uint32_t xy_expand(const StepParams &p, uint32_t pack
     Philox4 draw[DIM + 1];
     philox4x32_10_lanes<DIM + 1>(owners, tlo, thi, kTagBond, p.key0, p.key1, draw);
     const long long si = xy_cos(p.xy_tab, (wi & kXyAngle) + 65536u - phi);
+    const float kk_f = __double2float_rn(p.xy_kk);
     uint32_t want = 0;
 #pragma unroll
     for (int s = 0; s < 2 * DIM; ++s) {
@@ -115,7 +138,7 @@ __device__ __forceinline__ uint32_t xy_expand(const StepParams &p, uint32_t pack
         const int d = s >> 1;
         const uint32_t r = (s & 1) ? draw[d + 1].v[d] : draw[0].v[d];
         const long long sj = xy_cos(p.xy_tab, (v[s] & kXyAngle) + 65536u - phi);
-        if ((unsigned long long)r < xy_threshold(si * sj, p)) want |= 1u << s;
+        if (xy_bond_active(r, si * sj, kk_f, p)) want |= 1u << s;
     }
     unsigned int old[2 * DIM];
 #pragma unroll

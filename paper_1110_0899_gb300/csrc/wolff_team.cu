@@ -336,6 +336,43 @@ __device__ __forceinline__ void win_start(const StepParams &p, unsigned long lon
     levels = 0;
 }
 
+// Prefetches into L1 the lattice lines a member's neighbours will read if
+// they join: the neighbours of (x+-1, ...) lie in the lines the member reads
+// itself; those of (x, y+-1, ...) add the rows y+-2 (and, in 3D, z+-2 and the
+// four (y+-1, z+-1) diagonals).  Loads of the next level then hit L1 within
+// the same growth phase.
+__device__ __forceinline__ void prefetch_l1(const void *ptr) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(ptr));
+}
+
+__device__ __forceinline__ uint32_t wrap_add(uint32_t c, int d, uint32_t L) {
+    const int v = (int)c + d;
+    return (uint32_t)(v < 0 ? v + (int)L : v >= (int)L ? v - (int)L : v);
+}
+
+template <int DIM>
+__device__ __forceinline__ void prefetch_two_hop(const StepParams &p, uint32_t packed) {
+    uint32_t c[DIM];
+    unpack<DIM>(packed, c);
+    const uint32_t L = p.g.L;
+    if (DIM == 2) {
+        prefetch_l1(p.spins + c[0] + L * wrap_add(c[1], -2, L));
+        prefetch_l1(p.spins + c[0] + L * wrap_add(c[1], 2, L));
+    } else {
+        const uint32_t LL = p.g.LL;
+        const uint32_t x = c[0], y = c[1], z = c[DIM - 1];
+        prefetch_l1(p.spins + x + L * wrap_add(y, -2, L) + LL * z);
+        prefetch_l1(p.spins + x + L * wrap_add(y, 2, L) + LL * z);
+        prefetch_l1(p.spins + x + L * y + LL * wrap_add(z, -2, L));
+        prefetch_l1(p.spins + x + L * y + LL * wrap_add(z, 2, L));
+#pragma unroll
+        for (int a = -1; a <= 1; a += 2)
+#pragma unroll
+            for (int b = -1; b <= 1; b += 2)
+                prefetch_l1(p.spins + x + L * wrap_add(y, a, L) + LL * wrap_add(z, b, L));
+    }
+}
+
 // Warp: one level of speculative growth, members[lo, n) -> new members
 // appended.  Returns true when the cluster outgrew cap.
 template <int DIM>
@@ -356,6 +393,7 @@ __device__ __forceinline__ bool win_level(const StepParams &p, uint32_t *members
             uint8_t v[2 * DIM];
 #pragma unroll
             for (int s = 0; s < 2 * DIM; ++s) v[s] = __ldca(p.spins + nb2.idx[s]);
+            prefetch_two_hop<DIM>(p, members[k]);
             uint32_t par = 0;
 #pragma unroll
             for (int s = 0; s < 2 * DIM; ++s) par |= (uint32_t)((v[s] & 1u) == sig0bit) << s;
@@ -366,31 +404,52 @@ __device__ __forceinline__ bool win_level(const StepParams &p, uint32_t *members
             for (int d = 0; d < DIM; ++d) owners[d + 1] = nb2.idx[2 * d + 1];
             Philox4 draw[DIM + 1];
             philox4x32_10_lanes<DIM + 1>(owners, tlo, thi, kTagBond, p.key0, p.key1, draw);
+            // every active bond's home slot is tried at once; only a
+            // collision probes further
+            uint32_t cand = 0;
 #pragma unroll
             for (int s = 0; s < 2 * DIM; ++s) {
                 const int d = s >> 1;
                 const uint32_t r = (s & 1) ? draw[d + 1].v[d] : draw[0].v[d];
-                if (((par >> s) & 1u) && (unsigned long long)r < p.thr) {
-                    const int ins = burst_insert(hset, hslots, nb2.idx[s]);
-                    if (ins > 0) fresh |= 1u << s;
-                    if (ins < 0) full = true;
-                }
+                if (((par >> s) & 1u) && (unsigned long long)r < p.thr) cand |= 1u << s;
+            }
+            uint32_t prev[2 * DIM];
+#pragma unroll
+            for (int s = 0; s < 2 * DIM; ++s) {
+                prev[s] = 0;
+                if (cand & (1u << s))
+                    prev[s] = atomicCAS(hset + burst_hash(nb2.idx[s], hslots), kEmptyKey,
+                                        nb2.idx[s]);
+            }
+#pragma unroll
+            for (int s = 0; s < 2 * DIM; ++s) {
+                if (!(cand & (1u << s))) continue;
+                int ins;
+                if (prev[s] == kEmptyKey) ins = 1;
+                else if (prev[s] == nb2.idx[s]) ins = 0;
+                else ins = burst_insert(hset, hslots, nb2.idx[s]);
+                if (ins > 0) fresh |= 1u << s;
+                if (ins < 0) full = true;
             }
         }
-        const uint32_t cnt = __popc(fresh);
-        uint32_t incl = cnt;
+        // positions of the new members: one ballot per direction
+        const uint32_t lt = (1u << lane) - 1u;
+        uint32_t before = 0, total = 0, own = 0;
+        uint32_t pos_of[2 * DIM];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(kFullMask, incl, o);
-            if (lane >= o) incl += y;
+        for (int s = 0; s < 2 * DIM; ++s) {
+            const uint32_t m = __ballot_sync(kFullMask, (fresh >> s) & 1u);
+            before += __popc(m & lt);
+            total += __popc(m);
+            pos_of[s] = own;
+            own += (fresh >> s) & 1u;
         }
-        const uint32_t total = __shfl_sync(kFullMask, incl, 31);
-        uint32_t pos = n + incl - cnt;
+        // order: lanes first, then directions within a lane
 #pragma unroll
         for (int s = 0; s < 2 * DIM; ++s) {
             if (fresh & (1u << s)) {
+                const uint32_t pos = n + before + pos_of[s];
                 if (pos < cap) members[pos] = nb2.packed[s];
-                ++pos;
             }
         }
         n += total;
@@ -412,11 +471,20 @@ __device__ __forceinline__ int win_boundary(const StepParams &p, const uint32_t 
         uint32_t i;
         Neighbours<DIM> nb2;
         neighbours<DIM>(p.g, members[k], &i, nb2);
+        uint32_t home[2 * DIM];
+        uint8_t cur[2 * DIM];
 #pragma unroll
         for (int s = 0; s < 2 * DIM; ++s) {
-            if (burst_contains(hset, hslots, nb2.idx[s])) continue;
-            const uint32_t cur = __ldca(p.spins + nb2.idx[s]) & 1u;
-            dE += (cur == sig0bit) ? -1 : 1;
+            home[s] = hset[burst_hash(nb2.idx[s], hslots)];
+            cur[s] = __ldca(p.spins + nb2.idx[s]);
+        }
+#pragma unroll
+        for (int s = 0; s < 2 * DIM; ++s) {
+            // the home slot settles membership unless it holds another site
+            const bool member = home[s] == nb2.idx[s] ||
+                                (home[s] != kEmptyKey && burst_contains(hset, hslots, nb2.idx[s]));
+            if (member) continue;
+            dE += ((cur[s] & 1u) == sig0bit) ? -1 : 1;
         }
     }
 #pragma unroll

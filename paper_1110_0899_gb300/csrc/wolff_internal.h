@@ -109,6 +109,7 @@ struct StepParams {
     uint32_t burst;             // cluster schedule: window mode, growth levels per round (0 = off)
     unsigned long long budget_ns;   // cluster schedule: stop after this much device time (0 = none)
     uint32_t q;                 // Potts: number of colours (the Ising kernels ignore it)
+    unsigned long long prefetch_bytes;   // cluster schedule: spins to pull into L2 at kernel start
     // XY (the other kernels ignore these): the sites are 32-bit words
     // (angle | claim bit), spins points at them
     const int32_t *xy_tab;      // fixed-point quarter-wave cosine table, 16385 entries
@@ -153,7 +154,7 @@ struct WinCfg {
 };
 constexpr int kDefaultWindowLevels = 32;  // growth levels per warp between commit rounds
 const void *team_kernel(int dim);
-size_t window_smem_bytes(int threads, int window_slots);
+size_t window_smem_bytes(int threads, int window_slots, int cluster_size);
 cudaError_t launch_team(int dim, const StepParams &single, const StepParams *d_table, int njobs,
                         int cluster_size, int threads, int window_slots, cudaStream_t s);
 

@@ -74,7 +74,7 @@ extern "C" wolff_status wolff_step_static(int dim, int L, double J, double T, ui
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
         return WOLFF_ECUDA;
 
-    StepParams p;
+    StepParams p = {};   // fields this path does not use stay zero
     p.ctl = static_cast<DevCtl *>(scratch);
     p.list = reinterpret_cast<uint32_t *>(static_cast<char *>(scratch) + sizeof(DevCtl));
     // the caller's int8 +-1 lattice is turned into the kernel's spin bytes in

@@ -244,15 +244,22 @@ struct WinView {
     uint32_t *members, *j, *state, *cmin, *rg, *off, *scal;
     uint4 *meta;
     uint8_t *amask;
+    uint4 *lmeta;   // leader: results of updates c .. c + P - 1, pushed by their CTAs
 };
 enum : uint32_t { kScNextQ = 0, kScRgCount = 1, kScRgTake = 2, kScQEnd = 3, kScMin = 4 };
 constexpr uint32_t kWinScalars = 8;
 
-__device__ __forceinline__ WinView win_view(uint32_t *base, uint32_t S, uint32_t cap) {
+// Layout (32-bit words unless noted): members S*cap | meta S uint4 | lmeta
+// S*cs uint4 | j, state, cmin, rg S each | off S+1 | scalars | amask S*cap
+// bytes.  Both uint4 arrays start at multiples of 16 bytes (cap is a multiple
+// of 4 and the base is 16-byte aligned).
+__device__ __forceinline__ WinView win_view(uint32_t *base, uint32_t S, uint32_t cap,
+                                            uint32_t cs) {
     WinView v;
     v.members = base;
     v.meta = reinterpret_cast<uint4 *>(base + S * cap);
-    uint32_t *m = base + S * cap + 4 * S;
+    v.lmeta = v.meta + S;
+    uint32_t *m = base + S * cap + 4 * S + 4 * S * cs;
     v.j = m;
     v.state = m + S;
     v.cmin = m + 2 * S;
@@ -582,7 +589,7 @@ __device__ void win_records(const StepParams &p, TeamShared &sh, cg::cluster_gro
         const uint32_t j = base + threadIdx.x;
         const bool valid = j < cut;
         uint4 m = make_uint4(0, 0, 0, 0);
-        if (valid) m = cl.map_shared_rank(v.meta, j % cs)[(j / cs) & (S - 1)];
+        if (valid) m = v.lmeta[j - c];
         const uint32_t n = m.x, lev = m.y, sig = m.w;
         const int dE = (int)m.z;
         long long de = valid ? 2LL * dE : 0;
@@ -642,7 +649,7 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
     const uint32_t P = S * cs;
     TeamShared *lead = cl.map_shared_rank(&sh, 0);
     uint32_t *hset = &sh.front[0][0] + (warp % kWinMaxWarps) * hslots;
-    const WinView v = win_view(win_dyn, S, cap);
+    const WinView v = win_view(win_dyn, S, cap, cs);
     uint32_t c = resume ? c_start : 0;
     if (!resume) {
         for (uint32_t k = threadIdx.x; k < S; k += blockDim.x) v.state[k] = kSlotFree;
@@ -787,6 +794,13 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
             uint32_t cc[DIM];
             unpack<DIM>(v.members[s * cap + (f - v.off[s])], cc);
             atomicMin(p.list + site_index<DIM>(p.g, cc), v.j[s]);
+        }
+        {
+            // every finished update's result goes to the leader, at its
+            // offset from the window start, for the record scan of the commit
+            uint4 *lead_meta = cl.map_shared_rank(v.lmeta, 0);
+            for (uint32_t s = threadIdx.x; s < S; s += blockDim.x)
+                if (v.state[s] == kSlotDone) lead_meta[v.j[s] - c] = v.meta[s];
         }
         cl.sync();
         if (timer) win_tick(win_ns[1], tick);
@@ -1168,6 +1182,15 @@ __global__ void __launch_bounds__(512, 1) k_team(StepParams single, const StepPa
     __shared__ TeamShared sh;
     const unsigned int job = blockIdx.x / cl.num_blocks();
     const StepParams p = table ? table[job] : single;
+    if (p.prefetch_bytes) {
+        // pull the lattice into L2 (it may have been evicted since the last
+        // launch); the growth starts while the lines stream in
+        const unsigned long long stride = (unsigned long long)cl.num_blocks() * blockDim.x * 128ull;
+        for (unsigned long long off =
+                 ((unsigned long long)cl.block_rank() * blockDim.x + threadIdx.x) * 128ull;
+             off < p.prefetch_bytes; off += stride)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(p.spins + off));
+    }
     if (cl.block_rank() != 0) {
         team_worker<DIM>(p, sh, cl, wc);
         return;
@@ -1182,12 +1205,13 @@ const void *team_kernel(int dim) {
                     : reinterpret_cast<const void *>(&k_team<3>);
 }
 
-size_t window_smem_bytes(int threads, int window_slots) {
+size_t window_smem_bytes(int threads, int window_slots, int cluster_size) {
     if (window_slots <= 0) return 0;
     const uint32_t W = min((uint32_t)threads / 32u, (uint32_t)kWinMaxWarps);
     const uint32_t cap = W <= 8 ? 2 * kWinCap : kWinCap;
     const size_t S = (size_t)window_slots;
-    return (S * cap + 9 * S + 1 + kWinScalars) * sizeof(uint32_t) + S * cap;
+    return (S * cap + 9 * S + 1 + kWinScalars + 4 * S * (size_t)cluster_size) * sizeof(uint32_t) +
+           S * cap;
 }
 
 cudaError_t launch_team(int dim, const StepParams &single, const StepParams *d_table, int njobs,
@@ -1206,7 +1230,7 @@ cudaError_t launch_team(int dim, const StepParams &single, const StepParams *d_t
         const uint32_t W = min((uint32_t)threads / 32u, (uint32_t)kWinMaxWarps);
         wc.cap = W <= 8 ? 2 * kWinCap : kWinCap;
     }
-    const size_t dyn = window_smem_bytes(threads, window_slots);
+    const size_t dyn = window_smem_bytes(threads, window_slots, cluster_size);
     if (dyn > 0) {
         cudaError_t e =
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);

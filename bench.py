@@ -43,7 +43,7 @@ TC2 = 2.0 / math.log(1.0 + math.sqrt(2.0))
 # committed ncu capture (profiles/k_team_2d_L4096_random_start.md), valid only
 # while the kernel sources hash to the captured value.
 TRAFFIC_CAPTURES = {
-    ("2d", 1000): {"src": "a82fc47d1cc9", "bytes_per_launch": 1327104 + 0},
+    ("2d", 1000): {"src": "63c9d99947a0", "bytes_per_launch": 1571840 + 0},
 }
 
 
@@ -487,7 +487,7 @@ def run_xy(args):
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = xy_cpu_baseline(dim, L, T, seed, snap, t_snap, args.cpu_seconds)
-    warm = 0
+    warm = 1 if L ** dim >= (1 << 22) else 0   # the XY path's L2 warm-up kernel
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps,
@@ -665,10 +665,12 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(dim, L, T, seed, snap, t_snap, args.cpu_seconds, q=wl.get("q"))
-    # kernels per step: an L2 warm-up for lattices of 2^22 sites or more, the
-    # persistent schedule's pre-launch reset, the update kernel (or, for the
-    # graph schedule, one call kernel and levels + 3 nodes per update)
-    warm = 1 if L ** dim >= (1 << 22) else 0
+    # kernels per step: an L2 warm-up for lattices of 2^22 sites or more
+    # (except on the Ising cluster path), the persistent schedule's pre-launch
+    # reset, the update kernel (or, for the graph schedule, one call kernel and
+    # levels + 3 nodes per update)
+    warm = 1 if L ** dim >= (1 << 22) and (wl.get("q") or args.schedule in
+                                            ("persistent", "graph")) else 0
     if args.schedule == "graph":
         launches = int(args.steps * (1 + warm) + (levels + 3).sum())
     elif args.schedule == "persistent":

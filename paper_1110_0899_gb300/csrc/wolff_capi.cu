@@ -120,7 +120,6 @@ StepParams make_params(const wolff_ctx *c) {
     p.burst = (uint32_t)c->burst;
     p.budget_ns = 0;
     p.q = c->q;
-    p.prefetch_bytes = 0;
     p.xy_tab = c->xy_tab;
     p.xy_coef = c->xy_coef;
     p.xy_kk = c->xy_kk;
@@ -430,12 +429,12 @@ wolff_status wolff_step(wolff_ctx *c, uint64_t n_updates, void *d_records) {
     p.records = reinterpret_cast<wolff_record *>(d_records);
     p.n = n_updates;
     cudaError_t e;
-    // a large lattice may have been pushed out of L2 since the last call: the
-    // Ising cluster kernel prefetches it itself, the other paths get a kernel
+    // a large lattice may have been pushed out of L2 since the last call.  The
+    // level-synchronous paths stream it back first; the Ising cluster path,
+    // whose window mode touches scattered lines of tiny clusters, measured
+    // faster without (the prefetch launch cost more than the misses it saved)
     const bool big = c->N >= (1u << 22);
-    const bool in_kernel = !c->potts && !c->xy && c->schedule == WOLFF_SCHED_CLUSTER;
-    if (big && in_kernel) p.prefetch_bytes = c->N;
-    if (big && !in_kernel) {
+    if (big && (c->potts || c->xy || c->schedule != WOLFF_SCHED_CLUSTER)) {
         e = launch_prefetch_l2(c->spins, (unsigned long long)c->N * (c->xy ? 4u : 1u), c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "prefetch");
     }

@@ -109,7 +109,6 @@ struct StepParams {
     uint32_t burst;             // cluster schedule: window mode, growth levels per round (0 = off)
     unsigned long long budget_ns;   // cluster schedule: stop after this much device time (0 = none)
     uint32_t q;                 // Potts: number of colours (the Ising kernels ignore it)
-    unsigned long long prefetch_bytes;   // cluster schedule: spins to pull into L2 at kernel start
     // XY (the other kernels ignore these): the sites are 32-bit words
     // (angle | claim bit), spins points at them
     const int32_t *xy_tab;      // fixed-point quarter-wave cosine table, 16385 entries

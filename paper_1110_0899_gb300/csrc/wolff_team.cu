@@ -1182,15 +1182,6 @@ __global__ void __launch_bounds__(512, 1) k_team(StepParams single, const StepPa
     __shared__ TeamShared sh;
     const unsigned int job = blockIdx.x / cl.num_blocks();
     const StepParams p = table ? table[job] : single;
-    if (p.prefetch_bytes) {
-        // pull the lattice into L2 (it may have been evicted since the last
-        // launch); the growth starts while the lines stream in
-        const unsigned long long stride = (unsigned long long)cl.num_blocks() * blockDim.x * 128ull;
-        for (unsigned long long off =
-                 ((unsigned long long)cl.block_rank() * blockDim.x + threadIdx.x) * 128ull;
-             off < p.prefetch_bytes; off += stride)
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(p.spins + off));
-    }
     if (cl.block_rank() != 0) {
         team_worker<DIM>(p, sh, cl, wc);
         return;

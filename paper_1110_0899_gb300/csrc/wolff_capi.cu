@@ -157,7 +157,7 @@ int max_cluster_size(int dim, int threads) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(16);
     cfg.blockDim = dim3((unsigned)threads);
-    cfg.dynamicSmemBytes = window_smem_bytes(threads, kPlainWindowSlots, 16);
+    cfg.dynamicSmemBytes = window_smem_bytes(dim, threads, kPlainWindowSlots, 16);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)cfg.dynamicSmemBytes) != cudaSuccess) {
         cudaGetLastError();

@@ -153,7 +153,8 @@ struct WinCfg {
 };
 constexpr int kDefaultWindowLevels = 32;  // growth levels per warp between commit rounds
 const void *team_kernel(int dim);
-size_t window_smem_bytes(int threads, int window_slots, int cluster_size);
+uint32_t window_cap(int dim, int threads);
+size_t window_smem_bytes(int dim, int threads, int window_slots, int cluster_size);
 cudaError_t launch_team(int dim, const StepParams &single, const StepParams *d_table, int njobs,
                         int cluster_size, int threads, int window_slots, cudaStream_t s);
 

@@ -58,7 +58,7 @@ enum : unsigned int { kTeamLevels = 1, kTeamFinish = 2, kTeamExit = 3, kTeamBurs
 // whose cluster outgrows the cap (or whose flips do not fit the map) stops the
 // window; it runs the ordinary way.
 constexpr int kWinMaxWarps = 16;
-constexpr uint32_t kWinCap = 64;            // members per speculative update (128 at <= 8 warps)
+constexpr uint32_t kWinCap = 64;            // members per speculative update (see window_cap)
 constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint32_t kWinMaxStall = 4096;     // rounds without a commit before giving up
@@ -1196,10 +1196,18 @@ const void *team_kernel(int dim) {
                     : reinterpret_cast<const void *>(&k_team<3>);
 }
 
-size_t window_smem_bytes(int threads, int window_slots, int cluster_size) {
-    if (window_slots <= 0) return 0;
+// Members per speculative update: 64 with 16 warps per CTA in 2D, 128 in 3D
+// (where the random-start clusters reach ~90) and whenever a CTA has 8 warps
+// or fewer.  The per-warp hash sets (2 cap entries each) fill at most half of
+// the TeamShared raw area.
+uint32_t window_cap(int dim, int threads) {
     const uint32_t W = min((uint32_t)threads / 32u, (uint32_t)kWinMaxWarps);
-    const uint32_t cap = W <= 8 ? 2 * kWinCap : kWinCap;
+    return (W <= 8 || dim == 3) ? 2 * kWinCap : kWinCap;
+}
+
+size_t window_smem_bytes(int dim, int threads, int window_slots, int cluster_size) {
+    if (window_slots <= 0) return 0;
+    const size_t cap = window_cap(dim, threads);
     const size_t S = (size_t)window_slots;
     return (S * cap + 9 * S + 1 + kWinScalars + 4 * S * (size_t)cluster_size) * sizeof(uint32_t) +
            S * cap;
@@ -1217,11 +1225,8 @@ cudaError_t launch_team(int dim, const StepParams &single, const StepParams *d_t
     }
     WinCfg wc;
     wc.slots = (uint32_t)window_slots;
-    {
-        const uint32_t W = min((uint32_t)threads / 32u, (uint32_t)kWinMaxWarps);
-        wc.cap = W <= 8 ? 2 * kWinCap : kWinCap;
-    }
-    const size_t dyn = window_smem_bytes(threads, window_slots, cluster_size);
+    wc.cap = window_cap(dim, threads);
+    const size_t dyn = window_smem_bytes(dim, threads, window_slots, cluster_size);
     if (dyn > 0) {
         cudaError_t e =
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);

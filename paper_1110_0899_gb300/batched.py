@@ -134,12 +134,14 @@ def autotune(specs, probe_updates=40, seed_offset=10_000_000, use_cache=True, ve
         lats = [WolffLattice(s["dim"], s["L"], s["T"], seed=s["seed"] + seed_offset)
                 for s in specs]
         r = BatchedRunner(lats, p)
-        if k == 0:   # first-launch set-up outside the timing
-            warm = [WolffLattice(2, 8, 2.0, seed=1) for _ in range(2)]
-            BatchedRunner(warm, Plan([([0, 1], 2, 128)])).run(2, records=False)
-            torch.cuda.synchronize()
-            for x in warm:
-                x.close()
+        # first launches of a team shape (kernel attributes, shared-memory
+        # carve-out) happen outside the timing, on two throwaway lattices
+        warm = [WolffLattice(2, 8, 2.0, seed=1) for _ in range(2)]
+        for _, cs, th in p.groups:
+            BatchedRunner(warm, Plan([([0, 1], cs, th)])).run(2, records=False)
+        torch.cuda.synchronize()
+        for x in warm:
+            x.close()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         bufs = r.run(probe_updates, records=True)

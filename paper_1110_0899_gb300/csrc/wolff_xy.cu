@@ -87,23 +87,25 @@ __device__ __forceinline__ unsigned long long xy_threshold(long long prod, const
 
 // The bond test r < floor(2^32 (1 - e^-y)), decided first in single
 // precision.  p_f = 1 - expf(-y_f) with y_f = float(kk) * float(prod):
-// y_f = y (1 + e), |e| <= 3 * 2^-24, and expf is within 2 ulp (CUDA
-// programming guide, appendix on mathematical functions), so
-// |p_f - p| <= max_y (e^-y y 3 2^-24) + 2 * 2^-23 < 3.2e-7, and the exact
-// threshold x = p 2^32 lies within kXyMargin 2^32 of p_f 2^32.  Outside that
-// band the single-precision answer is the exact one (an integer r with
-// r + 1 <= x is below floor(x); r >= x is not); inside it (a few times 1e-6
-// of the tests) the double-precision path decides.
-constexpr double kXyMargin = 2.0e-6;
+// y_f = y (1 + e), |e| <= 3 * 2^-24, expf is within 2 ulp (CUDA programming
+// guide, appendix on mathematical functions), and the subtraction rounds by
+// at most 2^-24, so |p_f - p| < max_y (e^-y y 3 2^-24) + 2 * 2^-23 + 2^-24
+// < 4e-7.  The bounds (p_f -+ m) 2^32 are rounded by at most 512 units of r
+// and float(r) by at most 128, all far inside the margin m 2^32 = 8590
+// units: r + 1 <= lower bound proves r < floor(p 2^32) (accept), r >= upper
+// bound proves r >= floor(p 2^32) (reject).  Between the bounds (a few times
+// 1e-6 of the tests) the double-precision path decides.  The fast path uses
+// no double-precision operation.
+constexpr float kXyMargin = 2.0e-6f;
 
 __device__ __forceinline__ bool xy_bond_active(uint32_t r, long long prod, float kk_f,
                                                const StepParams &p) {
     if (prod <= 0) return false;
     const float yf = __fmul_rn(kk_f, __ll2float_rn(prod));
-    const double pf = 1.0 - (double)expf(-yf);
-    const double ru = (double)r;
-    if (ru + 1.0 <= (pf - kXyMargin) * 4294967296.0) return true;
-    if (ru >= (pf + kXyMargin) * 4294967296.0) return false;
+    const float pf = __fsub_rn(1.0f, expf(-yf));
+    const float rf = __uint2float_rn(r);
+    if (__fadd_rn(rf, 1.0f) <= __fmul_rn(__fsub_rn(pf, kXyMargin), 4294967296.0f)) return true;
+    if (rf >= __fmul_rn(__fadd_rn(pf, kXyMargin), 4294967296.0f)) return false;
     return (unsigned long long)r < xy_threshold(prod, p);
 }
 

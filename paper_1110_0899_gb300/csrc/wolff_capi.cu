@@ -60,7 +60,7 @@ struct wolff_ctx {
     unsigned long long wait_ns = 2000000000ull;
     uint32_t t_up = 128, t_down = 64;
     bool thresholds_set = false;
-    int burst = kDefaultWindowLevels;   // window mode: growth levels per round (0 = off)
+    int win_levels = kDefaultWindowLevels;   // window mode: growth levels per round (0 = off)
     int cluster = 8;
     int max_cluster = 8;
     std::string err;
@@ -117,7 +117,7 @@ StepParams make_params(const wolff_ctx *c) {
     p.wait_ns = c->wait_ns;
     p.t_up = c->t_up;
     p.t_down = c->t_down;
-    p.burst = (uint32_t)c->burst;
+    p.win_levels = (uint32_t)c->win_levels;
     p.budget_ns = 0;
     p.q = c->q;
     p.xy_tab = c->xy_tab;
@@ -418,7 +418,7 @@ wolff_status wolff_set_local_thresholds(wolff_ctx *c, uint32_t t_up, uint32_t t_
 wolff_status wolff_set_burst(wolff_ctx *c, int enable) {
     if (!c) return WOLFF_EINVAL;
     if (enable < 0) return fail(c, WOLFF_EINVAL, "enable must be >= 0");
-    c->burst = enable == 0 ? 0 : enable == 1 ? kDefaultWindowLevels : (enable > 64 ? 64 : enable);
+    c->win_levels = enable == 0 ? 0 : enable == 1 ? kDefaultWindowLevels : (enable > 64 ? 64 : enable);
     return WOLFF_OK;
 }
 

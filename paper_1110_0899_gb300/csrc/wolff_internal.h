@@ -106,7 +106,7 @@ struct StepParams {
     unsigned long long wait_ns; // bound of every device-side wait
     uint32_t t_up;              // leader hands a frontier larger than this to the grid
     uint32_t t_down;            // grid hands a frontier this small back to the leader
-    uint32_t burst;             // cluster schedule: window mode, growth levels per round (0 = off)
+    uint32_t win_levels;        // cluster schedule: window mode, growth levels per round (0 = off)
     unsigned long long budget_ns;   // cluster schedule: stop after this much device time (0 = none)
     uint32_t q;                 // Potts: number of colours (the Ising kernels ignore it)
     // XY (the other kernels ignore these): the sites are 32-bit words

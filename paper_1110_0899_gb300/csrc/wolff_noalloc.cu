@@ -92,7 +92,7 @@ extern "C" wolff_status wolff_step_static(int dim, int L, double J, double T, ui
     p.wait_ns = 2000000000ull;
     p.t_up = 512;
     p.t_down = 256;
-    p.burst = 0;
+    p.win_levels = 0;
     p.budget_ns = 0;
     p.q = 2;
 

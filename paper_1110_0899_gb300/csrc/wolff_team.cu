@@ -31,7 +31,7 @@ namespace wolff {
 
 namespace {
 
-enum : unsigned int { kTeamLevels = 1, kTeamFinish = 2, kTeamExit = 3, kTeamBurst = 4 };
+enum : unsigned int { kTeamLevels = 1, kTeamFinish = 2, kTeamExit = 3, kTeamWindow = 4 };
 
 // ---- window mode -------------------------------------------------------------
 // While clusters are small, consecutive updates rarely touch the same sites.
@@ -75,8 +75,8 @@ struct TeamShared {
     unsigned int wcut;          // lowest update of the window that cannot commit (atomic)
     unsigned int wlimit;        // lowest update found too big (atomic)
     unsigned int wstop;         // time budget spent
-    unsigned int bflag;
-    unsigned int bstop;
+    unsigned int wflag;         // leader: this update starts (or resumes) a window
+    unsigned int budget_stop;   // leader: the time budget stops the launch here
     unsigned int wlast[2];      // |C| and levels of the last committed update
     unsigned long long wlevels; // growth levels of all warps (atomic)
     long long wsum[3][kWinMaxWarps];  // per-warp totals of the record scan
@@ -186,7 +186,7 @@ __device__ void team_worker(const StepParams &p, TeamShared &sh, cg::cluster_gro
             team_levels<DIM>(p, sh, cl, lo, hi, level, sig0bit, tlo, thi, &finished);
         } else if (kind == kTeamFinish) {
             team_finish<DIM>(p, sh, cl, hi, sig0bit);
-        } else if (kind == kTeamBurst) {
+        } else if (kind == kTeamWindow) {
             long long E = 0, M = 0;
             unsigned long long tc = 0, rounds = 0;
             uint32_t lc = 0, ll = 0;
@@ -202,15 +202,16 @@ __device__ void team_worker(const StepParams &p, TeamShared &sh, cg::cluster_gro
     }
 }
 
-
-__device__ __forceinline__ uint32_t burst_hash(uint32_t key, uint32_t slots) {
+// ---- the warps' cluster hash sets --------------------------------------------
+// Multiplicative (Fibonacci) hashing: the top log2(slots) bits of key * 2^32/phi.
+__device__ __forceinline__ uint32_t set_hash(uint32_t key, uint32_t slots) {
     return (key * 0x9E3779B1u) >> (32 - __ffs(slots) + 1);
 }
 
 // Inserts key into an open-addressing set of `slots` entries (power of two).
 // Returns 1 if newly inserted, 0 if present, -1 if the set is full.
-__device__ __forceinline__ int burst_insert(uint32_t *set, uint32_t slots, uint32_t key) {
-    uint32_t h = burst_hash(key, slots);
+__device__ __forceinline__ int set_insert(uint32_t *set, uint32_t slots, uint32_t key) {
+    uint32_t h = set_hash(key, slots);
     for (uint32_t probe = 0; probe < slots; ++probe) {
         const uint32_t prev = atomicCAS(set + h, kEmptyKey, key);
         if (prev == kEmptyKey) return 1;
@@ -220,8 +221,8 @@ __device__ __forceinline__ int burst_insert(uint32_t *set, uint32_t slots, uint3
     return -1;
 }
 
-__device__ __forceinline__ bool burst_contains(const uint32_t *set, uint32_t slots, uint32_t key) {
-    uint32_t h = burst_hash(key, slots);
+__device__ __forceinline__ bool set_contains(const uint32_t *set, uint32_t slots, uint32_t key) {
+    uint32_t h = set_hash(key, slots);
     for (uint32_t probe = 0; probe < slots; ++probe) {
         const uint32_t v = set[h];
         if (v == key) return true;
@@ -230,7 +231,6 @@ __device__ __forceinline__ bool burst_contains(const uint32_t *set, uint32_t slo
     }
     return false;
 }
-
 
 // The window's per-CTA state in dynamic shared memory: S slots of `cap`
 // members (packed coordinates), each slot's result (|C|, levels, dE_bond / 2,
@@ -334,7 +334,7 @@ __device__ __forceinline__ void win_start(const StepParams &p, unsigned long lon
     const uint32_t i0 = seed_site(p, t);
     sig0bit = __ldca(p.spins + i0) & 1u;
     if (lane == 0) {
-        burst_insert(hset, hslots, i0);
+        set_insert(hset, hslots, i0);
         members[0] = pack_index<DIM>(p.g, i0);
     }
     __syncwarp();
@@ -425,7 +425,7 @@ __device__ __forceinline__ bool win_level(const StepParams &p, uint32_t *members
             for (int s = 0; s < 2 * DIM; ++s) {
                 prev[s] = 0;
                 if (cand & (1u << s))
-                    prev[s] = atomicCAS(hset + burst_hash(nb2.idx[s], hslots), kEmptyKey,
+                    prev[s] = atomicCAS(hset + set_hash(nb2.idx[s], hslots), kEmptyKey,
                                         nb2.idx[s]);
             }
 #pragma unroll
@@ -434,7 +434,7 @@ __device__ __forceinline__ bool win_level(const StepParams &p, uint32_t *members
                 int ins;
                 if (prev[s] == kEmptyKey) ins = 1;
                 else if (prev[s] == nb2.idx[s]) ins = 0;
-                else ins = burst_insert(hset, hslots, nb2.idx[s]);
+                else ins = set_insert(hset, hslots, nb2.idx[s]);
                 if (ins > 0) fresh |= 1u << s;
                 if (ins < 0) full = true;
             }
@@ -482,14 +482,14 @@ __device__ __forceinline__ int win_boundary(const StepParams &p, const uint32_t 
         uint8_t cur[2 * DIM];
 #pragma unroll
         for (int s = 0; s < 2 * DIM; ++s) {
-            home[s] = hset[burst_hash(nb2.idx[s], hslots)];
+            home[s] = hset[set_hash(nb2.idx[s], hslots)];
             cur[s] = __ldca(p.spins + nb2.idx[s]);
         }
 #pragma unroll
         for (int s = 0; s < 2 * DIM; ++s) {
             // the home slot settles membership unless it holds another site
             const bool member = home[s] == nb2.idx[s] ||
-                                (home[s] != kEmptyKey && burst_contains(hset, hslots, nb2.idx[s]));
+                                (home[s] != kEmptyKey && set_contains(hset, hslots, nb2.idx[s]));
             if (member) continue;
             dE += ((cur[s] & 1u) == sig0bit) ? -1 : 1;
         }
@@ -645,7 +645,7 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
     const uint32_t rank = cl.block_rank(), cs = cl.num_blocks();
     const uint32_t W = min((uint32_t)(blockDim.x >> 5), (uint32_t)kWinMaxWarps);
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t S = wc.slots, cap = wc.cap, hslots = 2 * cap, K = p.burst;
+    const uint32_t S = wc.slots, cap = wc.cap, hslots = 2 * cap, K = p.win_levels;
     const uint32_t P = S * cs;
     TeamShared *lead = cl.map_shared_rank(&sh, 0);
     uint32_t *hset = &sh.front[0][0] + (warp % kWinMaxWarps) * hslots;
@@ -952,7 +952,7 @@ __device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_gro
     // window policy (thread 0 decides, the CTA follows): windows run while the
     // recent clusters are small; a cluster too big for one pauses them
     unsigned int cooldown = 0, fail_streak = 0, skip_next = 0;
-    unsigned long long bursts_done = 0, burst_calls = 0;
+    unsigned long long window_updates = 0, window_rounds = 0;
     unsigned long long win_ns[5] = {0, 0, 0, 0, 0};
     // an open window (left for an update too big for it) resumes at
     // update win_u0 + win_next
@@ -963,17 +963,17 @@ __device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_gro
     unsigned long long u = 0;
     for (; u < p.n; ++u) {
         if (p.budget_ns && u > 0) {   // a time-budgeted job stops at an update boundary
-            if (t0) sh.bstop = (global_ns() - launch_t0 > p.budget_ns) ? 1u : 0u;
+            if (t0) sh.budget_stop = (global_ns() - launch_t0 > p.budget_ns) ? 1u : 0u;
             __syncthreads();
-            if (sh.bstop) break;
+            if (sh.budget_stop) break;
         }
-        if (p.burst && wc.slots && p.n - u >= 2) {
+        if (p.win_levels && wc.slots && p.n - u >= 2) {
             // a window stopped by an update too big for it leaves that update
             // to the ordinary path directly, then resumes with what it holds
             const bool resume = win_open && u == win_u0 + win_next;
-            if (t0) sh.bflag = (resume || (cooldown == 0 && !skip_next)) ? 1u : 0u;
+            if (t0) sh.wflag = (resume || (cooldown == 0 && !skip_next)) ? 1u : 0u;
             __syncthreads();
-            if (sh.bflag) {
+            if (sh.wflag) {
                 const unsigned long long u0w = resume ? win_u0 : u;
                 const uint32_t n_rem =
                     resume ? win_nrem : (uint32_t)min(p.n - u, 0x7FFFFFFFull);
@@ -984,14 +984,14 @@ __device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_gro
                     sh.wlevels = 0;
                 }
                 if (has_team)
-                    announce(sh, cl, kTeamBurst, (uint32_t)u0w, (uint32_t)(u0w >> 32), n_rem,
+                    announce(sh, cl, kTeamWindow, (uint32_t)u0w, (uint32_t)(u0w >> 32), n_rem,
                              resume ? 1u : 0u, c_start);
                 else
                     __syncthreads();
                 bool resumable = false;
                 const uint32_t c =
                     team_window<DIM>(p, sh, cl, wc, u0w, n_rem, launch_t0, E, M, total_C, last_C,
-                                     last_levels, burst_calls, win_ns, c_start, resume,
+                                     last_levels, window_rounds, win_ns, c_start, resume,
                                      resumable);
                 const uint32_t done = c - c_start;
                 // a resumed window that commits nothing is closed
@@ -1000,7 +1000,7 @@ __device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_gro
                 win_nrem = n_rem;
                 win_next = c + 1;
                 if (t0) {
-                    bursts_done += done;
+                    window_updates += done;
                     if (done > 0 && c < n_rem && !sh.wstop) skip_next = 1;
                     // back off only while fresh windows keep failing at their
                     // first update (the large-cluster regime): 0, 1, 3, ..., 63
@@ -1163,8 +1163,8 @@ __device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_gro
         ctl->st_ns_finish += ns_finish;
         ctl->st_handoffs += handoffs;
         ctl->st_grid_finishes += team_fin;
-        ctl->st_burst_updates += bursts_done;
-        ctl->st_bursts += burst_calls;
+        ctl->st_burst_updates += window_updates;
+        ctl->st_bursts += window_rounds;
         for (int k = 0; k < 4; ++k) ctl->st_ns_win[k] += win_ns[k];
         ctl->st_win_levels += win_ns[4];
         ctl->st_end_ns = global_ns();

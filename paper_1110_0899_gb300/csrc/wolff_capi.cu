@@ -183,6 +183,26 @@ cudaError_t empty_list(wolff_ctx *c) {
     return cudaMemsetAsync(c->list, 0xFF, (size_t)c->N * sizeof(uint32_t), c->stream);
 }
 
+// The Ising state transfers borrow the first N bytes of the cluster list as
+// int8 scratch; this restores them (the rest of the list is untouched).
+cudaError_t empty_scratch(wolff_ctx *c) {
+    return cudaMemsetAsync(c->list, 0xFF, c->N, c->stream);
+}
+
+// Enqueues an Ising lattice upload (int8 +-1 from host memory), the next
+// update index and the recount of E_bond and M; no synchronisation.
+cudaError_t enqueue_ising_upload(wolff_ctx *c, const int8_t *h_spins, uint64_t t) {
+    int8_t *scratch = reinterpret_cast<int8_t *>(c->list);
+    const StepParams p = make_params(c);
+    cudaError_t e = cudaMemcpyAsync(scratch, h_spins, c->N, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_reset_ctl(c->ctl, t, c->stream);
+    if (e == cudaSuccess)
+        e = launch_from_pm1_measure(c->dim, c->spins, scratch, p.g, c->ctl, c->stream);
+    if (e == cudaSuccess) e = empty_scratch(c);
+    if (e == cudaSuccess) c->t_host = t;
+    return e;
+}
+
 int default_blocks(const wolff_ctx *c) {
     int b = (int)(c->N / 2048u);
     if (b < 1) b = 1;
@@ -517,7 +537,7 @@ wolff_status wolff_get_state(wolff_ctx *c, int8_t *h_spins, uint64_t *t) {
         cudaError_t e = launch_to_pm1(scratch, c->spins, c->N, c->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(h_spins, scratch, c->N, cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess) e = empty_list(c);
+        if (e == cudaSuccess) e = empty_scratch(c);
         if (e != cudaSuccess) return cuda_fail(c, e, "get_state");
     }
     DevCtl h;
@@ -548,15 +568,8 @@ wolff_status wolff_set_state(wolff_ctx *c, const int8_t *h_spins, uint64_t t) {
         }
         return st;
     }
-    int8_t *scratch = reinterpret_cast<int8_t *>(c->list);
-    const StepParams p = make_params(c);
-    cudaError_t e = cudaMemcpyAsync(scratch, h_spins, c->N, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = launch_reset_ctl(c->ctl, t, c->stream);
-    if (e == cudaSuccess) e = launch_from_pm1(c->spins, scratch, c->N, c->ctl, c->stream);
-    if (e == cudaSuccess) e = launch_measure_full(c->dim, c->spins, p.g, c->ctl, 1, c->stream);
-    if (e == cudaSuccess) e = empty_list(c);
+    cudaError_t e = enqueue_ising_upload(c, h_spins, t);
     if (e != cudaSuccess) return cuda_fail(c, e, "set_state");
-    c->t_host = t;
     return sync_and_check(c, nullptr);
 }
 
@@ -566,8 +579,16 @@ wolff_status wolff_run_host(wolff_ctx *c, const int8_t *h_spins_in, uint64_t t_i
     if (c->xy) return fail(c, WOLFF_EUNSUPPORTED, "no host-buffer path for XY contexts");
     wolff_status s;
     if (h_spins_in) {
-        s = wolff_set_state(c, h_spins_in, t_in);
-        if (s != WOLFF_OK) return s;
+        // the upload is enqueued, not waited for: a rejected lattice (entries
+        // other than +-1, read as -1) is reported by the one synchronisation
+        // at the end of the call
+        if (c->potts) {
+            s = wolff_set_state(c, h_spins_in, t_in);
+            if (s != WOLFF_OK) return s;
+        } else {
+            cudaError_t e = enqueue_ising_upload(c, h_spins_in, t_in);
+            if (e != cudaSuccess) return cuda_fail(c, e, "upload");
+        }
     }
     wolff_record *d_rec = nullptr;
     if (h_records && n_updates) {

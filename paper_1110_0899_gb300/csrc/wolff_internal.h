@@ -130,6 +130,8 @@ cudaError_t launch_measure_full(int dim, const uint8_t *spins, Geometry g,
                                 DevCtl *ctl, int set_chain, cudaStream_t s);
 cudaError_t launch_from_pm1(uint8_t *spins, const int8_t *src, uint32_t N,
                             DevCtl *ctl, cudaStream_t s);
+cudaError_t launch_from_pm1_measure(int dim, uint8_t *spins, const int8_t *src, Geometry g,
+                                    DevCtl *ctl, cudaStream_t s);
 cudaError_t launch_to_pm1(int8_t *dst, const uint8_t *spins, uint32_t N,
                           cudaStream_t s);
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, const uint32_t *ctr,

@@ -140,6 +140,55 @@ __global__ void k_to_pm1(int8_t *dst, const uint8_t *spins, uint32_t N) {
         dst[i] = (spins[i] & 1) ? 1 : -1;
 }
 
+// Upload path in one pass: converts an int8 +-1 lattice into spin bytes and
+// sums E_bond and M from the same input (forward neighbours read from src);
+// entries other than +-1 become -1 and latch WOLFF_EINVAL.
+template <int DIM>
+__global__ void k_from_pm1_measure(uint8_t *spins, const int8_t *src, Geometry g, DevCtl *ctl) {
+    const uint32_t rows = g.N / g.L;
+    long long e = 0, m = 0;
+    for (uint32_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        const uint32_t y = row % g.L;
+        const uint32_t base = row * g.L;
+        const uint32_t yup = (y + 1 == g.L) ? base + g.L - g.LL : base + g.L;
+        uint32_t zup = 0;
+        if (DIM == 3) {
+            const uint32_t z = row / g.L;
+            zup = (z + 1 == g.L) ? base + g.LL - g.N : base + g.LL;
+        }
+        for (uint32_t x = threadIdx.x; x < g.L; x += blockDim.x) {
+            const int v = src[base + x];
+            if (v != 1 && v != -1) raise_status(ctl, WOLFF_EINVAL, base + x);
+            spins[base + x] = v == 1 ? 0x03 : 0x00;
+            const int si = v == 1 ? 1 : -1;
+            const uint32_t xr = (x + 1 == g.L) ? 0 : x + 1;
+            int nbsum = (src[base + xr] == 1 ? 1 : -1) + (src[yup + x] == 1 ? 1 : -1);
+            if (DIM == 3) nbsum += src[zup + x] == 1 ? 1 : -1;
+            e += si * nbsum;
+            m += si;
+        }
+    }
+    e = block_sum(e);
+    m = block_sum(m);
+    if (threadIdx.x == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->full_E), (unsigned long long)e);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->full_M), (unsigned long long)m);
+    }
+}
+
+cudaError_t launch_from_pm1_measure(int dim, uint8_t *spins, const int8_t *src, Geometry g,
+                                    DevCtl *ctl, cudaStream_t s) {
+    k_zero_full<<<1, 1, 0, s>>>(ctl);
+    const unsigned blocks = (unsigned)grid_for(g.N / g.L, 8192ull);
+    const unsigned threads = g.L >= 256 ? 256 : 64;
+    if (dim == 2)
+        k_from_pm1_measure<2><<<blocks, threads, 0, s>>>(spins, src, g, ctl);
+    else
+        k_from_pm1_measure<3><<<blocks, threads, 0, s>>>(spins, src, g, ctl);
+    k_full_to_chain<<<1, 1, 0, s>>>(ctl);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_from_pm1(uint8_t *spins, const int8_t *src, uint32_t N, DevCtl *ctl,
                             cudaStream_t s) {
     const unsigned blocks = grid_for((N + 255) / 256, 4096ull);

@@ -197,6 +197,39 @@ def test_host_buffer_path():
     rec, spins = lat.run_host(80, spins_in=s0, t_in=40)
     assert_records_equal(rec, ref, "run_host")
     assert np.array_equal(spins, s_ref)
+    # the upload and the updates are enqueued behind one synchronisation: a
+    # lattice entry other than +-1 is still reported, and the context then
+    # takes a valid lattice again
+    bad = s0.copy()
+    bad[5] = 3
+    with pytest.raises(w.WolffError) as ei:
+        lat.run_host(10, spins_in=bad, t_in=0)
+    assert ei.value.status == w.WOLFF_EINVAL
+    rec, spins = lat.run_host(80, spins_in=s0, t_in=40)
+    assert_records_equal(rec, ref, "run_host after a rejected upload")
+    assert np.array_equal(spins, s_ref)
+    lat.close()
+
+
+@pytest.mark.parametrize("dim,L", [(2, 4096), (3, 256)])
+def test_full_size_state_transfer(dim, L):
+    """The fused upload (int8 +-1 -> spin bytes, E_bond and M in the same
+    pass) and the download at the benchmark's sizes: E_bond and M equal the
+    oracle's definitions, the lattice comes back unchanged, and the cluster
+    list is left empty for the next update (the next 50 updates match)."""
+    torch, w = require_cuda()
+    rng = np.random.default_rng(dim)
+    s = rng.choice(np.array([-1, 1], np.int8), size=L ** dim)
+    lat = w.WolffLattice(dim, L, 1.0 if dim == 2 else 4.5115, seed=31)
+    lat.set_state(s, 77)
+    E, M, _ = lat.measure()
+    assert (E, M) == (oracle.energy_bond(dim, L, s), oracle.magnetisation(dim, L, s))
+    back, t = lat.get_state()
+    assert t == 77 and np.array_equal(back, s)
+    rec = lat.step(50)
+    T = 1.0 if dim == 2 else 4.5115
+    ref, s_ref = oracle_trajectory(dim, L, T, 31, 50, t0=77, s=s)
+    assert_records_equal(rec, ref, "after a full-size upload")
     lat.close()
 
 

@@ -243,6 +243,19 @@ wolff_status wolff_get_state(wolff_ctx *ctx, int8_t *h_spins, uint64_t *t);
  * +-1.  Synchronises. */
 wolff_status wolff_set_state(wolff_ctx *ctx, const int8_t *h_spins, uint64_t t);
 
+/* Bit-packed state transfers (Ising contexts): the lattice as ceil(N / 32)
+ * 32-bit words, bit (i mod 32) of word i / 32 set when site i is +1 (site
+ * order as above; the unused high bits of the last word are ignored on input
+ * and zero on output).  One bit per site moves 8x fewer bytes over the host
+ * link than the int8 form; the device keeps one byte per site.  Otherwise as
+ * wolff_set_state, wolff_get_state and wolff_run_host (every input is valid,
+ * so no EINVAL for entries).  Potts and XY contexts: WOLFF_EUNSUPPORTED. */
+wolff_status wolff_set_state_bits(wolff_ctx *ctx, const uint32_t *h_bits, uint64_t t);
+wolff_status wolff_get_state_bits(wolff_ctx *ctx, uint32_t *h_bits, uint64_t *t);
+wolff_status wolff_run_host_bits(wolff_ctx *ctx, const uint32_t *h_bits_in, uint64_t t_in,
+                                 uint64_t n_updates, wolff_record *h_records,
+                                 uint32_t *h_bits_out);
+
 /* Chooses the schedule and the CTA shape of the growth kernels (0 = keep /
  * library default).  For PERSISTENT and GRAPH grid_blocks is the number of
  * CTAs (PERSISTENT caps it at what can be co-resident); for CLUSTER it is the

@@ -94,6 +94,9 @@ def load_library():
         "measure_full": (i, [v, P(i64), P(i64)]),
         "wolff_get_state": (i, [v, v, P(u64)]),
         "wolff_set_state": (i, [v, v, u64]),
+        "wolff_get_state_bits": (i, [v, v, P(u64)]),
+        "wolff_set_state_bits": (i, [v, v, u64]),
+        "wolff_run_host_bits": (i, [v, v, u64, u64, v, v]),
         "wolff_set_schedule": (i, [v, i, i, i]),
         "wolff_get_info": (i, [v, P(_Info)]),
         "wolff_set_local_thresholds": (i, [v, u32, u32]),
@@ -218,15 +221,36 @@ def wolff_set_state(handle, spins, t):
            handle)
 
 
-def wolff_run_host(handle, N, n_updates, spins_in=None, t_in=0, records=True, spins_out=True):
-    """Host-buffer path: optional upload, n updates, records and lattice back."""
+def wolff_run_host(handle, N, n_updates, spins_in=None, t_in=0, records=True, spins_out=True,
+                   rec_out=None):
+    """Host-buffer path: optional upload, n updates, records and lattice back.
+    rec_out: optional host array of RECORD_DTYPE (e.g. in pinned memory) that
+    receives the records."""
     sin = None if spins_in is None else np.ascontiguousarray(spins_in, dtype=np.int8)
-    rec = np.zeros(int(n_updates), dtype=RECORD_DTYPE) if records else None
+    if records:
+        rec = rec_out if rec_out is not None else np.zeros(int(n_updates), dtype=RECORD_DTYPE)
+    else:
+        rec = None
     sout = np.empty(N, dtype=np.int8) if spins_out else None
     ptr = lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data)  # noqa: E731
     _check(load_library().wolff_run_host(handle, ptr(sin), int(t_in), int(n_updates), ptr(rec),
                                          ptr(sout)), handle)
     return rec, sout
+
+
+def pack_spins(spins):
+    """int8 +-1 lattice -> bit-packed uint32 words (bit i of word i/32 = +1)."""
+    b = np.packbits(np.asarray(spins) == 1, bitorder="little")
+    words = (len(spins) + 31) // 32
+    out = np.zeros(words * 4, dtype=np.uint8)
+    out[: len(b)] = b
+    return out.view(np.uint32)
+
+
+def unpack_bits(bits, N):
+    """Bit-packed uint32 words -> int8 +-1 lattice of N sites."""
+    b = np.unpackbits(np.asarray(bits, dtype=np.uint32).view(np.uint8), bitorder="little")[:N]
+    return (2 * b.astype(np.int8) - 1).astype(np.int8)
 
 
 def ising_free(handle):
@@ -318,7 +342,53 @@ class WolffLattice:
         wolff_set_state(self.handle, spins, t)
 
     def run_host(self, n, spins_in=None, t_in=0, records=True, spins_out=True):
-        return wolff_run_host(self.handle, self.N, n, spins_in, t_in, records, spins_out)
+        rec_out = None
+        if records:
+            # records land in a pinned buffer kept by the lattice (a direct
+            # DMA), and the caller gets a copy
+            torch = _torch()
+            need = int(n) * RECORD_BYTES
+            if getattr(self, "_h_records", None) is None or self._h_records.numel() < need:
+                self._h_records = torch.empty(max(need, RECORD_BYTES), dtype=torch.uint8,
+                                              pin_memory=True)
+            rec_out = self._h_records.numpy()[:need].view(RECORD_DTYPE)
+        rec, sout = wolff_run_host(self.handle, self.N, n, spins_in, t_in, records, spins_out,
+                                   rec_out)
+        return (rec.copy() if rec is not None else None), sout
+
+    def get_state_bits(self):
+        bits = np.zeros((self.N + 31) // 32, dtype=np.uint32)
+        t = ctypes.c_uint64()
+        _check(load_library().wolff_get_state_bits(self.handle, ctypes.c_void_p(bits.ctypes.data),
+                                                   ctypes.byref(t)), self.handle)
+        return bits, t.value
+
+    def set_state_bits(self, bits, t):
+        bits = np.ascontiguousarray(bits, dtype=np.uint32)
+        if bits.size != (self.N + 31) // 32:
+            raise ValueError("need %d words" % ((self.N + 31) // 32))
+        _check(load_library().wolff_set_state_bits(self.handle, ctypes.c_void_p(bits.ctypes.data),
+                                                   int(t)), self.handle)
+
+    def run_host_bits(self, n, bits_in=None, t_in=0, records=True, bits_out=True):
+        """As run_host with bit-packed lattices (see pack_spins)."""
+        words = (self.N + 31) // 32
+        bin_ = None if bits_in is None else np.ascontiguousarray(bits_in, dtype=np.uint32)
+        if bin_ is not None and bin_.size != words:
+            raise ValueError("need %d words" % words)
+        rec = None
+        if records:
+            torch = _torch()
+            need = int(n) * RECORD_BYTES
+            if getattr(self, "_h_records", None) is None or self._h_records.numel() < need:
+                self._h_records = torch.empty(max(need, RECORD_BYTES), dtype=torch.uint8,
+                                              pin_memory=True)
+            rec = self._h_records.numpy()[:need].view(RECORD_DTYPE)
+        bout = np.empty(words, dtype=np.uint32) if bits_out else None
+        ptr = lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+        _check(load_library().wolff_run_host_bits(self.handle, ptr(bin_), int(t_in), int(n),
+                                                  ptr(rec), ptr(bout)), self.handle)
+        return (rec.copy() if rec is not None else None), bout
 
     def selftest_wait_timeout(self, wait_ns):
         obs = ctypes.c_int()

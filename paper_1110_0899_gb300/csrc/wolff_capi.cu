@@ -57,6 +57,7 @@ struct wolff_ctx {
     uint64_t t_host = 0;
     void *rec_stage = nullptr;
     size_t rec_stage_bytes = 0;
+    DevCtl *h_ctl = nullptr;       // pinned host copy of the control block (nullable)
     unsigned long long wait_ns = 2000000000ull;
     uint32_t t_up = 128, t_down = 64;
     bool thresholds_set = false;
@@ -132,9 +133,13 @@ StepParams make_params(const wolff_ctx *c) {
 wolff_status sync_and_check(wolff_ctx *c, DevCtl *host_copy) {
     DevCtl tmp;
     DevCtl *dst = host_copy ? host_copy : &tmp;
-    cudaError_t e = cudaMemcpyAsync(dst, c->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream);
+    // through the context's pinned copy when it has one (a direct DMA, no
+    // staging through pageable memory)
+    DevCtl *land = c->h_ctl ? c->h_ctl : dst;
+    cudaError_t e = cudaMemcpyAsync(land, c->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "synchronise");
+    if (land != dst) memcpy(dst, land, sizeof(DevCtl));
     c->t_host = dst->t;   // the device's count (a time-budgeted run may stop early)
     if (dst->status != 0) {
         char buf[160];
@@ -158,8 +163,7 @@ int max_cluster_size(int dim, int threads) {
     cfg.gridDim = dim3(16);
     cfg.blockDim = dim3((unsigned)threads);
     cfg.dynamicSmemBytes = window_smem_bytes(dim, threads, kPlainWindowSlots, 16);
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)cfg.dynamicSmemBytes) != cudaSuccess) {
+    if (ensure_team_dyn_smem(dim, cfg.dynamicSmemBytes) != cudaSuccess) {
         cudaGetLastError();
         return 8;
     }
@@ -183,10 +187,52 @@ cudaError_t empty_list(wolff_ctx *c) {
     return cudaMemsetAsync(c->list, 0xFF, (size_t)c->N * sizeof(uint32_t), c->stream);
 }
 
+// Device staging for host-bound records, kept by the context and grown on
+// demand so that repeated calls do not allocate.
+wolff_status ensure_rec_stage(wolff_ctx *c, size_t bytes) {
+    if (bytes <= c->rec_stage_bytes) return WOLFF_OK;
+    cudaStreamSynchronize(c->stream);
+    if (c->rec_stage) cudaFree(c->rec_stage);
+    c->rec_stage = nullptr;
+    c->rec_stage_bytes = 0;
+    if (cudaMalloc(&c->rec_stage, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, WOLFF_ENOMEM, "record staging buffer");
+    }
+    c->rec_stage_bytes = bytes;
+    return WOLFF_OK;
+}
+
 // The Ising state transfers borrow the first N bytes of the cluster list as
 // int8 scratch; this restores them (the rest of the list is untouched).
 cudaError_t empty_scratch(wolff_ctx *c) {
     return cudaMemsetAsync(c->list, 0xFF, c->N, c->stream);
+}
+
+// Enqueues a bit-packed Ising lattice upload (ceil(N/32) words), the next
+// update index and the recount; the words borrow the start of the list.
+cudaError_t enqueue_ising_upload_bits(wolff_ctx *c, const uint32_t *h_bits, uint64_t t) {
+    uint32_t *scratch = c->list;
+    const size_t bytes = ((size_t)c->N + 31) / 32 * sizeof(uint32_t);
+    const StepParams p = make_params(c);
+    cudaError_t e = cudaMemcpyAsync(scratch, h_bits, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_reset_ctl(c->ctl, t, c->stream);
+    if (e == cudaSuccess)
+        e = launch_from_bits_measure(c->dim, c->spins, scratch, p.g, c->ctl, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0xFF, bytes, c->stream);
+    if (e == cudaSuccess) c->t_host = t;
+    return e;
+}
+
+// Enqueues a bit-packed download of the lattice into host memory.
+cudaError_t enqueue_ising_download_bits(wolff_ctx *c, uint32_t *h_bits) {
+    uint32_t *scratch = c->list;
+    const size_t bytes = ((size_t)c->N + 31) / 32 * sizeof(uint32_t);
+    cudaError_t e = launch_to_bits(scratch, c->spins, c->N, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h_bits, scratch, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0xFF, bytes, c->stream);
+    return e;
 }
 
 // Enqueues an Ising lattice upload (int8 +-1 from host memory), the next
@@ -331,6 +377,12 @@ static wolff_status init_common(wolff_ctx **out, int dim, int L, double J, doubl
         }
         c->own_ws = true;
         c->ws_bytes = need;
+    }
+    // pinned landing buffer for control-block reads (optional: without it
+    // the reads stage through pageable memory)
+    if (cudaMallocHost(reinterpret_cast<void **>(&c->h_ctl), sizeof(DevCtl)) != cudaSuccess) {
+        cudaGetLastError();
+        c->h_ctl = nullptr;
     }
     char *base = static_cast<char *>(c->ws);
     c->ctl = reinterpret_cast<DevCtl *>(base);
@@ -592,20 +644,8 @@ wolff_status wolff_run_host(wolff_ctx *c, const int8_t *h_spins_in, uint64_t t_i
     }
     wolff_record *d_rec = nullptr;
     if (h_records && n_updates) {
-        // device staging for the records, kept by the context and grown on
-        // demand so that repeated calls do not allocate
-        const size_t bytes = n_updates * sizeof(wolff_record);
-        if (bytes > c->rec_stage_bytes) {
-            cudaStreamSynchronize(c->stream);
-            if (c->rec_stage) cudaFree(c->rec_stage);
-            c->rec_stage = nullptr;
-            c->rec_stage_bytes = 0;
-            if (cudaMalloc(&c->rec_stage, bytes) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(c, WOLFF_ENOMEM, "record staging buffer");
-            }
-            c->rec_stage_bytes = bytes;
-        }
+        s = ensure_rec_stage(c, n_updates * sizeof(wolff_record));
+        if (s != WOLFF_OK) return s;
         d_rec = reinterpret_cast<wolff_record *>(c->rec_stage);
     }
     s = wolff_step(c, n_updates, d_rec);
@@ -619,6 +659,57 @@ wolff_status wolff_run_host(wolff_ctx *c, const int8_t *h_spins_in, uint64_t t_i
     } else if (s == WOLFF_OK) {
         s = sync_and_check(c, nullptr);
     }
+    return s;
+}
+
+wolff_status wolff_set_state_bits(wolff_ctx *c, const uint32_t *h_bits, uint64_t t) {
+    if (!c || !h_bits) return WOLFF_EINVAL;
+    if (c->potts || c->xy) return fail(c, WOLFF_EUNSUPPORTED, "bit-packed states are Ising only");
+    cudaError_t e = enqueue_ising_upload_bits(c, h_bits, t);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set_state_bits");
+    return sync_and_check(c, nullptr);
+}
+
+wolff_status wolff_get_state_bits(wolff_ctx *c, uint32_t *h_bits, uint64_t *t) {
+    if (!c) return WOLFF_EINVAL;
+    if (c->potts || c->xy) return fail(c, WOLFF_EUNSUPPORTED, "bit-packed states are Ising only");
+    if (h_bits) {
+        cudaError_t e = enqueue_ising_download_bits(c, h_bits);
+        if (e != cudaSuccess) return cuda_fail(c, e, "get_state_bits");
+    }
+    DevCtl h;
+    wolff_status s = sync_and_check(c, &h);
+    if (s != WOLFF_OK) return s;
+    if (t) *t = h.t;
+    return WOLFF_OK;
+}
+
+wolff_status wolff_run_host_bits(wolff_ctx *c, const uint32_t *h_bits_in, uint64_t t_in,
+                                 uint64_t n_updates, wolff_record *h_records,
+                                 uint32_t *h_bits_out) {
+    if (!c) return WOLFF_EINVAL;
+    if (c->potts || c->xy) return fail(c, WOLFF_EUNSUPPORTED, "bit-packed states are Ising only");
+    if (h_bits_in) {
+        cudaError_t e = enqueue_ising_upload_bits(c, h_bits_in, t_in);
+        if (e != cudaSuccess) return cuda_fail(c, e, "upload");
+    }
+    wolff_record *d_rec = nullptr;
+    if (h_records && n_updates) {
+        wolff_status s = ensure_rec_stage(c, n_updates * sizeof(wolff_record));
+        if (s != WOLFF_OK) return s;
+        d_rec = reinterpret_cast<wolff_record *>(c->rec_stage);
+    }
+    wolff_status s = wolff_step(c, n_updates, d_rec);
+    if (s == WOLFF_OK && d_rec) {
+        cudaError_t e = cudaMemcpyAsync(h_records, d_rec, n_updates * sizeof(wolff_record),
+                                        cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) s = cuda_fail(c, e, "records copy");
+    }
+    if (s == WOLFF_OK && h_bits_out) {
+        cudaError_t e = enqueue_ising_download_bits(c, h_bits_out);
+        if (e != cudaSuccess) s = cuda_fail(c, e, "download");
+    }
+    if (s == WOLFF_OK) s = sync_and_check(c, nullptr);
     return s;
 }
 
@@ -749,6 +840,7 @@ wolff_status ising_free(wolff_ctx *c) {
     if (c->graph) cudaGraphDestroy(c->graph);
     if (c->own_ws && c->ws) cudaFree(c->ws);
     if (c->rec_stage) cudaFree(c->rec_stage);
+    if (c->h_ctl) cudaFreeHost(c->h_ctl);
     delete c;
     return WOLFF_OK;
 }

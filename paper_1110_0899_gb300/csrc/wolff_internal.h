@@ -48,6 +48,7 @@ struct alignas(256) DevCtl {
     long long full_M;
     long long My;                  // XY: second magnetisation component
     long long full_My;
+    unsigned int up_blocks;        // blocks of the fused upload pass done (atomic)
     // line 1: grid barrier
     // bar_word = arrivals << 32 | entries appended this level (atomic): the
     // warps reserve list slots and the CTAs arrive on the same word, so the
@@ -132,6 +133,9 @@ cudaError_t launch_from_pm1(uint8_t *spins, const int8_t *src, uint32_t N,
                             DevCtl *ctl, cudaStream_t s);
 cudaError_t launch_from_pm1_measure(int dim, uint8_t *spins, const int8_t *src, Geometry g,
                                     DevCtl *ctl, cudaStream_t s);
+cudaError_t launch_from_bits_measure(int dim, uint8_t *spins, const uint32_t *bits, Geometry g,
+                                     DevCtl *ctl, cudaStream_t s);
+cudaError_t launch_to_bits(uint32_t *bits, const uint8_t *spins, uint32_t N, cudaStream_t s);
 cudaError_t launch_to_pm1(int8_t *dst, const uint8_t *spins, uint32_t N,
                           cudaStream_t s);
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, const uint32_t *ctr,
@@ -155,6 +159,9 @@ struct WinCfg {
 };
 constexpr int kDefaultWindowLevels = 32;  // growth levels per warp between commit rounds
 const void *team_kernel(int dim);
+// Raises the team kernel's dynamic shared-memory limit to at least `bytes`
+// (on the current device); never lowers it.
+cudaError_t ensure_team_dyn_smem(int dim, size_t bytes);
 uint32_t window_cap(int dim, int threads);
 size_t window_smem_bytes(int dim, int threads, int window_slots, int cluster_size);
 cudaError_t launch_team(int dim, const StepParams &single, const StepParams *d_table, int njobs,

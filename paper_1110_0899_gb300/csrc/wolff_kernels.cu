@@ -173,19 +173,100 @@ __global__ void k_from_pm1_measure(uint8_t *spins, const int8_t *src, Geometry g
     if (threadIdx.x == 0) {
         atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->full_E), (unsigned long long)e);
         atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->full_M), (unsigned long long)m);
+        // the last block to finish publishes the sums as the chain state
+        __threadfence();
+        if (atomicAdd(&ctl->up_blocks, 1u) == gridDim.x - 1) {
+            __threadfence();
+            ctl->E = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->full_E), 0ull);
+            ctl->M = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->full_M), 0ull);
+            ctl->up_blocks = 0;
+        }
     }
 }
 
+// Bit-packed upload: bit i of word i / 32 set <=> spin +1.  Same single pass
+// as k_from_pm1_measure (spin bytes, E_bond and M from the input bits).
+__device__ __forceinline__ int bit_spin(const uint32_t *bits, uint32_t i) {
+    return ((__ldg(bits + (i >> 5)) >> (i & 31u)) & 1u) ? 1 : -1;
+}
+
+template <int DIM>
+__global__ void k_from_bits_measure(uint8_t *spins, const uint32_t *bits, Geometry g,
+                                    DevCtl *ctl) {
+    const uint32_t rows = g.N / g.L;
+    long long e = 0, m = 0;
+    for (uint32_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        const uint32_t y = row % g.L;
+        const uint32_t base = row * g.L;
+        const uint32_t yup = (y + 1 == g.L) ? base + g.L - g.LL : base + g.L;
+        uint32_t zup = 0;
+        if (DIM == 3) {
+            const uint32_t z = row / g.L;
+            zup = (z + 1 == g.L) ? base + g.LL - g.N : base + g.LL;
+        }
+        for (uint32_t x = threadIdx.x; x < g.L; x += blockDim.x) {
+            const int si = bit_spin(bits, base + x);
+            spins[base + x] = si > 0 ? 0x03 : 0x00;
+            const uint32_t xr = (x + 1 == g.L) ? 0 : x + 1;
+            int nbsum = bit_spin(bits, base + xr) + bit_spin(bits, yup + x);
+            if (DIM == 3) nbsum += bit_spin(bits, zup + x);
+            e += si * nbsum;
+            m += si;
+        }
+    }
+    e = block_sum(e);
+    m = block_sum(m);
+    if (threadIdx.x == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->full_E), (unsigned long long)e);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->full_M), (unsigned long long)m);
+        __threadfence();
+        if (atomicAdd(&ctl->up_blocks, 1u) == gridDim.x - 1) {
+            __threadfence();
+            ctl->E = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->full_E), 0ull);
+            ctl->M = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->full_M), 0ull);
+            ctl->up_blocks = 0;
+        }
+    }
+}
+
+// Bit-packed download: one warp ballot per 32 consecutive sites.
+__global__ void k_to_bits(uint32_t *bits, const uint8_t *spins, uint32_t N) {
+    const uint32_t words = (N + 31u) / 32u;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < words; w += warps) {
+        const uint32_t i = w * 32u + lane;
+        const uint32_t b = __ballot_sync(0xffffffffu, i < N && (spins[i] & 1u));
+        if (lane == 0) bits[w] = b;
+    }
+}
+
+cudaError_t launch_from_bits_measure(int dim, uint8_t *spins, const uint32_t *bits, Geometry g,
+                                     DevCtl *ctl, cudaStream_t s) {
+    const unsigned blocks = (unsigned)grid_for(g.N / g.L, 8192ull);
+    const unsigned threads = g.L >= 256 ? 256 : 64;
+    if (dim == 2)
+        k_from_bits_measure<2><<<blocks, threads, 0, s>>>(spins, bits, g, ctl);
+    else
+        k_from_bits_measure<3><<<blocks, threads, 0, s>>>(spins, bits, g, ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_bits(uint32_t *bits, const uint8_t *spins, uint32_t N, cudaStream_t s) {
+    const unsigned long long words = (N + 31ull) / 32ull;
+    k_to_bits<<<grid_for((words * 32ull + 255ull) / 256ull, 4096ull), 256, 0, s>>>(bits, spins, N);
+    return cudaGetLastError();
+}
+
+// Expects a control block reset by k_reset_ctl (full sums and block count 0).
 cudaError_t launch_from_pm1_measure(int dim, uint8_t *spins, const int8_t *src, Geometry g,
                                     DevCtl *ctl, cudaStream_t s) {
-    k_zero_full<<<1, 1, 0, s>>>(ctl);
     const unsigned blocks = (unsigned)grid_for(g.N / g.L, 8192ull);
     const unsigned threads = g.L >= 256 ? 256 : 64;
     if (dim == 2)
         k_from_pm1_measure<2><<<blocks, threads, 0, s>>>(spins, src, g, ctl);
     else
         k_from_pm1_measure<3><<<blocks, threads, 0, s>>>(spins, src, g, ctl);
-    k_full_to_chain<<<1, 1, 0, s>>>(ctl);
     return cudaGetLastError();
 }
 
@@ -231,6 +312,8 @@ __global__ void k_reset_ctl(DevCtl *ctl, unsigned long long t) {
     ctl->total_C = 0;
     ctl->status = 0;
     ctl->err_detail = 0;
+    ctl->full_E = ctl->full_M = ctl->full_My = 0;
+    ctl->up_blocks = 0;
     for (int k = 0; k < 4; ++k) ctl->cnt[k] = 0;
     ctl->dE = 0;
     ctl->bar_word = 0;

@@ -23,6 +23,8 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "wolff_device.cuh"
 
 namespace cg = cooperative_groups;
@@ -1189,11 +1191,36 @@ __global__ void __launch_bounds__(512, 1) k_team(StepParams single, const StepPa
     team_leader<DIM>(p, sh, cl, wc);
 }
 
+// Kernel attributes already set, per device and dimension.
+constexpr int kAttrDevices = 64;
+std::atomic<bool> g_nonportable_set[kAttrDevices][2];
+std::atomic<size_t> g_dyn_smem_set[kAttrDevices][2];
+
 }  // namespace
 
 const void *team_kernel(int dim) {
     return dim == 2 ? reinterpret_cast<const void *>(&k_team<2>)
                     : reinterpret_cast<const void *>(&k_team<3>);
+}
+
+cudaError_t ensure_team_dyn_smem(int dim, size_t bytes) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kAttrDevices) {
+        cudaGetLastError();
+        return cudaFuncSetAttribute(team_kernel(dim), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)bytes);
+    }
+    // the attribute is an upper bound: it only ever grows to the largest
+    // request, so a value recorded here is never above the real one
+    std::atomic<size_t> &cur = g_dyn_smem_set[dev][dim == 2 ? 0 : 1];
+    size_t seen = cur.load();
+    if (bytes <= seen) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(team_kernel(dim),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    while (seen < bytes && !cur.compare_exchange_weak(seen, bytes)) {
+    }
+    return cudaSuccess;
 }
 
 // Members per speculative update: 64 with 16 warps per CTA in 2D, 128 in 3D
@@ -1219,17 +1246,25 @@ cudaError_t launch_team(int dim, const StepParams &single, const StepParams *d_t
     if (window_slots < 0 || (window_slots & (window_slots - 1)) != 0 || window_slots > 1024)
         return cudaErrorInvalidValue;
     const void *fn = team_kernel(dim);
-    if (cluster_size > 8) {
+    // kernel attributes are set once per device and value (a driver call per
+    // launch otherwise)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kAttrDevices) {
+        cudaGetLastError();
+        dev = -1;
+    }
+    const int di = dim == 2 ? 0 : 1;
+    if (cluster_size > 8 && (dev < 0 || !g_nonportable_set[dev][di].load())) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
+        if (dev >= 0) g_nonportable_set[dev][di].store(true);
     }
     WinCfg wc;
     wc.slots = (uint32_t)window_slots;
     wc.cap = window_cap(dim, threads);
     const size_t dyn = window_smem_bytes(dim, threads, window_slots, cluster_size);
     if (dyn > 0) {
-        cudaError_t e =
-            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        cudaError_t e = ensure_team_dyn_smem(dim, dyn);
         if (e != cudaSuccess) return e;
     }
     cudaLaunchConfig_t cfg = {};

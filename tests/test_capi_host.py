@@ -102,3 +102,20 @@ def test_xy_workspace_and_argument_checks(lib):
     assert lib.xy_get_state(None, None, None) == w.WOLFF_EINVAL
     assert lib.xy_set_state(None, None, 0) == w.WOLFF_EINVAL
     assert w.XY_RECORD_DTYPE.itemsize == 32 and w.XY_RECORD_DTYPE == oracle.XY_RECORD_DTYPE
+
+
+def test_bit_packing_definition(lib):
+    """Bit (i mod 32) of word i / 32 is set when site i is +1; unused high
+    bits of the last word are zero; unpacking inverts packing."""
+    import numpy as np
+    import paper_1110_0899_gb300 as w
+    rng = np.random.default_rng(4)
+    for N in (1, 31, 32, 33, 1331, 4096):
+        s = rng.choice(np.array([-1, 1], np.int8), N)
+        b = w.pack_spins(s)
+        assert b.dtype == np.uint32 and b.size == (N + 31) // 32
+        for i in rng.integers(0, N, 50):
+            assert ((int(b[i // 32]) >> (i % 32)) & 1) == int(s[i] == 1)
+        if N % 32:
+            assert int(b[-1]) >> (N % 32) == 0
+        assert np.array_equal(w.unpack_bits(b, N), s)

@@ -211,6 +211,26 @@ def test_host_buffer_path():
     lat.close()
 
 
+@pytest.mark.parametrize("dim,L", [(2, 37), (3, 11)])
+def test_bit_packed_transfers(dim, L):
+    """The bit-packed state transfers and host-buffer path give what the int8
+    ones give (ragged N: the last word is partial)."""
+    torch, w = require_cuda()
+    T, seed = (2.5, 8) if dim == 2 else (4.8, 9)
+    s0 = oracle.init_lattice(dim, L, seed)
+    ref, s_ref = oracle_trajectory(dim, L, T, seed, 60, t0=13, s=s0)
+    lat = w.WolffLattice(dim, L, T, seed=seed)
+    lat.set_state_bits(w.pack_spins(s0), 13)
+    assert lat.measure()[:2] == (oracle.energy_bond(dim, L, s0), oracle.magnetisation(dim, L, s0))
+    bits, t = lat.get_state_bits()
+    assert t == 13 and np.array_equal(bits, w.pack_spins(s0))
+    rec, bout = lat.run_host_bits(60, bits_in=w.pack_spins(s0), t_in=13)
+    assert_records_equal(rec, ref, "run_host_bits")
+    assert np.array_equal(w.unpack_bits(bout, L ** dim), s_ref)
+    assert np.array_equal(lat.get_state()[0], s_ref)
+    lat.close()
+
+
 @pytest.mark.parametrize("dim,L", [(2, 4096), (3, 256)])
 def test_full_size_state_transfer(dim, L):
     """The fused upload (int8 +-1 -> spin bytes, E_bond and M in the same
@@ -226,6 +246,10 @@ def test_full_size_state_transfer(dim, L):
     assert (E, M) == (oracle.energy_bond(dim, L, s), oracle.magnetisation(dim, L, s))
     back, t = lat.get_state()
     assert t == 77 and np.array_equal(back, s)
+    bits, t = lat.get_state_bits()
+    assert t == 77 and np.array_equal(bits, w.pack_spins(s))
+    lat.set_state_bits(bits, 77)
+    assert lat.measure()[:2] == (E, M)
     rec = lat.step(50)
     T = 1.0 if dim == 2 else 4.5115
     ref, s_ref = oracle_trajectory(dim, L, T, 31, 50, t0=77, s=s)

@@ -43,7 +43,7 @@ TC2 = 2.0 / math.log(1.0 + math.sqrt(2.0))
 # committed ncu capture (profiles/k_team_2d_L4096_random_start.md), valid only
 # while the kernel sources hash to the captured value.
 TRAFFIC_CAPTURES = {
-    ("2d", 1000): {"src": "68701d8b9e8c", "bytes_per_launch": 1574144 + 0},
+    ("2d", 1000): {"src": "7ef1fca820b0", "bytes_per_launch": 1570816 + 0},
 }
 
 

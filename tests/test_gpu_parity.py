@@ -445,3 +445,44 @@ def test_full_size_in_bench_configuration(dim, L, T, seed, equil, sample):
     st = lat.stats()
     assert st["burst_updates"] > 0   # the bench's burst path is the one exercised
     lat.close()
+
+
+@pytest.mark.parametrize("dim,L,T,seed", [(2, 4096, TC2, 2), (3, 256, 4.5115, 3)])
+def test_whole_trajectory_in_segments(dim, L, T, seed):
+    """The full specified runs (2000 equilibration + 10^4 measured updates, in
+    the benchmark's launch configuration): the GPU snapshots its lattice every
+    500 updates; the oracle replays every segment from the previous snapshot
+    and must reach the next one bit for bit (any wrong cluster anywhere in
+    the segment would change it); E_bond and M at every snapshot equal the
+    definitions; every record of the 10^4 measured updates obeys
+    |dM| = 2|C| and E changes by an even amount."""
+    torch, w = require_cuda()
+    thr = oracle.bond_threshold(1.0, T)
+    lat = w.WolffLattice(dim, L, T, seed=seed)
+    snaps = [lat.get_state()]
+    recs = []
+    for k in range(24):                       # 12000 updates in steps of 500
+        rec = lat.step(500)
+        if k >= 4:
+            recs.append(rec)
+        snaps.append(lat.get_state())
+    E, M, _ = lat.measure()
+    lat.close()
+    for (s_a, t_a), (s_b, t_b) in zip(snaps, snaps[1:]):
+        assert t_b == t_a + 500
+        s = np.array(s_a, dtype=np.int8, copy=True)
+        oracle.run(dim, L, thr, seed, t_a, 500, s, records=False)
+        assert np.array_equal(s, s_b), "segment starting at update %d" % t_a
+    assert (E, M) == (oracle.energy_bond(dim, L, snaps[-1][0]),
+                      oracle.magnetisation(dim, L, snaps[-1][0]))
+    rec = np.concatenate(recs)
+    E_prev = oracle.energy_bond(dim, L, snaps[4][0])
+    M_prev = oracle.magnetisation(dim, L, snaps[4][0])
+    for k, r in enumerate(rec):
+        assert abs(int(r["M"]) - M_prev) == 2 * int(r["C"]), k
+        assert (int(r["E"]) - E_prev) % 2 == 0, k
+        E_prev, M_prev = int(r["E"]), int(r["M"])
+        if (k + 1) % 500 == 0:   # the record at a snapshot equals its recount
+            s_k = snaps[4 + (k + 1) // 500][0]
+            assert (E_prev, M_prev) == (oracle.energy_bond(dim, L, s_k),
+                                        oracle.magnetisation(dim, L, s_k)), k

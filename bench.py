@@ -39,11 +39,13 @@ UNIT = "flipped spins/s"
 ALGO_BYTES_PER_FLIP = {2: 23.0, 3: 27.0}
 
 TC2 = 2.0 / math.log(1.0 + math.sqrt(2.0))
-# DRAM traffic of one timed k_team launch of the default workload, from the
-# committed ncu capture (profiles/k_team_2d_L4096_random_start.md), valid only
-# while the kernel sources hash to the captured value.
+# DRAM traffic of one timed k_team launch of the specified workloads, from the
+# committed ncu captures (profiles/k_team_2d_L4096_random_start.md and
+# profiles/k_team_3d_L256_random_start.md), valid only while the kernel sources
+# hash to the captured value.
 TRAFFIC_CAPTURES = {
     ("2d", 1000): {"src": "7ef1fca820b0", "bytes_per_launch": 1570816 + 0},
+    ("3d", 1000): {"src": "7ef1fca820b0", "bytes_per_launch": 4409856 + 0},
 }
 
 

@@ -345,123 +345,82 @@ __device__ __forceinline__ void win_start(const StepParams &p, unsigned long lon
     levels = 0;
 }
 
-// Prefetches into L1 the lattice lines a member's neighbours will read if
-// they join: the neighbours of (x+-1, ...) lie in the lines the member reads
-// itself; those of (x, y+-1, ...) add the rows y+-2 (and, in 3D, z+-2 and the
-// four (y+-1, z+-1) diagonals).  Loads of the next level then hit L1 within
-// the same growth phase.
-__device__ __forceinline__ void prefetch_l1(const void *ptr) {
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(ptr));
-}
-
-__device__ __forceinline__ uint32_t wrap_add(uint32_t c, int d, uint32_t L) {
-    const int v = (int)c + d;
-    return (uint32_t)(v < 0 ? v + (int)L : v >= (int)L ? v - (int)L : v);
-}
-
+// Neighbour s of the member `packed` (s = 2d: forward along axis d, 2d + 1:
+// backward): its site index and packed coordinates, and the owner of the bond
+// (the member for a forward bond, the neighbour for a backward one).
 template <int DIM>
-__device__ __forceinline__ void prefetch_two_hop(const StepParams &p, uint32_t packed) {
+__device__ __forceinline__ void neighbour_of(const Geometry &g, uint32_t packed, uint32_t s,
+                                             uint32_t &self, uint32_t &j, uint32_t &pj,
+                                             uint32_t &owner) {
     uint32_t c[DIM];
     unpack<DIM>(packed, c);
-    const uint32_t L = p.g.L;
-    if (DIM == 2) {
-        prefetch_l1(p.spins + c[0] + L * wrap_add(c[1], -2, L));
-        prefetch_l1(p.spins + c[0] + L * wrap_add(c[1], 2, L));
-    } else {
-        const uint32_t LL = p.g.LL;
-        const uint32_t x = c[0], y = c[1], z = c[DIM - 1];
-        prefetch_l1(p.spins + x + L * wrap_add(y, -2, L) + LL * z);
-        prefetch_l1(p.spins + x + L * wrap_add(y, 2, L) + LL * z);
-        prefetch_l1(p.spins + x + L * y + LL * wrap_add(z, -2, L));
-        prefetch_l1(p.spins + x + L * y + LL * wrap_add(z, 2, L));
+    self = site_index<DIM>(g, c);
+    const uint32_t d = s >> 1;
+    uint32_t cd = c[0], st = 1, sh = 0;
 #pragma unroll
-        for (int a = -1; a <= 1; a += 2)
-#pragma unroll
-            for (int b = -1; b <= 1; b += 2)
-                prefetch_l1(p.spins + x + L * wrap_add(y, a, L) + LL * wrap_add(z, b, L));
-    }
+    for (int k = 1; k < DIM; ++k)
+        if (d == (uint32_t)k) {
+            cd = c[k];
+            st = axis_stride<DIM>(g, k);
+            sh = Pack<DIM>::shift(k);
+        }
+    const uint32_t nc = (s & 1u) ? (cd == 0 ? g.L - 1 : cd - 1) : (cd + 1 == g.L ? 0u : cd + 1);
+    j = self + (nc - cd) * st;
+    pj = packed + ((nc - cd) << sh);
+    owner = (s & 1u) ? j : self;
 }
 
 // Warp: one level of speculative growth, members[lo, n) -> new members
-// appended.  Returns true when the cluster outgrew cap.
+// appended.  One lane per (member, direction) pair: a lane loads one
+// neighbour, evaluates the one Philox chain its bond draws from and tries
+// one claim, so a level costs the warp about one chain instead of D + 1.
+// Returns true when the cluster outgrew cap.
 template <int DIM>
 __device__ __forceinline__ bool win_level(const StepParams &p, uint32_t *members, uint8_t *amask,
                                           uint32_t *hset, uint32_t hslots, uint32_t cap,
                                           uint32_t lane, uint32_t &lo, uint32_t &n,
                                           uint32_t sig0bit, uint32_t tlo, uint32_t thi) {
+    constexpr uint32_t Z = 2 * DIM;          // directions per member
+    constexpr uint32_t PER = 32 / Z;         // members per pass (8 in 2D, 5 in 3D)
     const uint32_t hi = n;
+    const uint32_t km = lane / Z, s = lane % Z;
+    const uint32_t lt = (1u << lane) - 1u;
     bool too_big = false;
-    for (uint32_t b = lo; b < hi && !too_big; b += 32) {
-        const uint32_t k = b + lane;
-        Neighbours<DIM> nb2;
-        uint32_t fresh = 0;
-        bool full = false;
-        if (k < hi) {
-            uint32_t i;
-            neighbours<DIM>(p.g, members[k], &i, nb2);
-            uint8_t v[2 * DIM];
-#pragma unroll
-            for (int s = 0; s < 2 * DIM; ++s) v[s] = __ldca(p.spins + nb2.idx[s]);
-            prefetch_two_hop<DIM>(p, members[k]);
-            uint32_t par = 0;
-#pragma unroll
-            for (int s = 0; s < 2 * DIM; ++s) par |= (uint32_t)((v[s] & 1u) == sig0bit) << s;
-            amask[k] = (uint8_t)par;
-            uint32_t owners[DIM + 1];
-            owners[0] = i;
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) owners[d + 1] = nb2.idx[2 * d + 1];
-            Philox4 draw[DIM + 1];
-            philox4x32_10_lanes<DIM + 1>(owners, tlo, thi, kTagBond, p.key0, p.key1, draw);
-            // every active bond's home slot is tried at once; only a
-            // collision probes further
-            uint32_t cand = 0;
-#pragma unroll
-            for (int s = 0; s < 2 * DIM; ++s) {
-                const int d = s >> 1;
-                const uint32_t r = (s & 1) ? draw[d + 1].v[d] : draw[0].v[d];
-                if (((par >> s) & 1u) && (unsigned long long)r < p.thr) cand |= 1u << s;
-            }
-            uint32_t prev[2 * DIM];
-#pragma unroll
-            for (int s = 0; s < 2 * DIM; ++s) {
-                prev[s] = 0;
-                if (cand & (1u << s))
-                    prev[s] = atomicCAS(hset + set_hash(nb2.idx[s], hslots), kEmptyKey,
-                                        nb2.idx[s]);
-            }
-#pragma unroll
-            for (int s = 0; s < 2 * DIM; ++s) {
-                if (!(cand & (1u << s))) continue;
-                int ins;
-                if (prev[s] == kEmptyKey) ins = 1;
-                else if (prev[s] == nb2.idx[s]) ins = 0;
-                else ins = set_insert(hset, hslots, nb2.idx[s]);
-                if (ins > 0) fresh |= 1u << s;
-                if (ins < 0) full = true;
-            }
+    for (uint32_t b = lo; b < hi && !too_big; b += PER) {
+        const uint32_t k = b + km;
+        const bool act = km < PER && k < hi;
+        uint32_t j = 0, pj = 0;
+        bool par = false, cand = false;
+        if (act) {
+            uint32_t self, owner;
+            neighbour_of<DIM>(p.g, members[k], s, self, j, pj, owner);
+            const uint8_t v = __ldca(p.spins + j);
+            Philox4 draw;
+            philox4x32_10_lanes<1>(&owner, tlo, thi, kTagBond, p.key0, p.key1, &draw);
+            const uint32_t d = s >> 1;
+            const uint32_t r = d == 0 ? draw.v[0] : d == 1 ? draw.v[1] : draw.v[2];
+            par = (uint32_t)(v & 1u) == sig0bit;
+            cand = par && (unsigned long long)r < p.thr;
         }
-        // positions of the new members: one ballot per direction
-        const uint32_t lt = (1u << lane) - 1u;
-        uint32_t before = 0, total = 0, own = 0;
-        uint32_t pos_of[2 * DIM];
-#pragma unroll
-        for (int s = 0; s < 2 * DIM; ++s) {
-            const uint32_t m = __ballot_sync(kFullMask, (fresh >> s) & 1u);
-            before += __popc(m & lt);
-            total += __popc(m);
-            pos_of[s] = own;
-            own += (fresh >> s) & 1u;
+        // the member's alignment mask, as its Z lanes read it
+        const uint32_t pm = __ballot_sync(kFullMask, par);
+        if (act && s == 0) amask[k] = (uint8_t)((pm >> (km * Z)) & ((1u << Z) - 1u));
+        bool fresh = false, full = false;
+        if (cand) {
+            const uint32_t prev = atomicCAS(hset + set_hash(j, hslots), kEmptyKey, j);
+            int ins;
+            if (prev == kEmptyKey) ins = 1;
+            else if (prev == j) ins = 0;
+            else ins = set_insert(hset, hslots, j);
+            fresh = ins > 0;
+            full = ins < 0;
         }
-        // order: lanes first, then directions within a lane
-#pragma unroll
-        for (int s = 0; s < 2 * DIM; ++s) {
-            if (fresh & (1u << s)) {
-                const uint32_t pos = n + before + pos_of[s];
-                if (pos < cap) members[pos] = nb2.packed[s];
-            }
+        const uint32_t fm = __ballot_sync(kFullMask, fresh);
+        if (fresh) {
+            const uint32_t pos = n + __popc(fm & lt);
+            if (pos < cap) members[pos] = pj;
         }
-        n += total;
+        n += __popc(fm);
         if (__any_sync(kFullMask, full) || n > cap) too_big = true;
     }
     __syncwarp();
@@ -470,30 +429,27 @@ __device__ __forceinline__ bool win_level(const StepParams &p, uint32_t *members
 }
 
 // Warp: sum over the boundary bonds of the grown cluster of (the neighbour is
-// parallel ? -1 : +1), i.e. dE_bond / 2 of flipping it (every lane gets it).
+// parallel ? -1 : +1), i.e. dE_bond / 2 of flipping it (every lane gets it);
+// one lane per (member, direction) pair.
 template <int DIM>
 __device__ __forceinline__ int win_boundary(const StepParams &p, const uint32_t *members,
                                             const uint32_t *hset, uint32_t hslots, uint32_t n,
                                             uint32_t sig0bit, uint32_t lane) {
+    constexpr uint32_t Z = 2 * DIM;
+    constexpr uint32_t PER = 32 / Z;
+    const uint32_t km = lane / Z, s = lane % Z;
     int dE = 0;
-    for (uint32_t k = lane; k < n; k += 32) {
-        uint32_t i;
-        Neighbours<DIM> nb2;
-        neighbours<DIM>(p.g, members[k], &i, nb2);
-        uint32_t home[2 * DIM];
-        uint8_t cur[2 * DIM];
-#pragma unroll
-        for (int s = 0; s < 2 * DIM; ++s) {
-            home[s] = hset[set_hash(nb2.idx[s], hslots)];
-            cur[s] = __ldca(p.spins + nb2.idx[s]);
-        }
-#pragma unroll
-        for (int s = 0; s < 2 * DIM; ++s) {
+    for (uint32_t b = 0; b < n; b += PER) {
+        const uint32_t k = b + km;
+        if (km < PER && k < n) {
+            uint32_t self, j, pj, owner;
+            neighbour_of<DIM>(p.g, members[k], s, self, j, pj, owner);
+            const uint32_t home = hset[set_hash(j, hslots)];
+            const uint8_t cur = __ldca(p.spins + j);
             // the home slot settles membership unless it holds another site
-            const bool member = home[s] == nb2.idx[s] ||
-                                (home[s] != kEmptyKey && set_contains(hset, hslots, nb2.idx[s]));
-            if (member) continue;
-            dE += ((cur[s] & 1u) == sig0bit) ? -1 : 1;
+            const bool member =
+                home == j || (home != kEmptyKey && set_contains(hset, hslots, j));
+            if (!member) dE += ((cur & 1u) == sig0bit) ? -1 : 1;
         }
     }
 #pragma unroll

@@ -652,6 +652,7 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
     const bool timer = win_ns != nullptr && rank == 0 && threadIdx.x == 0;
     unsigned long long tick = timer ? global_ns() : 0;
     uint32_t stall = 0;
+    uint32_t rec_lo = 0, rec_hi = 0;   // committed updates whose records are pending
     resumable = false;
     while (true) {
         const uint32_t lim = min(n_rem, c + P);
@@ -676,6 +677,11 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
             if (rank == 0) sh.wcut = lim;
         }
         __syncthreads();
+        if (rank == 0 && rec_hi > rec_lo) {
+            win_records(p, sh, cl, v, S, cs, u0, rec_lo, rec_hi, E, M, total_C, last_C,
+                        last_levels);
+            rec_lo = rec_hi = 0;
+        }
         if (warp < W) {
             uint32_t steps = 0;
             while (steps < K) {
@@ -806,8 +812,13 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
                 p.spins[site_index<DIM>(p.g, cc)] = v.meta[s].w ? 0x00 : 0x03;
             }
         }
-        if (rank == 0 && cut > c)
-            win_records(p, sh, cl, v, S, cs, u0, c, cut, E, M, total_C, last_C, last_levels);
+        // the leader writes the records of [c, cut) at the start of the next
+        // round (or on leaving), off this phase's critical path; their
+        // results stay in lmeta until the next stamping phase rewrites it
+        if (cut > c) {
+            rec_lo = c;
+            rec_hi = cut;
+        }
         // the committed slots are free; a finished update that read a
         // committed flip grows again
         for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) {
@@ -853,6 +864,8 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
         for (uint32_t k = threadIdx.x; k < S; k += blockDim.x)
             if (v.state[k] == kSlotTooBig) v.state[k] = v.j[k] == c ? kSlotFree : kSlotRegrow;
     }
+    if (rank == 0 && rec_hi > rec_lo)
+        win_records(p, sh, cl, v, S, cs, u0, rec_lo, rec_hi, E, M, total_C, last_C, last_levels);
     // leave the cluster list empty, and ordered before whatever uses it next
     {
         const uint32_t total = v.off[S];

@@ -44,8 +44,8 @@ TC2 = 2.0 / math.log(1.0 + math.sqrt(2.0))
 # profiles/k_team_3d_L256_random_start.md), valid only while the kernel sources
 # hash to the captured value.
 TRAFFIC_CAPTURES = {
-    ("2d", 1000): {"src": "7ef1fca820b0", "bytes_per_launch": 1570816 + 0},
-    ("3d", 1000): {"src": "7ef1fca820b0", "bytes_per_launch": 4409856 + 0},
+    ("2d", 1000): {"src": "5e01158fc7e3", "bytes_per_launch": 1321728 + 0},
+    ("3d", 1000): {"src": "5e01158fc7e3", "bytes_per_launch": 3102208 + 0},
 }
 
 

@@ -2,10 +2,12 @@
 
 Default workload (N=1): 2D square lattice L = 4096 (16.8M spins), periodic,
 J = 1, T = T_c = 2/ln(1+sqrt 2), int8 spins, Philox random start from seed 2,
-equilibrated for 2000 updates (untimed), then K timed steps of U updates each,
-one lattice per launch (the plain form), records written every update (the
-"+ measurement" form of the paper's Tables 1-2).  --workload 3d runs the
-simple-cubic L = 256 lattice at T = 4.5115, seed 3.
+equilibrated for 2000 updates (untimed); every step then runs the 10^4
+measured updates (t = 2000 .. 11999) in one launch (the plain form), records
+written every update (the "+ measurement" form of the paper's Tables 1-2).
+Before each step the equilibrated lattice is restored (untimed), so every
+step repeats the same chain and must give the same records.  --workload 3d
+runs the simple-cubic L = 256 lattice at T = 4.5115, seed 3.
 
 value = sum of cluster sizes over the timed updates / device time of the
 timed steps (CUDA events on the lattice's stream, an L2 flush of 256 MB
@@ -44,8 +46,8 @@ TC2 = 2.0 / math.log(1.0 + math.sqrt(2.0))
 # profiles/k_team_3d_L256_random_start.md), valid only while the kernel sources
 # hash to the captured value.
 TRAFFIC_CAPTURES = {
-    ("2d", 1000): {"src": "5e01158fc7e3", "bytes_per_launch": 1321728 + 0},
-    ("3d", 1000): {"src": "5e01158fc7e3", "bytes_per_launch": 3102208 + 0},
+    ("2d", 10000): {"src": "5e01158fc7e3", "bytes_per_launch": 11237888 + 512},
+    ("3d", 10000): {"src": "5e01158fc7e3", "bytes_per_launch": 24314624 + 94208},
 }
 
 
@@ -62,8 +64,8 @@ def kernel_source_hash():
 
 WORKLOADS = {
     # the configurations as specified: random start, 2000 equilibration updates
-    "2d": dict(dim=2, L=4096, T=TC2, seed=2, equil=2000, start="random"),
-    "3d": dict(dim=3, L=256, T=4.5115, seed=3, equil=2000, start="random"),
+    "2d": dict(dim=2, L=4096, T=TC2, seed=2, equil=2000, start="random", updates=10000),
+    "3d": dict(dim=3, L=256, T=4.5115, seed=3, equil=2000, start="random", updates=10000),
     # the same lattices at equilibrium (ordered start, which the cluster
     # update equilibrates quickly at T_c), where clusters are large
     "2d-eq": dict(dim=2, L=4096, T=TC2, seed=2, equil=1000, start="ordered"),
@@ -91,7 +93,9 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="2d",
                     choices=sorted(WORKLOADS) + ["batched", "served", "binder"])
-    ap.add_argument("--updates-per-step", type=int, default=1000)
+    ap.add_argument("--updates-per-step", type=int, default=None,
+                    help="updates per step (default: the workload's measured run, "
+                         "10^4 for 2d and 3d, else 1000)")
     ap.add_argument("--equil", type=int, default=None)
     ap.add_argument("--schedule", default="auto",
                     choices=["auto", "persistent", "graph", "cluster"])
@@ -272,7 +276,7 @@ def run_batched(args, n_replicas=512, updates=None, embed=False):
     import paper_1110_0899_gb300 as w
     from paper_1110_0899_gb300 import batched, workloads
     torch.cuda.set_device(0)
-    U = updates or args.updates_per_step
+    U = updates or args.updates_per_step or 1000
     specs = workloads.batched_replicas(n_replicas)
     plan, table = batched.autotune(specs, probe_updates=max(10, U // 4))
     lat_b = [w.WolffLattice(s["dim"], s["L"], s["T"], seed=s["seed"]) for s in specs]
@@ -419,7 +423,7 @@ def run_xy(args):
     dim, L, T = wl["dim"], wl["L"], wl["T"]
     seed = rank_seed(wl["seed"], rank)
     equil = wl["equil"] if args.equil is None else args.equil
-    U = args.updates_per_step
+    U = args.updates_per_step or wl.get("updates", 1000)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         lat = w.WolffXY(dim, L, T, seed=seed, stream=stream, grid_blocks=args.blocks,
@@ -567,7 +571,7 @@ def main():
     dim, L, T = wl["dim"], wl["L"], wl["T"]
     seed = rank_seed(wl["seed"], rank)
     equil = wl["equil"] if args.equil is None else args.equil
-    U = args.updates_per_step
+    U = args.updates_per_step or wl.get("updates", 1000)
     sched = {"auto": w.SCHED_AUTO, "persistent": w.SCHED_PERSISTENT, "graph": w.SCHED_GRAPH,
              "cluster": w.SCHED_CLUSTER}[args.schedule]
 
@@ -592,11 +596,19 @@ def main():
             done += k
         torch.cuda.synchronize()
         snap, t_snap = lat.get_state()
+        if wl.get("q"):
+            def restore():
+                lat.set_state(snap, t_snap)
+        else:
+            snap_bits = w.pack_spins(snap)
+
+            def restore():   # 2.1 MB upload of the equilibrated lattice, untimed
+                lat.set_state_bits(snap_bits, t_snap)
         # warm-up steps
         for _ in range(args.warmup):
+            restore()
             w.wolff_step(lat.handle, U, rec_buf)
         torch.cuda.synchronize()
-        stats0 = lat.stats()
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         recs = []
@@ -606,6 +618,7 @@ def main():
         clocks = ClockSampler(local)
         clocks.start()
         for k in range(args.steps):
+            restore()
             flush.fill_(k & 0xFF)
             starts[k].record(stream)
             w.wolff_step(lat.handle, U, rec_buf)
@@ -613,11 +626,19 @@ def main():
             recs.append(rec_buf[: U * w.RECORD_BYTES].clone())
         torch.cuda.synchronize()
         clk = clocks.stop()
+        # the kernel's counters over one more (untimed) step: restoring the
+        # lattice resets them
+        restore()
+        stats0 = lat.stats()
+        w.wolff_step(lat.handle, U, rec_buf)
         stats1 = lat.stats()
         if world > 1:
             torch.distributed.barrier()
         step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-        records = np.concatenate([r.cpu().numpy().view(w.RECORD_DTYPE) for r in recs])
+        step_recs = [r.cpu().numpy().view(w.RECORD_DTYPE) for r in recs]
+        # every step ran the same updates from the same lattice
+        repeat_identical = all(np.array_equal(step_recs[0], r) for r in step_recs[1:])
+        records = np.concatenate(step_recs)
         flips = int(records["C"].astype(np.int64).sum())
         total_ms = float(sum(step_ms))
         levels = records["levels"].astype(np.int64)
@@ -643,6 +664,7 @@ def main():
                                          bits_out=False)
                 e2e_s += time.perf_counter() - t0
                 e2e_flips += int(r["C"].astype(np.int64).sum())
+                repeat_identical = repeat_identical and np.array_equal(r, step_recs[0])
             e2e = {"value": e2e_flips / e2e_s, "unit": UNIT,
                    "h2d_bytes_per_step": int(snap_in.nbytes),
                    "d2h_bytes_per_step": int(U * w.RECORD_BYTES)}
@@ -695,10 +717,11 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
         "data": "synthetic",
-        "config": {"workload": "%s%dD L=%d T=%.6g J=1 seed %d, %s start, %d equilibration + %d x %d "
-                               "recorded updates, one lattice per launch"
+        "config": {"workload": "%s%dD L=%d T=%.6g J=1 seed %d, %s start, %d equilibration "
+                               "updates, then per step the next %d recorded updates in one "
+                               "launch from the restored equilibrated lattice"
                                % ("q=%d Potts, " % wl["q"] if wl.get("q") else "", dim, L, T, seed,
-                                  wl["start"], equil, args.steps, U),
+                                  wl["start"], equil, U),
                    "dim": dim, "L": L, "T": T, "seed": seed, "updates_per_step": U,
                    "schedule": args.schedule, "grid_blocks": info["grid_blocks"],
                    "t_up": args.t_up, "t_down": args.t_down,
@@ -709,7 +732,8 @@ def main():
         "clocks": clk, "batched": batched_out, "served": served_out,
         "detail": {"mean_cluster": flips / len(records), "mean_levels": float(levels.mean()),
                    "max_levels": int(levels.max()), "ms_per_update": total_ms / len(records),
-                   "persistent_counters": {k: stats1[k] - stats0[k] for k in stats1}},
+                   "steps_and_e2e_records_identical": bool(repeat_identical),
+                   "step_counters": {k: stats1[k] - stats0[k] for k in stats1}},
     }
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -61,7 +61,7 @@ struct wolff_ctx {
     unsigned long long wait_ns = 2000000000ull;
     uint32_t t_up = 128, t_down = 64;
     bool thresholds_set = false;
-    int win_levels = kDefaultWindowLevels;   // window mode: growth levels per round (0 = off)
+    int win_levels = 0;   // window mode: growth levels per round (0 = off; set at init)
     int cluster = 8;
     int max_cluster = 8;
     std::string err;
@@ -335,6 +335,7 @@ static wolff_status init_common(wolff_ctx **out, int dim, int L, double J, doubl
     wolff_ctx *c = new (std::nothrow) wolff_ctx;
     if (!c) return WOLFF_ENOMEM;
     c->dim = dim;
+    c->win_levels = default_window_levels(dim);
     c->L = L;
     c->N = sites(dim, L);
     c->J = J;
@@ -490,7 +491,8 @@ wolff_status wolff_set_local_thresholds(wolff_ctx *c, uint32_t t_up, uint32_t t_
 wolff_status wolff_set_burst(wolff_ctx *c, int enable) {
     if (!c) return WOLFF_EINVAL;
     if (enable < 0) return fail(c, WOLFF_EINVAL, "enable must be >= 0");
-    c->win_levels = enable == 0 ? 0 : enable == 1 ? kDefaultWindowLevels : (enable > 64 ? 64 : enable);
+    c->win_levels = enable == 0 ? 0 : enable == 1 ? default_window_levels(c->dim)
+                                                 : (enable > 64 ? 64 : enable);
     return WOLFF_OK;
 }
 

@@ -325,6 +325,29 @@ __device__ __forceinline__ uint32_t flat_slot(const uint32_t *off, uint32_t S, u
     return lo;
 }
 
+__device__ __forceinline__ void prefetch_l1(const void *ptr) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(ptr));
+}
+
+// Lines a member j, added through direction s >= 2 (along y or z), reads
+// when it expands that its parent's level did not: the next row (or plane)
+// on along s, and in 3D the two lines beside j along the other of y, z.
+// Indices are taken mod N; a wrong line at a wrap only costs a prefetch.
+template <int DIM>
+__device__ __forceinline__ void prefetch_two_hop(const Geometry &g, const uint8_t *spins,
+                                                 uint32_t j, uint32_t s) {
+    const uint32_t N = g.N;
+    const uint32_t st = (s >> 1) == 1 ? g.L : g.LL;
+    const uint32_t ahead = (s & 1u) ? (j >= st ? j - st : j + N - st)
+                                    : (j + st < N ? j + st : j + st - N);
+    prefetch_l1(spins + ahead);
+    if (DIM == 3) {
+        const uint32_t o = (s >> 1) == 1 ? g.LL : g.L;
+        prefetch_l1(spins + (j + o < N ? j + o : j + o - N));
+        prefetch_l1(spins + (j >= o ? j - o : j + N - o));
+    }
+}
+
 // Warp: a fresh speculative growth of update t (seed claimed in the hash set).
 template <int DIM>
 __device__ __forceinline__ void win_start(const StepParams &p, unsigned long long t,
@@ -335,6 +358,15 @@ __device__ __forceinline__ void win_start(const StepParams &p, unsigned long lon
     __syncwarp();
     const uint32_t i0 = seed_site(p, t);
     sig0bit = __ldca(p.spins + i0) & 1u;
+    // the first level reads the rows next to the seed's (index +-L, and +-L^2
+    // in 3D, taken mod N: a wrong line at a wrap only costs a prefetch)
+    if (lane < 2 * (DIM - 1)) {
+        const uint32_t step = (lane >> 1) == 0 ? p.g.L : p.g.LL;
+        const uint32_t N = p.g.N;
+        const uint32_t nb = (lane & 1u) ? (i0 >= step ? i0 - step : i0 + N - step)
+                                        : (i0 + step < N ? i0 + step : i0 + step - N);
+        prefetch_l1(p.spins + nb);
+    }
     if (lane == 0) {
         set_insert(hset, hslots, i0);
         members[0] = pack_index<DIM>(p.g, i0);
@@ -419,6 +451,9 @@ __device__ __forceinline__ bool win_level(const StepParams &p, uint32_t *members
         if (fresh) {
             const uint32_t pos = n + __popc(fm & lt);
             if (pos < cap) members[pos] = pj;
+            // a member added along y or z expands next level into the row
+            // beyond it (and, in 3D, the planes beside it): start those lines
+            if (s >= 2) prefetch_two_hop<DIM>(p.g, p.spins, j, s);
         }
         n += __popc(fm);
         if (__any_sync(kFullMask, full) || n > cap) too_big = true;
@@ -433,8 +468,8 @@ __device__ __forceinline__ bool win_level(const StepParams &p, uint32_t *members
 // one lane per (member, direction) pair.
 template <int DIM>
 __device__ __forceinline__ int win_boundary(const StepParams &p, const uint32_t *members,
-                                            const uint32_t *hset, uint32_t hslots, uint32_t n,
-                                            uint32_t sig0bit, uint32_t lane) {
+                                            const uint8_t *amask, const uint32_t *hset,
+                                            uint32_t hslots, uint32_t n, uint32_t lane) {
     constexpr uint32_t Z = 2 * DIM;
     constexpr uint32_t PER = 32 / Z;
     const uint32_t km = lane / Z, s = lane % Z;
@@ -445,11 +480,14 @@ __device__ __forceinline__ int win_boundary(const StepParams &p, const uint32_t 
             uint32_t self, j, pj, owner;
             neighbour_of<DIM>(p.g, members[k], s, self, j, pj, owner);
             const uint32_t home = hset[set_hash(j, hslots)];
-            const uint8_t cur = __ldca(p.spins + j);
+            // the neighbour's alignment as the growth read it: the lattice
+            // has not changed under it since (a commit that flips a site of
+            // the read set restarts the update)
+            const bool par = (amask[k] >> s) & 1u;
             // the home slot settles membership unless it holds another site
             const bool member =
                 home == j || (home != kEmptyKey && set_contains(hset, hslots, j));
-            if (!member) dE += ((cur & 1u) == sig0bit) ? -1 : 1;
+            if (!member) dE += par ? -1 : 1;
         }
     }
 #pragma unroll
@@ -686,12 +724,19 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
             uint32_t steps = 0;
             while (steps < K) {
                 if (!have) {
-                    uint32_t took = kNone;
+                    uint32_t took = kNone, tj = 0;
                     if (lane == 0) {
-                        const uint32_t r = atomicAdd(&v.scal[kScRgTake], 1u);
-                        if (r < v.scal[kScRgCount]) {
-                            took = v.rg[r];
-                        } else {
+                        // the regrowth queue first (the queue only shrinks
+                        // while warps grow, so a plain read may skip it)
+                        const uint32_t rg_n = v.scal[kScRgCount];
+                        if (ld_volatile_u32(&v.scal[kScRgTake]) < rg_n) {
+                            const uint32_t r = atomicAdd(&v.scal[kScRgTake], 1u);
+                            if (r < rg_n) {
+                                took = v.rg[r];
+                                tj = v.j[took];
+                            }
+                        }
+                        if (took == kNone) {
                             // the next fresh update, if below the window's
                             // end (never handed out twice: next_q only grows)
                             const uint32_t q_end = v.scal[kScQEnd];
@@ -700,7 +745,8 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
                                 const uint32_t prev = atomicCAS(&v.scal[kScNextQ], q, q + 1);
                                 if (prev == q) {
                                     took = q & (S - 1);
-                                    v.j[took] = q * cs + rank;
+                                    tj = q * cs + rank;
+                                    v.j[took] = tj;
                                     break;
                                 }
                                 q = prev;
@@ -709,10 +755,10 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
                         if (took != kNone) v.state[took] = kSlotGrowing;
                     }
                     took = __shfl_sync(kFullMask, took, 0);
+                    tj = __shfl_sync(kFullMask, tj, 0);
                     if (took == kNone) break;
-                    __syncwarp();
                     g_slot = took;
-                    g_j = v.j[took];
+                    g_j = tj;
                     have = true;
                     restart = true;
                 }
@@ -734,7 +780,8 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
                     }
                     have = false;
                 } else if (g_lo == g_n) {
-                    const int dE = win_boundary<DIM>(p, members, hset, hslots, g_n, g_sig, lane);
+                    const int dE = win_boundary<DIM>(p, members, v.amask + g_slot * cap, hset,
+                                                     hslots, g_n, lane);
                     if (lane == 0) {
                         v.meta[g_slot] = make_uint4(g_n, g_levels, (uint32_t)dE, g_sig);
                         v.state[g_slot] = kSlotDone;

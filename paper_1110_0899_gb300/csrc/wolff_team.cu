@@ -47,18 +47,21 @@ enum : unsigned int { kTeamLevels = 1, kTeamFinish = 2, kTeamExit = 3, kTeamWind
 //     update index that flips this site", spread over the CTAs' shared
 //     memory (each site has an owner CTA, reached through distributed shared
 //     memory);
-//   - update j conflicts if it reads (its members and their neighbours) a
-//     site that an earlier finished update of the window flips;
+//   - update j conflicts if an earlier finished update of the window flips
+//     one of its members or a neighbour across an open boundary bond (draw
+//     below the threshold): only those flips can change its cluster;
 //   - the round commits [c, cut), cut = the first update that is unfinished
-//     or conflicts: it flips their members and writes their records;
+//     or conflicts: it flips their members and writes their records, each
+//     boundary sum corrected for the earlier flips of neighbours across
+//     closed bonds (a closed bond's neighbour stays out whatever its spin,
+//     and its term only changes sign);
 //   - every uncommitted update, finished or still growing, that read a site
 //     the committed ones flip is grown again from its seed; the others keep
 //     their clusters, which the new lattice leaves unchanged.
-// An update that read no site flipped by an earlier one sees exactly the
-// lattice the serial chain shows it, so every committed update is the serial
-// one: the same component, level count, boundary sum and record.  An update
-// whose cluster outgrows the cap (or whose flips do not fit the map) stops the
-// window; it runs the ordinary way.
+// A committed update therefore finds the component, level count, boundary
+// sum and record of the serial chain.  An update whose cluster outgrows the
+// cap (or whose flips do not fit the map) stops the window; it runs the
+// ordinary way.
 constexpr int kWinMaxWarps = 16;
 constexpr uint32_t kWinCap = 64;            // members per speculative update (see window_cap)
 constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;
@@ -236,25 +239,30 @@ __device__ __forceinline__ bool set_contains(const uint32_t *set, uint32_t slots
 
 // The window's per-CTA state in dynamic shared memory: S slots of `cap`
 // members (packed coordinates), each slot's result (|C|, levels, dE_bond / 2,
-// seed spin) as one 16-byte word, then the slot's update index, state and
-// lowest conflicting update, the regrowth queue, the slot offsets of the
-// flattened member list, a few counters, and per member the alignment of
-// its 2 DIM neighbours with the seed spin as the growth read them (bit s =
-// neighbour s parallel), which revalidates a finished update after a change
-// of the lattice made outside the window.
+// seed spin) as one 16-byte word, then per slot the update index, state,
+// lowest update it conflicts with, lowest update that flips any site it read,
+// and the correction of its boundary sum; the regrowth queue, the slot offsets
+// of the flattened member list and a few counters; and per member three bit
+// masks over its 2 DIM bonds (bit s = bond to neighbour s):
+//   amask: the neighbour was parallel to the seed spin when the growth read it
+//          (also revalidates a finished update after a change of the lattice
+//          made outside the window),
+//   omask: the bond's draw is below the threshold (the bond is open),
+//   bmask: the neighbour is not a member (a boundary bond).
 struct WinView {
-    uint32_t *members, *j, *state, *cmin, *rg, *off, *scal;
+    uint32_t *members, *j, *state, *cmin, *amin, *rg, *off, *scal;
+    int *dcorr;
     uint4 *meta;
-    uint8_t *amask;
+    uint8_t *amask, *omask, *bmask;
     uint4 *lmeta;   // leader: results of updates c .. c + P - 1, pushed by their CTAs
 };
 enum : uint32_t { kScNextQ = 0, kScRgCount = 1, kScRgTake = 2, kScQEnd = 3, kScMin = 4 };
 constexpr uint32_t kWinScalars = 8;
 
 // Layout (32-bit words unless noted): members S*cap | meta S uint4 | lmeta
-// S*cs uint4 | j, state, cmin, rg S each | off S+1 | scalars | amask S*cap
-// bytes.  Both uint4 arrays start at multiples of 16 bytes (cap is a multiple
-// of 4 and the base is 16-byte aligned).
+// S*cs uint4 | j, state, cmin, amin, dcorr, rg S each | off S+1 | scalars |
+// amask, omask, bmask S*cap bytes each.  Both uint4 arrays start at multiples
+// of 16 bytes (cap is a multiple of 4 and the base is 16-byte aligned).
 __device__ __forceinline__ WinView win_view(uint32_t *base, uint32_t S, uint32_t cap,
                                             uint32_t cs) {
     WinView v;
@@ -265,10 +273,14 @@ __device__ __forceinline__ WinView win_view(uint32_t *base, uint32_t S, uint32_t
     v.j = m;
     v.state = m + S;
     v.cmin = m + 2 * S;
-    v.rg = m + 3 * S;
-    v.off = m + 4 * S;          // S + 1 entries
-    v.scal = m + 5 * S + 1;     // kWinScalars
-    v.amask = reinterpret_cast<uint8_t *>(m + 5 * S + 1 + kWinScalars);   // S * cap bytes
+    v.amin = m + 3 * S;
+    v.dcorr = reinterpret_cast<int *>(m + 4 * S);
+    v.rg = m + 5 * S;
+    v.off = m + 6 * S;          // S + 1 entries
+    v.scal = m + 7 * S + 1;     // kWinScalars
+    v.amask = reinterpret_cast<uint8_t *>(m + 7 * S + 1 + kWinScalars);   // S * cap bytes
+    v.omask = v.amask + S * cap;
+    v.bmask = v.omask + S * cap;
     return v;
 }
 
@@ -409,7 +421,8 @@ __device__ __forceinline__ void neighbour_of(const Geometry &g, uint32_t packed,
 // Returns true when the cluster outgrew cap.
 template <int DIM>
 __device__ __forceinline__ bool win_level(const StepParams &p, uint32_t *members, uint8_t *amask,
-                                          uint32_t *hset, uint32_t hslots, uint32_t cap,
+                                          uint8_t *omask, uint32_t *hset, uint32_t hslots,
+                                          uint32_t cap,
                                           uint32_t lane, uint32_t &lo, uint32_t &n,
                                           uint32_t sig0bit, uint32_t tlo, uint32_t thi) {
     constexpr uint32_t Z = 2 * DIM;          // directions per member
@@ -422,7 +435,7 @@ __device__ __forceinline__ bool win_level(const StepParams &p, uint32_t *members
         const uint32_t k = b + km;
         const bool act = km < PER && k < hi;
         uint32_t j = 0, pj = 0;
-        bool par = false, cand = false;
+        bool par = false, open = false;
         if (act) {
             uint32_t self, owner;
             neighbour_of<DIM>(p.g, members[k], s, self, j, pj, owner);
@@ -432,11 +445,16 @@ __device__ __forceinline__ bool win_level(const StepParams &p, uint32_t *members
             const uint32_t d = s >> 1;
             const uint32_t r = d == 0 ? draw.v[0] : d == 1 ? draw.v[1] : draw.v[2];
             par = (uint32_t)(v & 1u) == sig0bit;
-            cand = par && (unsigned long long)r < p.thr;
+            open = (unsigned long long)r < p.thr;
         }
-        // the member's alignment mask, as its Z lanes read it
+        const bool cand = par && open;
+        // the member's alignment and open-bond masks, as its Z lanes read them
         const uint32_t pm = __ballot_sync(kFullMask, par);
-        if (act && s == 0) amask[k] = (uint8_t)((pm >> (km * Z)) & ((1u << Z) - 1u));
+        const uint32_t om = __ballot_sync(kFullMask, open);
+        if (act && s == 0) {
+            amask[k] = (uint8_t)((pm >> (km * Z)) & ((1u << Z) - 1u));
+            omask[k] = (uint8_t)((om >> (km * Z)) & ((1u << Z) - 1u));
+        }
         bool fresh = false, full = false;
         if (cand) {
             const uint32_t prev = atomicCAS(hset + set_hash(j, hslots), kEmptyKey, j);
@@ -468,15 +486,18 @@ __device__ __forceinline__ bool win_level(const StepParams &p, uint32_t *members
 // one lane per (member, direction) pair.
 template <int DIM>
 __device__ __forceinline__ int win_boundary(const StepParams &p, const uint32_t *members,
-                                            const uint8_t *amask, const uint32_t *hset,
-                                            uint32_t hslots, uint32_t n, uint32_t lane) {
+                                            const uint8_t *amask, uint8_t *bmask,
+                                            const uint32_t *hset, uint32_t hslots, uint32_t n,
+                                            uint32_t lane) {
     constexpr uint32_t Z = 2 * DIM;
     constexpr uint32_t PER = 32 / Z;
     const uint32_t km = lane / Z, s = lane % Z;
     int dE = 0;
     for (uint32_t b = 0; b < n; b += PER) {
         const uint32_t k = b + km;
-        if (km < PER && k < n) {
+        const bool act = km < PER && k < n;
+        bool outside = false;
+        if (act) {
             uint32_t self, j, pj, owner;
             neighbour_of<DIM>(p.g, members[k], s, self, j, pj, owner);
             const uint32_t home = hset[set_hash(j, hslots)];
@@ -485,10 +506,11 @@ __device__ __forceinline__ int win_boundary(const StepParams &p, const uint32_t 
             // the read set restarts the update)
             const bool par = (amask[k] >> s) & 1u;
             // the home slot settles membership unless it holds another site
-            const bool member =
-                home == j || (home != kEmptyKey && set_contains(hset, hslots, j));
-            if (!member) dE += par ? -1 : 1;
+            outside = !(home == j || (home != kEmptyKey && set_contains(hset, hslots, j)));
+            if (outside) dE += par ? -1 : 1;
         }
+        const uint32_t bm = __ballot_sync(kFullMask, outside);
+        if (act && s == 0) bmask[k] = (uint8_t)((bm >> (km * Z)) & ((1u << Z) - 1u));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dE += __shfl_xor_sync(kFullMask, dE, o);
@@ -514,6 +536,46 @@ __device__ __forceinline__ uint32_t read_conflict(const StepParams &p, uint32_t 
     for (int q = 0; q < 2 * DIM + 1; ++q)
         if (v[q] < below && v[q] < best) best = v[q];
     return best;
+}
+
+// A finished update's dependence on an earlier update that flips one of the
+// sites it read, for its member `packed` (stamps as in read_conflict, only
+// updates below `below` count):
+//   rel:   the lowest that flips the member itself or the neighbour across an
+//          open boundary bond (rmask).  Those flips change the cluster: section
+//          2's cluster holds every site reached through an open bond from a
+//          member with the seed spin, and flipping an anti-parallel neighbour
+//          across an open bond would add it;
+//   any:   the lowest that flips any site read (the member and its boundary
+//          neighbours; neighbours that are members check themselves);
+//   delta: the change of the update's boundary sum (dE_bond / 2) if every
+//          flip of a neighbour across a closed boundary bond (cmask) comes
+//          first.  A closed bond never joins its neighbour whatever its spin,
+//          so such a flip only turns that bond's term from -1 to +1 or back.
+template <int DIM>
+__device__ __forceinline__ void check_member(const StepParams &p, uint32_t packed, uint32_t below,
+                                             uint32_t rmask, uint32_t cmask, uint32_t amask,
+                                             uint32_t &rel, uint32_t &any, int &delta) {
+    uint32_t i;
+    Neighbours<DIM> nb2;
+    neighbours<DIM>(p.g, packed, &i, nb2);
+    uint32_t v[2 * DIM + 1];
+    v[0] = __ldcg(p.list + i);
+#pragma unroll
+    for (int s = 0; s < 2 * DIM; ++s) v[s + 1] = __ldcg(p.list + nb2.idx[s]);
+    rel = v[0] < below ? v[0] : kNone;
+    any = rel;
+    delta = 0;
+#pragma unroll
+    for (int s = 0; s < 2 * DIM; ++s) {
+        if (v[s + 1] >= below) continue;
+        if ((rmask >> s) & 1u) rel = min(rel, v[s + 1]);
+        if ((cmask >> s) & 1u) {
+            any = min(any, v[s + 1]);
+            delta += ((amask >> s) & 1u) ? 2 : -2;
+        }
+    }
+    any = min(any, rel);
 }
 
 // Block: inclusive scan of three 64-bit sums (blockDim.x <= 512); also
@@ -769,7 +831,8 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
                     restart = false;
                 }
                 const bool big =
-                    win_level<DIM>(p, members, v.amask + g_slot * cap, hset, hslots, cap, lane,
+                    win_level<DIM>(p, members, v.amask + g_slot * cap, v.omask + g_slot * cap,
+                                   hset, hslots, cap, lane,
                                    g_lo, g_n, g_sig, (uint32_t)t, (uint32_t)(t >> 32));
                 ++g_levels;
                 ++steps;
@@ -780,8 +843,9 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
                     }
                     have = false;
                 } else if (g_lo == g_n) {
-                    const int dE = win_boundary<DIM>(p, members, v.amask + g_slot * cap, hset,
-                                                     hslots, g_n, lane);
+                    const int dE = win_boundary<DIM>(p, members, v.amask + g_slot * cap,
+                                                     v.bmask + g_slot * cap, hset, hslots, g_n,
+                                                     lane);
                     if (lane == 0) {
                         v.meta[g_slot] = make_uint4(g_n, g_levels, (uint32_t)dE, g_sig);
                         v.state[g_slot] = kSlotDone;
@@ -795,7 +859,11 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
         __syncthreads();
         // ---- flatten this CTA's finished updates: off[s] = members before slot s
         if (warp == 0) win_flatten(v, S, lane);
-        for (uint32_t k = threadIdx.x; k < S; k += blockDim.x) v.cmin[k] = kNone;
+        for (uint32_t k = threadIdx.x; k < S; k += blockDim.x) {
+            v.cmin[k] = kNone;
+            v.amin[k] = kNone;
+            v.dcorr[k] = 0;
+        }
         cl.sync();   // every stamp is clear, every CTA has grown and flattened
         if (timer) win_tick(win_ns[0], tick);
         // ---- stamp the flips of the finished updates: list[i] = lowest one
@@ -806,21 +874,21 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
             unpack<DIM>(v.members[s * cap + (f - v.off[s])], cc);
             atomicMin(p.list + site_index<DIM>(p.g, cc), v.j[s]);
         }
-        {
-            // every finished update's result goes to the leader, at its
-            // offset from the window start, for the record scan of the commit
-            uint4 *lead_meta = cl.map_shared_rank(v.lmeta, 0);
-            for (uint32_t s = threadIdx.x; s < S; s += blockDim.x)
-                if (v.state[s] == kSlotDone) lead_meta[v.j[s] - c] = v.meta[s];
-        }
         cl.sync();
         if (timer) win_tick(win_ns[1], tick);
-        // ---- conflicts: lowest earlier update flipping a site each one read
+        // ---- conflicts: the lowest earlier update whose flips change each
+        // finished update's cluster, and the corrections of its boundary sum
         for (uint32_t f = threadIdx.x; f < total; f += blockDim.x) {
             const uint32_t s = flat_slot(v.off, S, f);
-            const uint32_t jj = v.j[s];
-            const uint32_t best = read_conflict<DIM>(p, v.members[s * cap + (f - v.off[s])], jj);
-            if (best != kNone) atomicMin(&v.cmin[s], best);
+            const uint32_t k = s * cap + (f - v.off[s]);
+            const uint32_t bm = v.bmask[k], om = v.omask[k];
+            uint32_t rel, any;
+            int delta;
+            check_member<DIM>(p, v.members[k], v.j[s], bm & om, bm & ~om, v.amask[k], rel, any,
+                              delta);
+            if (rel != kNone) atomicMin(&v.cmin[s], rel);
+            if (any != kNone) atomicMin(&v.amin[s], any);
+            if (delta) atomicAdd(&v.dcorr[s], delta);
         }
         __syncthreads();
         {
@@ -860,18 +928,26 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
             }
         }
         // the leader writes the records of [c, cut) at the start of the next
-        // round (or on leaving), off this phase's critical path; their
-        // results stay in lmeta until the next stamping phase rewrites it
+        // round (or on leaving), off this phase's critical path, from the
+        // results pushed here at their offsets from the window start: every
+        // update below it commits, so each boundary correction applies
         if (cut > c) {
             rec_lo = c;
             rec_hi = cut;
         }
+        uint4 *lead_meta = cl.map_shared_rank(v.lmeta, 0);
         // the committed slots are free; a finished update that read a
         // committed flip grows again
         for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) {
             if (v.state[s] == kSlotDone) {
-                if (v.j[s] < cut) v.state[s] = kSlotFree;
-                else if (v.cmin[s] < cut) v.state[s] = kSlotRegrow;
+                if (v.j[s] < cut) {
+                    uint4 m = v.meta[s];
+                    m.z = (uint32_t)((int)m.z + v.dcorr[s]);
+                    lead_meta[v.j[s] - c] = m;
+                    v.state[s] = kSlotFree;
+                } else if (v.amin[s] < cut) {
+                    v.state[s] = kSlotRegrow;
+                }
             }
         }
         // an update still growing that read a committed flip starts again
@@ -1252,8 +1328,8 @@ size_t window_smem_bytes(int dim, int threads, int window_slots, int cluster_siz
     if (window_slots <= 0) return 0;
     const size_t cap = window_cap(dim, threads);
     const size_t S = (size_t)window_slots;
-    return (S * cap + 9 * S + 1 + kWinScalars + 4 * S * (size_t)cluster_size) * sizeof(uint32_t) +
-           S * cap;
+    return (S * cap + 11 * S + 1 + kWinScalars + 4 * S * (size_t)cluster_size) * sizeof(uint32_t) +
+           3 * S * cap;
 }
 
 cudaError_t launch_team(int dim, const StepParams &single, const StepParams *d_table, int njobs,

@@ -418,18 +418,18 @@ def check_run_window(w, dim, L, T, n, levels, cs, threads, seed, ref, s_ref):
                                                       (3, 256, 4.5115, 3, 2000, 8)])
 def test_full_size_in_bench_configuration(dim, L, T, seed, equil, sample):
     """The workloads bench.py times, at full size and in its launch
-    configuration (default schedule: one 16-CTA cluster, 512 threads, bursts):
-    after the specified equilibration the GPU runs one bench step of 1000
-    recorded updates.  The oracle replays the first `sample` updates from the
-    GPU's snapshot and must match them bit for bit; all 1000 records must obey
-    the update's invariants; the incremental E and M must equal a full
-    recount of the final lattice."""
+    configuration (default schedule: one 16-CTA cluster, 512 threads, window
+    mode): after the specified equilibration the GPU runs one bench step, the
+    10^4 measured updates in one launch.  The oracle replays the first
+    `sample` updates from the GPU's snapshot and must match them bit for bit;
+    all 10^4 records must obey the update's invariants; the incremental E and
+    M must equal a full recount of the final lattice."""
     torch, w = require_cuda()
     lat = w.WolffLattice(dim, L, T, seed=seed)
     lat.step(equil, records=False)
     snap, t0 = lat.get_state()
     assert t0 == equil
-    rec = lat.step(1000)
+    rec = lat.step(10000)
     ref, _ = oracle_trajectory(dim, L, T, seed, sample, t0=t0, s=snap)
     assert_records_equal(rec[:sample], ref, "full size %dD L=%d" % (dim, L))
     N = L ** dim
@@ -455,7 +455,9 @@ def test_whole_trajectory_in_segments(dim, L, T, seed):
     and must reach the next one bit for bit (any wrong cluster anywhere in
     the segment would change it); E_bond and M at every snapshot equal the
     definitions; every record of the 10^4 measured updates obeys
-    |dM| = 2|C| and E changes by an even amount."""
+    |dM| = 2|C| and E changes by an even amount.  The benchmark's own step,
+    the 10^4 measured updates in one launch from the equilibrated lattice,
+    must then give the same records and reach the oracle-checked end."""
     torch, w = require_cuda()
     thr = oracle.bond_threshold(1.0, T)
     lat = w.WolffLattice(dim, L, T, seed=seed)
@@ -486,3 +488,11 @@ def test_whole_trajectory_in_segments(dim, L, T, seed):
             s_k = snaps[4 + (k + 1) // 500][0]
             assert (E_prev, M_prev) == (oracle.energy_bond(dim, L, s_k),
                                         oracle.magnetisation(dim, L, s_k)), k
+    # one launch of the 10^4 measured updates, as bench.py times them
+    lat = w.WolffLattice(dim, L, T, seed=seed)
+    lat.set_state(*snaps[4])
+    one = lat.step(10000)
+    end, t_end = lat.get_state()
+    lat.close()
+    assert t_end == snaps[-1][1] and np.array_equal(end, snaps[-1][0])
+    assert np.array_equal(one, rec)

@@ -241,8 +241,9 @@ __device__ __forceinline__ bool set_contains(const uint32_t *set, uint32_t slots
 // members (packed coordinates), each slot's result (|C|, levels, dE_bond / 2,
 // seed spin) as one 16-byte word, then per slot the update index, state,
 // lowest update it conflicts with, lowest update that flips any site it read,
-// and the correction of its boundary sum; the regrowth queue, the slot offsets
-// of the flattened member list and a few counters; and per member three bit
+// and the correction of its boundary sum; the regrowth queue, each slot's seed
+// site, the slot offsets of the flattened member list and a few counters; and
+// per member three bit
 // masks over its 2 DIM bonds (bit s = bond to neighbour s):
 //   amask: the neighbour was parallel to the seed spin when the growth read it
 //          (also revalidates a finished update after a change of the lattice
@@ -250,17 +251,18 @@ __device__ __forceinline__ bool set_contains(const uint32_t *set, uint32_t slots
 //   omask: the bond's draw is below the threshold (the bond is open),
 //   bmask: the neighbour is not a member (a boundary bond).
 struct WinView {
-    uint32_t *members, *j, *state, *cmin, *amin, *rg, *off, *scal;
+    uint32_t *members, *j, *state, *cmin, *amin, *rg, *seed, *off, *scal;
     int *dcorr;
     uint4 *meta;
     uint8_t *amask, *omask, *bmask;
     uint4 *lmeta;   // leader: results of updates c .. c + P - 1, pushed by their CTAs
 };
-enum : uint32_t { kScNextQ = 0, kScRgCount = 1, kScRgTake = 2, kScQEnd = 3, kScMin = 4 };
+enum : uint32_t { kScNextQ = 0, kScRgCount = 1, kScRgTake = 2, kScQEnd = 3, kScMin = 4,
+                  kScSeeded = 5, kScSeedLo = 6 };
 constexpr uint32_t kWinScalars = 8;
 
 // Layout (32-bit words unless noted): members S*cap | meta S uint4 | lmeta
-// S*cs uint4 | j, state, cmin, amin, dcorr, rg S each | off S+1 | scalars |
+// S*cs uint4 | j, state, cmin, amin, dcorr, rg, seed S each | off S+1 | scalars |
 // amask, omask, bmask S*cap bytes each.  Both uint4 arrays start at multiples
 // of 16 bytes (cap is a multiple of 4 and the base is 16-byte aligned).
 __device__ __forceinline__ WinView win_view(uint32_t *base, uint32_t S, uint32_t cap,
@@ -276,9 +278,10 @@ __device__ __forceinline__ WinView win_view(uint32_t *base, uint32_t S, uint32_t
     v.amin = m + 3 * S;
     v.dcorr = reinterpret_cast<int *>(m + 4 * S);
     v.rg = m + 5 * S;
-    v.off = m + 6 * S;          // S + 1 entries
-    v.scal = m + 7 * S + 1;     // kWinScalars
-    v.amask = reinterpret_cast<uint8_t *>(m + 7 * S + 1 + kWinScalars);   // S * cap bytes
+    v.seed = m + 6 * S;
+    v.off = m + 7 * S;          // S + 1 entries
+    v.scal = m + 8 * S + 1;     // kWinScalars
+    v.amask = reinterpret_cast<uint8_t *>(m + 8 * S + 1 + kWinScalars);   // S * cap bytes
     v.omask = v.amask + S * cap;
     v.bmask = v.omask + S * cap;
     return v;
@@ -360,15 +363,15 @@ __device__ __forceinline__ void prefetch_two_hop(const Geometry &g, const uint8_
     }
 }
 
-// Warp: a fresh speculative growth of update t (seed claimed in the hash set).
+// Warp: a fresh speculative growth of the update with seed site i0 (claimed
+// in the hash set).
 template <int DIM>
-__device__ __forceinline__ void win_start(const StepParams &p, unsigned long long t,
-                                          uint32_t *members, uint32_t *hset, uint32_t hslots,
-                                          uint32_t lane, uint32_t &n, uint32_t &lo,
-                                          uint32_t &levels, uint32_t &sig0bit) {
+__device__ __forceinline__ void win_start(const StepParams &p, uint32_t i0, uint32_t *members,
+                                          uint32_t *hset, uint32_t hslots, uint32_t lane,
+                                          uint32_t &n, uint32_t &lo, uint32_t &levels,
+                                          uint32_t &sig0bit) {
     for (uint32_t k = lane; k < hslots; k += 32) hset[k] = kEmptyKey;
     __syncwarp();
-    const uint32_t i0 = seed_site(p, t);
     sig0bit = __ldca(p.spins + i0) & 1u;
     // the first level reads the rows next to the seed's (index +-L, and +-L^2
     // in 3D, taken mod N: a wrong line at a wrap only costs a prefetch)
@@ -713,6 +716,7 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
         for (uint32_t k = threadIdx.x; k < S; k += blockDim.x) v.state[k] = kSlotFree;
         if (threadIdx.x == 0) {
             v.scal[kScNextQ] = 0;
+            v.scal[kScSeeded] = 0;
             v.scal[kScRgCount] = 0;
             v.scal[kScRgTake] = 0;
         }
@@ -772,9 +776,34 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
         if (threadIdx.x == 0) {
             const uint32_t wl = ld_volatile_u32(&lead->wlimit);
             const uint32_t l2 = min(lim, wl);
-            v.scal[kScQEnd] = l2 > rank ? (l2 - rank + cs - 1) / cs : 0;
+            const uint32_t q_end = l2 > rank ? (l2 - rank + cs - 1) / cs : 0;
+            v.scal[kScQEnd] = q_end;
             v.scal[kScMin] = kNone;
+            const uint32_t seeded = v.scal[kScSeeded];
+            v.scal[kScSeedLo] = max(seeded, v.scal[kScNextQ]);
+            v.scal[kScSeeded] = max(seeded, q_end);
             if (rank == 0) sh.wcut = lim;
+        }
+        __syncthreads();
+        {
+            // the seed sites of the fresh updates this round may hand out
+            // (each slot a fresh update will take is free), their lines and
+            // the rows their first level reads started towards L1, so that
+            // a warp starting one finds them there
+            const uint32_t N = p.g.N, L = p.g.L;
+            for (uint32_t q = v.scal[kScSeedLo] + threadIdx.x; q < v.scal[kScQEnd];
+                 q += blockDim.x) {
+                const uint32_t i0 = seed_site(p, p.t0 + u0 + (unsigned long long)(q * cs + rank));
+                v.seed[q & (S - 1)] = i0;
+                prefetch_l1(p.spins + i0);
+                prefetch_l1(p.spins + (i0 + L < N ? i0 + L : i0 + L - N));
+                prefetch_l1(p.spins + (i0 >= L ? i0 - L : i0 + N - L));
+                if (DIM == 3) {
+                    const uint32_t LL = p.g.LL;
+                    prefetch_l1(p.spins + (i0 + LL < N ? i0 + LL : i0 + LL - N));
+                    prefetch_l1(p.spins + (i0 >= LL ? i0 - LL : i0 + N - LL));
+                }
+            }
         }
         __syncthreads();
         if (rank == 0 && rec_hi > rec_lo) {
@@ -827,7 +856,8 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
                 const unsigned long long t = p.t0 + u0 + g_j;
                 uint32_t *members = v.members + g_slot * cap;
                 if (restart) {
-                    win_start<DIM>(p, t, members, hset, hslots, lane, g_n, g_lo, g_levels, g_sig);
+                    win_start<DIM>(p, v.seed[g_slot], members, hset, hslots, lane, g_n, g_lo,
+                                   g_levels, g_sig);
                     restart = false;
                 }
                 const bool big =
@@ -1328,7 +1358,7 @@ size_t window_smem_bytes(int dim, int threads, int window_slots, int cluster_siz
     if (window_slots <= 0) return 0;
     const size_t cap = window_cap(dim, threads);
     const size_t S = (size_t)window_slots;
-    return (S * cap + 11 * S + 1 + kWinScalars + 4 * S * (size_t)cluster_size) * sizeof(uint32_t) +
+    return (S * cap + 12 * S + 1 + kWinScalars + 4 * S * (size_t)cluster_size) * sizeof(uint32_t) +
            3 * S * cap;
 }
 

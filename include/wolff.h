@@ -282,7 +282,7 @@ wolff_status wolff_set_local_thresholds(wolff_ctx *ctx, uint32_t t_up, uint32_t 
  * committed update is exactly the serial one (section 2's cluster depends
  * only on the spins it reads and on the counter-based bond draws), so results
  * do not depend on the setting.  enable: 0 = off, 1 = on with the default
- * levels per round (24 in 2D, 16 in 3D), k >= 2 = on with k levels per round
+ * levels per round (24 in 2D, 28 in 3D), k >= 2 = on with k levels per round
  * (at most 64).  EINVAL if enable < 0. */
 wolff_status wolff_set_burst(wolff_ctx *ctx, int enable);
 

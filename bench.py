@@ -46,8 +46,8 @@ TC2 = 2.0 / math.log(1.0 + math.sqrt(2.0))
 # profiles/k_team_3d_L256_random_start.md), valid only while the kernel sources
 # hash to the captured value.
 TRAFFIC_CAPTURES = {
-    ("2d", 10000): {"src": "5e01158fc7e3", "bytes_per_launch": 11237888 + 512},
-    ("3d", 10000): {"src": "5e01158fc7e3", "bytes_per_launch": 24314624 + 94208},
+    ("2d", 10000): {"src": "2773a496567b", "bytes_per_launch": 11246848 + 256},
+    ("3d", 10000): {"src": "2773a496567b", "bytes_per_launch": 24329728 + 34560},
 }
 
 

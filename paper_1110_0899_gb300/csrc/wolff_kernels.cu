@@ -93,6 +93,88 @@ __global__ void k_measure_full(const uint8_t *spins, Geometry g, DevCtl *ctl) {
     }
 }
 
+// ---- 32 sites per thread (L a multiple of 32) ------------------------------
+// A word w covers sites 32w .. 32w+31 of one row, bit k = site 32w + k is +1.
+// Its forward bonds along x are the bits against the word shifted by one
+// (the last site against bit 0 of the next word of the row, wrapping to the
+// row's first word); along y (z) the bits of the word L/32 (L^2/32) further
+// on, wrapping within the plane (the lattice).  Over the 32 sites the bonds
+// sum to 32 - 2 popc(b ^ nb) and the spins to 2 popc(b) - 32.
+struct WordGeom {
+    uint32_t wpr, plane, words;   // words per row, per xy plane (2D: all), in all
+};
+
+__device__ __forceinline__ WordGeom word_geom(const Geometry &g, int dim) {
+    WordGeom w;
+    w.wpr = g.L >> 5;
+    w.words = g.N >> 5;
+    w.plane = dim == 3 ? (g.LL >> 5) : w.words;
+    return w;
+}
+
+template <int DIM>
+__device__ __forceinline__ void word_neighbours(const WordGeom &wg, uint32_t w, uint32_t &nxt,
+                                                uint32_t &up, uint32_t &zup) {
+    const uint32_t wr = w % wg.wpr;
+    nxt = (wr + 1 == wg.wpr) ? w - wr : w + 1;
+    const uint32_t ip = DIM == 3 ? w % wg.plane : w;
+    up = (ip + wg.wpr < wg.plane) ? w + wg.wpr : w + wg.wpr - wg.plane;
+    zup = 0;
+    if (DIM == 3) zup = (w + wg.plane < wg.words) ? w + wg.plane : w + wg.plane - wg.words;
+}
+
+__device__ __forceinline__ int word_bonds(uint32_t b, uint32_t nb) {
+    return 32 - 2 * __popc(b ^ nb);
+}
+
+// Bit 0 of each of 4 bytes -> 4 bits (byte k -> bit k): the masked bytes
+// times 2^24 + 2^17 + 2^10 + 2^3 put byte k's bit at 24 + k with every
+// other partial product outside bits 24..27 and no carries.
+__device__ __forceinline__ uint32_t bytes_to_nibble(uint32_t w) {
+    return (((w & 0x01010101u) * 0x01020408u) >> 24) & 0xFu;
+}
+
+// 32 spin bytes (16-byte aligned) -> their bit mask.
+__device__ __forceinline__ uint32_t load_word_bits(const uint8_t *p) {
+    const uint4 a = __ldg(reinterpret_cast<const uint4 *>(p));
+    const uint4 b = __ldg(reinterpret_cast<const uint4 *>(p) + 1);
+    return bytes_to_nibble(a.x) | bytes_to_nibble(a.y) << 4 | bytes_to_nibble(a.z) << 8 |
+           bytes_to_nibble(a.w) << 12 | bytes_to_nibble(b.x) << 16 | bytes_to_nibble(b.y) << 20 |
+           bytes_to_nibble(b.z) << 24 | bytes_to_nibble(b.w) << 28;
+}
+
+// 4 bits -> 4 spin bytes (0x03 for +1, 0x00 for -1): the nibble times
+// 1 + 2^7 + 2^14 + 2^21 puts bit k at 8k (partial products at 0-3, 7-10,
+// 14-17, 21-24 never overlap), masked and tripled.
+__device__ __forceinline__ uint32_t nibble_to_bytes(uint32_t nib) {
+    return ((nib * 0x00204081u) & 0x01010101u) * 3u;
+}
+
+// a8 with 32 sites per thread: 64 bytes of loads (the word and the one above
+// in y; 96 in 3D) and one byte of the next word for 32 sites.
+template <int DIM>
+__global__ void k_measure_words(const uint8_t *spins, Geometry g, DevCtl *ctl) {
+    const WordGeom wg = word_geom(g, DIM);
+    long long e = 0, m = 0;
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < wg.words;
+         w += gridDim.x * blockDim.x) {
+        uint32_t nxt, up, zup;
+        word_neighbours<DIM>(wg, w, nxt, up, zup);
+        const uint32_t b = load_word_bits(spins + 32ull * w);
+        const uint32_t right = (b >> 1) | ((uint32_t)(spins[32ull * nxt] & 1u) << 31);
+        int bonds = word_bonds(b, right) + word_bonds(b, load_word_bits(spins + 32ull * up));
+        if (DIM == 3) bonds += word_bonds(b, load_word_bits(spins + 32ull * zup));
+        e += bonds;
+        m += 2 * __popc(b) - 32;
+    }
+    e = block_sum(e);
+    m = block_sum(m);
+    if (threadIdx.x == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->full_E), (unsigned long long)e);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->full_M), (unsigned long long)m);
+    }
+}
+
 __global__ void k_zero_full(DevCtl *ctl) {
     ctl->full_E = 0;
     ctl->full_M = 0;
@@ -103,16 +185,29 @@ __global__ void k_full_to_chain(DevCtl *ctl) {
     ctl->M = ctl->full_M;
 }
 
+// Blocks for the 32-sites-per-thread passes: enough 256-thread blocks for
+// the words, at most 4 per SM of a 152-SM GPU (one pair of atomics each).
+static inline unsigned word_blocks(const Geometry &g) {
+    return grid_for(((g.N >> 5) + 255ull) / 256ull, 608ull);
+}
+
 cudaError_t launch_measure_full(int dim, const uint8_t *spins, Geometry g, DevCtl *ctl,
                                 int set_chain, cudaStream_t s) {
     k_zero_full<<<1, 1, 0, s>>>(ctl);
-    const uint32_t rows = g.N / g.L;
-    const unsigned blocks = grid_for(rows, 8192ull);
-    const unsigned threads = g.L >= 256 ? 256 : 64;
-    if (dim == 2)
-        k_measure_full<2><<<blocks, threads, 0, s>>>(spins, g, ctl);
-    else
-        k_measure_full<3><<<blocks, threads, 0, s>>>(spins, g, ctl);
+    if (g.L % 32 == 0) {
+        if (dim == 2)
+            k_measure_words<2><<<word_blocks(g), 256, 0, s>>>(spins, g, ctl);
+        else
+            k_measure_words<3><<<word_blocks(g), 256, 0, s>>>(spins, g, ctl);
+    } else {
+        const uint32_t rows = g.N / g.L;
+        const unsigned blocks = grid_for(rows, 8192ull);
+        const unsigned threads = g.L >= 256 ? 256 : 64;
+        if (dim == 2)
+            k_measure_full<2><<<blocks, threads, 0, s>>>(spins, g, ctl);
+        else
+            k_measure_full<3><<<blocks, threads, 0, s>>>(spins, g, ctl);
+    }
     if (set_chain) k_full_to_chain<<<1, 1, 0, s>>>(ctl);
     return cudaGetLastError();
 }
@@ -229,6 +324,45 @@ __global__ void k_from_bits_measure(uint8_t *spins, const uint32_t *bits, Geomet
     }
 }
 
+// The bit-packed upload with 32 sites per thread (L a multiple of 32): one
+// word and its neighbour words in, 32 spin bytes out (two 16-byte stores),
+// E_bond and M published by the last block as in k_from_bits_measure.
+template <int DIM>
+__global__ void k_from_bits_words(uint8_t *spins, const uint32_t *bits, Geometry g,
+                                  DevCtl *ctl) {
+    const WordGeom wg = word_geom(g, DIM);
+    long long e = 0, m = 0;
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < wg.words;
+         w += gridDim.x * blockDim.x) {
+        uint32_t nxt, up, zup;
+        word_neighbours<DIM>(wg, w, nxt, up, zup);
+        const uint32_t b = __ldg(bits + w);
+        const uint32_t right = (b >> 1) | (__ldg(bits + nxt) << 31);
+        int bonds = word_bonds(b, right) + word_bonds(b, __ldg(bits + up));
+        if (DIM == 3) bonds += word_bonds(b, __ldg(bits + zup));
+        e += bonds;
+        m += 2 * __popc(b) - 32;
+        uint4 *dst = reinterpret_cast<uint4 *>(spins + 32ull * w);
+        dst[0] = make_uint4(nibble_to_bytes(b & 0xFu), nibble_to_bytes((b >> 4) & 0xFu),
+                            nibble_to_bytes((b >> 8) & 0xFu), nibble_to_bytes((b >> 12) & 0xFu));
+        dst[1] = make_uint4(nibble_to_bytes((b >> 16) & 0xFu), nibble_to_bytes((b >> 20) & 0xFu),
+                            nibble_to_bytes((b >> 24) & 0xFu), nibble_to_bytes(b >> 28));
+    }
+    e = block_sum(e);
+    m = block_sum(m);
+    if (threadIdx.x == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->full_E), (unsigned long long)e);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->full_M), (unsigned long long)m);
+        __threadfence();
+        if (atomicAdd(&ctl->up_blocks, 1u) == gridDim.x - 1) {
+            __threadfence();
+            ctl->E = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->full_E), 0ull);
+            ctl->M = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->full_M), 0ull);
+            ctl->up_blocks = 0;
+        }
+    }
+}
+
 // Bit-packed download: one warp ballot per 32 consecutive sites.
 __global__ void k_to_bits(uint32_t *bits, const uint8_t *spins, uint32_t N) {
     const uint32_t words = (N + 31u) / 32u;
@@ -243,6 +377,13 @@ __global__ void k_to_bits(uint32_t *bits, const uint8_t *spins, uint32_t N) {
 
 cudaError_t launch_from_bits_measure(int dim, uint8_t *spins, const uint32_t *bits, Geometry g,
                                      DevCtl *ctl, cudaStream_t s) {
+    if (g.L % 32 == 0) {
+        if (dim == 2)
+            k_from_bits_words<2><<<word_blocks(g), 256, 0, s>>>(spins, bits, g, ctl);
+        else
+            k_from_bits_words<3><<<word_blocks(g), 256, 0, s>>>(spins, bits, g, ctl);
+        return cudaGetLastError();
+    }
     const unsigned blocks = (unsigned)grid_for(g.N / g.L, 8192ull);
     const unsigned threads = g.L >= 256 ? 256 : 64;
     if (dim == 2)

@@ -231,6 +231,27 @@ def test_bit_packed_transfers(dim, L):
     lat.close()
 
 
+@pytest.mark.parametrize("dim,L", [(2, 32), (2, 96), (2, 1024), (3, 32), (3, 64), (2, 48),
+                                   (3, 24)])
+def test_word_parallel_measure_and_upload(dim, L):
+    """Lattices whose side is a multiple of 32 take the 32-sites-per-thread
+    recount and bit-packed upload (other sides the per-site ones): E_bond
+    and M equal the oracle's definitions on random and ordered lattices, and
+    the uploaded lattice reads back unchanged."""
+    torch, w = require_cuda()
+    rng = np.random.default_rng(1000 * dim + L)
+    for s in (rng.choice(np.array([-1, 1], np.int8), size=L ** dim),
+              np.ones(L ** dim, np.int8), -np.ones(L ** dim, np.int8)):
+        lat = w.WolffLattice(dim, L, 2.5 if dim == 2 else 4.8, seed=5)
+        lat.set_state_bits(w.pack_spins(s), 3)
+        ref = (oracle.energy_bond(dim, L, s), oracle.magnetisation(dim, L, s))
+        assert lat.measure()[:2] == ref
+        assert lat.measure_full() == ref
+        back, t = lat.get_state()
+        assert t == 3 and np.array_equal(back, s)
+        lat.close()
+
+
 @pytest.mark.parametrize("dim,L", [(2, 4096), (3, 256)])
 def test_full_size_state_transfer(dim, L):
     """The fused upload (int8 +-1 -> spin bytes, E_bond and M in the same

@@ -43,21 +43,24 @@ ALGO_BYTES_PER_FLIP = {2: 23.0, 3: 27.0}
 TC2 = 2.0 / math.log(1.0 + math.sqrt(2.0))
 # DRAM traffic of one timed k_team launch of the specified workloads, from the
 # committed ncu captures (profiles/k_team_2d_L4096_random_start.md and
-# profiles/k_team_3d_L256_random_start.md), valid only while the kernel sources
-# hash to the captured value.
+# profiles/k_team_3d_L256_random_start.md), valid only while the sources of
+# k_team hash to the captured value.
 TRAFFIC_CAPTURES = {
-    ("2d", 10000): {"src": "2773a496567b", "bytes_per_launch": 11246848 + 256},
-    ("3d", 10000): {"src": "2773a496567b", "bytes_per_launch": 24329728 + 34560},
+    ("2d", 10000): {"src": "44e40f8418e9", "bytes_per_launch": 11246848 + 256},
+    ("3d", 10000): {"src": "44e40f8418e9", "bytes_per_launch": 24329728 + 34560},
 }
 
 
+# the sources the cluster-schedule kernel k_team is built from
+TEAM_SOURCES = ("wolff_device.cuh", "wolff_internal.h", "wolff_team.cu")
+
+
 def kernel_source_hash():
-    import glob
     import hashlib
     h = hashlib.sha1()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1110_0899_gb300", "csrc", "*"))):
-        h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
+    for name in TEAM_SOURCES:
+        h.update(name.encode())
+        with open(os.path.join(ROOT, "paper_1110_0899_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
 

@@ -46,8 +46,8 @@ TC2 = 2.0 / math.log(1.0 + math.sqrt(2.0))
 # profiles/k_team_3d_L256_random_start.md), valid only while the sources of
 # k_team hash to the captured value.
 TRAFFIC_CAPTURES = {
-    ("2d", 10000): {"src": "44e40f8418e9", "bytes_per_launch": 11246848 + 256},
-    ("3d", 10000): {"src": "44e40f8418e9", "bytes_per_launch": 24329728 + 34560},
+    ("2d", 10000): {"src": "35704c4b61f6", "bytes_per_launch": 11246848 + 256},
+    ("3d", 10000): {"src": "35704c4b61f6", "bytes_per_launch": 24329728 + 34560},
 }
 
 

@@ -44,9 +44,8 @@ enum : unsigned int { kTeamLevels = 1, kTeamFinish = 2, kTeamExit = 3, kTeamWind
 // per CTA times the cluster size; update j lives in CTA j mod CS, slot
 // (j / CS) mod S.  Rounds of K levels of growth alternate with commits:
 //   - every finished update records the sites it flips in a map "lowest
-//     update index that flips this site", spread over the CTAs' shared
-//     memory (each site has an owner CTA, reached through distributed shared
-//     memory);
+//     update index that flips this site": the cluster-list array indexed by
+//     site, written with L2 atomics and read with L2 loads;
 //   - update j conflicts if an earlier finished update of the window flips
 //     one of its members or a neighbour across an open boundary bond (draw
 //     below the threshold): only those flips can change its cluster;
@@ -243,8 +242,7 @@ __device__ __forceinline__ bool set_contains(const uint32_t *set, uint32_t slots
 // lowest update it conflicts with, lowest update that flips any site it read,
 // and the correction of its boundary sum; the regrowth queue, each slot's seed
 // site, the slot offsets of the flattened member list and a few counters; and
-// per member three bit
-// masks over its 2 DIM bonds (bit s = bond to neighbour s):
+// per member three bit masks over its 2 DIM bonds (bit s = bond to neighbour s):
 //   amask: the neighbour was parallel to the seed spin when the growth read it
 //          (also revalidates a finished update after a change of the lattice
 //          made outside the window),

@@ -277,11 +277,12 @@ wolff_status wolff_set_local_thresholds(wolff_ctx *ctx, uint32_t t_up, uint32_t 
  * speculatively on the current lattice, one update per warp at a time, each
  * taking the next free update of a window of up to 2048 when done.  Rounds
  * of `levels` growth levels alternate with commits: the prefix of finished
- * updates that read no site flipped by an earlier one is applied in order,
- * and an uncommitted update that read a committed flip is grown again.  A
- * committed update is exactly the serial one (section 2's cluster depends
- * only on the spins it reads and on the counter-based bond draws), so results
- * do not depend on the setting.  enable: 0 = off, 1 = on with the default
+ * updates none of whose members, nor neighbours across open bonds, an
+ * earlier one flips is applied in order, each boundary sum corrected for the
+ * earlier flips of neighbours across closed bonds; an uncommitted update that
+ * read a committed flip is grown again.  A committed update is exactly the
+ * serial one (section 2's cluster depends only on those spins and on the
+ * counter-based bond draws), so results do not depend on the setting.  enable: 0 = off, 1 = on with the default
  * levels per round (24 in 2D, 28 in 3D), k >= 2 = on with k levels per round
  * (at most 64).  EINVAL if enable < 0. */
 wolff_status wolff_set_burst(wolff_ctx *ctx, int enable);

@@ -736,6 +736,10 @@ def main():
         "detail": {"mean_cluster": flips / len(records), "mean_levels": float(levels.mean()),
                    "max_levels": int(levels.max()), "ms_per_update": total_ms / len(records),
                    "steps_and_e2e_records_identical": bool(repeat_identical),
+                   # window mode commits updates in rounds, so the device time
+                   # is per step (U updates), not per update
+                   "step_ms_p50": float(np.percentile(step_ms, 50)),
+                   "step_ms_p99": float(np.percentile(step_ms, 99)),
                    "step_counters": {k: stats1[k] - stats0[k] for k in stats1}},
     }
     print(json.dumps(line), flush=True)

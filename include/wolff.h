@@ -340,27 +340,50 @@ wolff_status wolff_selftest_wait_timeout(wolff_ctx *ctx, uint64_t wait_ns, int *
  * wolff_step_static runs n_updates updates (t0 .. t0+n-1, the same Philox
  * streams and results as a context with this dim, L, J, T and seed) on a
  * caller-owned lattice, using no workspace and allocating nothing.  Its
- * scratch (control block and cluster list) is a file-scope __device__ array
- * of WOLFF_STATIC_MAX_SITES 32-bit entries plus 256 bytes (about 4 MiB),
- * which every GPU that loads the library holds until the process exits.
+ * scratch (a 1 KiB control block and a cluster list of
+ * WOLFF_STATIC_MAX_SITES 32-bit entries, 4 MiB + 1 KiB in all) is a
+ * file-scope __device__ array, which every GPU that loads the library holds
+ * until the process exits.
  *   d_spins    device int8 lattice of +-1 values (N = L^dim entries, site
- *              i = x + L*y (+ L*L*z)), 4-byte aligned, with room for
- *              N rounded up to a multiple of 4 bytes; updated in place.
- *              Entries other than +-1 are read as -1;
- *   d_records  nullable, n_updates wolff_record entries;
+ *              i = x + L*y (+ L*L*z)), 16-byte aligned, with room for
+ *              N rounded up to a multiple of 4 bytes; updated in place;
+ *   d_records  nullable, n_updates wolff_record entries, 8-byte aligned;
  *   stream     cudaStream_t (NULL = default stream); asynchronous.
- * Returns WOLFF_EINVAL for a bad shape/parameter, a misaligned lattice, or
- * L^dim > WOLFF_STATIC_MAX_SITES.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls share the one array and it keeps the last call's
- * contents (each call clears what must start at zero), so calls whose work
- * overlaps on the GPU -- on different streams, or from different threads --
- * race and must be serialised by the caller. */
+ * Returns, before touching the lattice, WOLFF_EINVAL for a bad
+ * shape/parameter, a misaligned lattice or record buffer, or
+ * L^dim > WOLFF_STATIC_MAX_SITES, and WOLFF_ECUDA when a query of the
+ * device fails.  WOLFF_ECUDA from a later launch still leaves the lattice
+ * converted back to +-1.
+ * Errors found on the device are latched in the static control block and
+ * read by wolff_step_static_status (below), not by this call's return
+ * value:
+ *   - an entry other than +-1 latches WOLFF_EINVAL; no update runs, no
+ *     record is written, and that entry comes back as -1;
+ *   - a bounded wait that ran out latches WOLFF_ETIMEOUT; the updates stop
+ *     at the next check (every 32 updates) and only the records of the
+ *     completed updates are written.
+ * Each call looks up the array's device address on the current device; the
+ * first call on a device also loads the library's device code, so make it
+ * before any stream capture.  All calls share the one array and it keeps
+ * the last call's contents (each call clears what must start at zero, its
+ * status included), so calls whose work overlaps on the GPU -- on different
+ * streams, or from different threads -- race and must be serialised by the
+ * caller. */
 #define WOLFF_STATIC_MAX_SITES (1u << 20)
 wolff_status wolff_step_static(int dim, int L, double J, double T, uint64_t seed,
                                uint64_t t0, uint64_t n_updates, void *d_spins,
                                void *d_records, void *stream);
+
+/* Synchronises `stream` (the one the last wolff_step_static call used) and
+ * reads what that call's work latched on the device: *device_status = 0 or
+ * a wolff_status (WOLFF_EINVAL, WOLFF_ETIMEOUT), *detail = where it was
+ * raised (for EINVAL, the index of a bad entry), *t_next = the index
+ * of the next update (t0 + the updates completed).  Outputs are nullable.
+ * The next wolff_step_static call clears these values, so read them before
+ * it.  Allocates nothing.  Returns WOLFF_ECUDA if the copy or the
+ * synchronisation fails, else WOLFF_OK. */
+wolff_status wolff_step_static_status(void *stream, int *device_status, uint32_t *detail,
+                                      uint64_t *t_next);
 
 /* ---- batched form: many lattices in one launch ----------------------------
  * A batch runs the next updates of several contexts in one kernel launch,

@@ -107,6 +107,7 @@ def load_library():
         "wolff_batch_run_timed": (i, [v, v, i, v, v, i, i, u64]),
         "wolff_batch_free": (i, [v]),
         "wolff_step_static": (i, [i, i, d, d, u64, u64, u64, v, v, v]),
+        "wolff_step_static_status": (i, [v, P(i), P(u32), P(u64)]),
         "wolff_bond_threshold": (u64, [d, d]),
         "wolff_philox": (i, [u32, u32, v, v, u64, v]),
         "wolff_selftest_wait_timeout": (i, [v, u64, P(i)]),

@@ -785,18 +785,23 @@ __global__ void __launch_bounds__(512, 1) k_persistent(StepParams p) {
         const uint32_t tlo = (uint32_t)t, thi = (uint32_t)(t >> 32);
         unsigned long long clk = 0;
         if (t0) {
-            // seed: one uncontended XOR flips its bit 0 and returns its spin
-            const uint32_t i0 = seed_site(p, t);
-            unsigned int *w = reinterpret_cast<unsigned int *>(p.spins) + (i0 >> 2);
-            const unsigned int sh0 = (i0 & 3u) * 8u;
-            const uint32_t s0 = (atomicXor(w, 1u << sh0) >> sh0) & 1u;
-            const uint32_t p0 = pack_index<DIM>(p.g, i0);
-            p.list[0] = p0;
-            sh.list[0] = p0;
-            sh.front[0][0] = p0;
-            sh.cnt[0] = sh.cnt[1] = sh.cnt[2] = 0;
-            sh.sig0bit = s0;
-            sh.flag = ((u & 31u) == 31u) ? ld_volatile_u32(&ctl->status) : 0u;
+            // a status latched before this launch (an invalid input lattice)
+            // or during it stops the chain before the next seed is claimed,
+            // so the lattice is left as the last completed update made it
+            sh.flag = (u == 0 || (u & 31u) == 31u) ? ld_volatile_u32(&ctl->status) : 0u;
+            if (sh.flag == 0u) {
+                // seed: one uncontended XOR flips its bit 0 and returns its spin
+                const uint32_t i0 = seed_site(p, t);
+                unsigned int *w = reinterpret_cast<unsigned int *>(p.spins) + (i0 >> 2);
+                const unsigned int sh0 = (i0 & 3u) * 8u;
+                const uint32_t s0 = (atomicXor(w, 1u << sh0) >> sh0) & 1u;
+                const uint32_t p0 = pack_index<DIM>(p.g, i0);
+                p.list[0] = p0;
+                sh.list[0] = p0;
+                sh.front[0][0] = p0;
+                sh.cnt[0] = sh.cnt[1] = sh.cnt[2] = 0;
+                sh.sig0bit = s0;
+            }
             clk = global_ns();
         }
         __syncthreads();

@@ -16,7 +16,7 @@
 // static scratch instead of a context's workspace.
 #include <cuda_runtime.h>
 
-#include <mutex>
+#include <stddef.h>
 
 #include "wolff.h"
 #include "wolff_internal.h"
@@ -28,29 +28,23 @@ namespace {
 // Control block, then the cluster list of up to WOLFF_STATIC_MAX_SITES entries.
 constexpr size_t kScratchBytes =
     sizeof(DevCtl) + (size_t)WOLFF_STATIC_MAX_SITES * sizeof(uint32_t);
+// the size the header states: 1 KiB of control block and 4 MiB of list
+static_assert(sizeof(DevCtl) == 1024, "the header states a 1 KiB control block");
+static_assert(kScratchBytes == (4u << 20) + 1024u, "the header states 4 MiB + 1 KiB");
 
 static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-void *g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device.  The symbol's
-// name in host code is only a host-side stand-in, so its device address is
-// looked up once per device, with that device current.
+// Device address of the scratch array on the current device.  In host code
+// the symbol's name is only a host-side stand-in, so the address is asked of
+// the runtime with the device current.  It is looked up on every call: the
+// lookup is cheap next to the launches, and a cached address would go stale
+// if the caller reset the device (the module, and the array with it, can
+// move when it is loaded again).
 cudaError_t scratch_for_current_device(void **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
-        void *ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_static_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = ptr;
-    }
-    *out = g_scratch_ptr[dev];
+    *out = ptr;
     return cudaSuccess;
 }
 
@@ -59,12 +53,17 @@ cudaError_t scratch_for_current_device(void **out) {
 extern "C" wolff_status wolff_step_static(int dim, int L, double J, double T, uint64_t seed,
                                           uint64_t t0, uint64_t n_updates, void *d_spins,
                                           void *d_records, void *stream) {
+    // ---- everything that can be rejected is checked before the lattice is
+    // touched, so a rejected call leaves the caller's buffer as it was
     const bool shape = (dim == 2 && L >= 2 && L <= 32767) || (dim == 3 && L >= 2 && L <= 1024);
     if (!shape || !(J >= 0.0) || !(T > 0.0) || !d_spins) return WOLFF_EINVAL;
     uint64_t n = 1;
     for (int d = 0; d < dim; ++d) n *= (uint64_t)L;
     if (n > WOLFF_STATIC_MAX_SITES) return WOLFF_EINVAL;
-    if (reinterpret_cast<uintptr_t>(d_spins) % 4u) return WOLFF_EINVAL;
+    // the 32-sites-per-thread recount reads the lattice in 16-byte vectors
+    if (reinterpret_cast<uintptr_t>(d_spins) % 16u) return WOLFF_EINVAL;
+    if (d_records && reinterpret_cast<uintptr_t>(d_records) % alignof(wolff_record))
+        return WOLFF_EINVAL;
 
     void *scratch = nullptr;
     if (scratch_for_current_device(&scratch) != cudaSuccess) return WOLFF_ECUDA;
@@ -73,6 +72,19 @@ extern "C" wolff_status wolff_step_static(int dim, int L, double J, double T, ui
     if (cudaGetDevice(&device) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
         return WOLFF_ECUDA;
+    const int threads = 256;
+    int blocks = 0;
+    if (n_updates) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel(dim), threads,
+                                                          0) != cudaSuccess)
+            return WOLFF_ECUDA;
+        blocks = (int)(n / 2048u);
+        if (blocks < 1) blocks = 1;
+        if (blocks > sms) blocks = sms;
+        if (blocks > per_sm * sms) blocks = per_sm * sms;
+        if (blocks < 1) return WOLFF_EUNSUPPORTED;
+    }
 
     StepParams p = {};   // fields this path does not use stay zero
     p.ctl = static_cast<DevCtl *>(scratch);
@@ -99,27 +111,36 @@ extern "C" wolff_status wolff_step_static(int dim, int L, double J, double T, ui
     // every call starts from a cleared control block: the array keeps the
     // previous call's contents
     cudaError_t e = launch_reset_ctl(p.ctl, t0, s);
-    if (e == cudaSuccess)
-        e = launch_from_pm1(p.spins, static_cast<const int8_t *>(d_spins), p.g.N, p.ctl, s);
-    if (e == cudaSuccess) e = launch_measure_full(dim, p.spins, p.g, p.ctl, 1, s);
+    if (e != cudaSuccess) return WOLFF_ECUDA;
+    // an entry other than +-1 becomes -1 and latches WOLFF_EINVAL, which the
+    // update kernel sees before its first update: it then runs none
+    e = launch_from_pm1(p.spins, static_cast<const int8_t *>(d_spins), p.g.N, p.ctl, s);
+    if (e != cudaSuccess) return WOLFF_ECUDA;
+    // from here on the lattice holds spin bytes: whatever fails, the
+    // conversion back to +-1 is still enqueued
+    e = launch_measure_full(dim, p.spins, p.g, p.ctl, 1, s);
     // the update expects every cluster-list slot to hold the empty marker
     if (e == cudaSuccess) e = cudaMemsetAsync(p.list, 0xFF, (size_t)p.g.N * sizeof(uint32_t), s);
     if (e == cudaSuccess && n_updates) {
-        const int threads = 256;
-        int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel(dim),
-                                                          threads, 0);
-        int blocks = (int)(p.g.N / 2048u);
-        if (blocks < 1) blocks = 1;
-        if (blocks > sms) blocks = sms;
-        if (e == cudaSuccess && blocks > per_sm * sms) blocks = per_sm * sms;
-        if (e == cudaSuccess && blocks < 1) return WOLFF_EUNSUPPORTED;
         void *args[] = {&p};
-        if (e == cudaSuccess)
-            e = cudaLaunchCooperativeKernel(persistent_kernel(dim), dim3(blocks), dim3(threads),
-                                            args, 0, s);
+        e = cudaLaunchCooperativeKernel(persistent_kernel(dim), dim3(blocks), dim3(threads), args,
+                                        0, s);
     }
-    if (e == cudaSuccess)
-        e = launch_to_pm1(static_cast<int8_t *>(d_spins), p.spins, p.g.N, s);
-    return e == cudaSuccess ? WOLFF_OK : WOLFF_ECUDA;
+    const cudaError_t back = launch_to_pm1(static_cast<int8_t *>(d_spins), p.spins, p.g.N, s);
+    return (e == cudaSuccess && back == cudaSuccess) ? WOLFF_OK : WOLFF_ECUDA;
+}
+
+extern "C" wolff_status wolff_step_static_status(void *stream, int *device_status,
+                                                 uint32_t *detail, uint64_t *t_next) {
+    void *scratch = nullptr;
+    if (scratch_for_current_device(&scratch) != cudaSuccess) return WOLFF_ECUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DevCtl h;
+    cudaError_t e = cudaMemcpyAsync(&h, scratch, sizeof(DevCtl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return WOLFF_ECUDA;
+    if (device_status) *device_status = (int)h.status;
+    if (detail) *detail = h.err_detail;
+    if (t_next) *t_next = h.t;
+    return WOLFF_OK;
 }

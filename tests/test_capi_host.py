@@ -119,3 +119,24 @@ def test_bit_packing_definition(lib):
         if N % 32:
             assert int(b[-1]) >> (N % 32) == 0
         assert np.array_equal(w.unpack_bits(b, N), s)
+
+
+def test_static_entry_checks_before_touching_the_device(lib):
+    """wolff_step_static rejects a lattice pointer that is not 16-byte aligned
+    (its recount reads 16-byte vectors), a misaligned record buffer, a bad
+    shape and an oversized lattice, all on the host: none of these pointers
+    is ever dereferenced, and no CUDA call is made."""
+    import paper_1110_0899_gb300 as w
+    tc = w.TC_2D
+    base = 1 << 20   # a stand-in address, never dereferenced
+    for off in (4, 8, 12, 1):
+        assert lib.wolff_step_static(2, 64, 1.0, tc, 1, 0, 1, ctypes.c_void_p(base + off),
+                                     None, None) == w.WOLFF_EINVAL, off
+    assert lib.wolff_step_static(2, 64, 1.0, tc, 1, 0, 1, ctypes.c_void_p(base),
+                                 ctypes.c_void_p(base + 4), None) == w.WOLFF_EINVAL
+    for dim, L in ((2, 1), (4, 8), (3, 1025), (2, 1025), (3, 102)):
+        assert lib.wolff_step_static(dim, L, 1.0, tc, 1, 0, 1, ctypes.c_void_p(base),
+                                     None, None) == w.WOLFF_EINVAL, (dim, L)
+    assert lib.wolff_step_static(2, 64, 1.0, 0.0, 1, 0, 1, ctypes.c_void_p(base),
+                                 None, None) == w.WOLFF_EINVAL
+    assert lib.wolff_step_static(2, 64, 1.0, tc, 1, 0, 1, None, None, None) == w.WOLFF_EINVAL

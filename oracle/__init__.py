@@ -47,6 +47,8 @@ def _load():
     lib.orc_cluster.argtypes = [i32, u32, u64, u64, u64, p, p, p, p]
     lib.orc_cluster.restype = u32
     lib.orc_run.argtypes = [i32, u32, u64, u64, u64, u64, p, p]
+    lib.orc_run_local.restype = ctypes.c_int
+    lib.orc_run_local.argtypes = [i32, u32, u64, u64, u64, u64, p, p, p]
     lib.orc_run.restype = i32
     lib.orc_enumerate.argtypes = [i32, u32, p]
     lib.orc_enumerate.restype = i32
@@ -84,6 +86,8 @@ def _load():
     lib.orc_xy_cluster.argtypes = [i32, u32, i32, f64, u64, u64, p, p, p, p, p]
     lib.orc_xy_cluster.restype = u32
     lib.orc_xy_run.argtypes = [i32, u32, i32, f64, u64, u64, u64, p, p]
+    lib.orc_xy_run_local.restype = ctypes.c_int
+    lib.orc_xy_run_local.argtypes = [i32, u32, i32, f64, u64, u64, u64, p, p]
     lib.orc_xy_run.restype = i32
     _lib = lib
     return lib
@@ -158,6 +162,23 @@ def run(dim, L, thr, seed, t0, n, s, records=True):
     rc = _load().orc_run(dim, L, thr, seed, t0, n, _ptr(s),
                          _ptr(rec) if rec is not None else None)
     if rc != 0:
+        raise MemoryError("oracle could not allocate its scratch arrays")
+    return rec
+
+
+def run_local(dim, L, thr, seed, t0, n, s, em=None):
+    """The updates of run() with every record, E_bond and M kept by a local
+    recount of the terms each flip changes (O(|C|) per update instead of
+    O(N)): the same records as run(), fast enough for whole runs of the
+    2^24-site lattices.  em: optional int64 array [E_bond, M] of s on entry
+    (else counted from the definitions), updated to the final lattice's."""
+    if s.dtype != np.int8 or not s.flags.c_contiguous:
+        raise ValueError("s must be a contiguous int8 array")
+    if em is not None and (em.dtype != np.int64 or em.size != 2):
+        raise ValueError("em must be an int64 array of two entries")
+    rec = np.zeros(int(n), dtype=RECORD_DTYPE)
+    if _load().orc_run_local(dim, L, thr, seed, t0, n, _ptr(s),
+                             _ptr(em) if em is not None else None, _ptr(rec)) != 0:
         raise MemoryError("oracle could not allocate its scratch arrays")
     return rec
 
@@ -364,5 +385,15 @@ def xy_run(dim, L, bits, kk, seed, t0, n, theta, records=True):
     rc = _load().orc_xy_run(dim, L, bits, kk, seed, t0, n, _ptr(theta),
                             _ptr(rec) if rec is not None else None)
     if rc != 0:
+        raise MemoryError("oracle could not allocate its scratch arrays (or bad angle bits)")
+    return rec
+
+
+def xy_run_local(dim, L, bits, kk, seed, t0, n, theta):
+    """The XY updates of xy_run() with every record kept by a local recount."""
+    if theta.dtype != np.uint16 or not theta.flags.c_contiguous:
+        raise ValueError("theta must be a contiguous uint16 array")
+    rec = np.zeros(int(n), dtype=XY_RECORD_DTYPE)
+    if _load().orc_xy_run_local(dim, L, bits, kk, seed, t0, n, _ptr(theta), _ptr(rec)) != 0:
         raise MemoryError("oracle could not allocate its scratch arrays (or bad angle bits)")
     return rec

@@ -251,6 +251,77 @@ int orc_run(int dim, uint32_t L, uint64_t thr, uint64_t seed, uint64_t t0,
     return 0;
 }
 
+/* ---- the update loop with the records kept by a local recount -----------
+ *
+ * The same updates as orc_run (same cluster, same flip), but E_bond and M are
+ * counted from their definitions only once, before the first update; after
+ * that each record follows from the previous one by recounting, before and
+ * after the flip, only the terms the flip can change.  E_bond is a sum over
+ * bonds, and a bond's term s_a s_b changes only when one of its ends is
+ * flipped, so every bond that does not touch the cluster keeps its term.
+ * orc_touching_bonds sums s_a s_b over the 2D bonds at every member i -- its
+ * forward bonds (i, nb(i,d,+1)) and the bonds (nb(i,d,-1), i) that end at i
+ * -- so a bond with both ends in the cluster is counted twice, before and
+ * after alike, and its term (both ends flipped) does not change; a bond with
+ * one end in the cluster is counted once.  Hence
+ *     E_after = E_before + touching(after) - touching(before),
+ *     M_after = M_before + sum over members of (s_after - s_before).
+ * This costs O(|C|) per update instead of O(N), so whole runs of the
+ * 2^24-site lattices can be replayed record by record. */
+
+static int64_t orc_touching_bonds(int dim, uint32_t L, const int8_t *s,
+                                  const uint32_t *list, uint32_t c)
+{
+    int64_t sum = 0;
+    for (uint32_t k = 0; k < c; ++k) {
+        uint32_t i = list[k];
+        for (int d = 0; d < dim; ++d) {
+            sum += (int64_t)s[i] * (int64_t)s[orc_neighbour(dim, L, i, d, +1)];
+            sum += (int64_t)s[orc_neighbour(dim, L, i, d, -1)] * (int64_t)s[i];
+        }
+    }
+    return sum;
+}
+
+/* em (nullable): on entry E_bond and M of s, which the caller already has
+ * (else they are counted here from their definitions); on return those of
+ * the final lattice. */
+int orc_run_local(int dim, uint32_t L, uint64_t thr, uint64_t seed, uint64_t t0,
+                  uint64_t n, int8_t *s, int64_t *em, orc_record *rec)
+{
+    uint32_t sites = orc_sites(dim, L);
+    uint8_t *member = (uint8_t *)calloc(sites, 1);
+    uint32_t *list = (uint32_t *)malloc((size_t)sites * sizeof(uint32_t));
+    if (!member || !list) { free(member); free(list); return -1; }
+    int64_t e = em ? em[0] : orc_energy_bond(dim, L, s);
+    int64_t m = em ? em[1] : orc_magnetisation(dim, L, s);
+    for (uint64_t u = 0; u < n; ++u) {
+        uint64_t t = t0 + u;
+        uint32_t levels = 0;
+        uint32_t c = orc_cluster(dim, L, thr, seed, t, s, member, list, &levels);
+        int64_t before = orc_touching_bonds(dim, L, s, list, c);
+        int64_t m_before = 0, m_after = 0;
+        for (uint32_t k = 0; k < c; ++k) m_before += s[list[k]];
+        for (uint32_t k = 0; k < c; ++k) {   /* step (iii): flip the members */
+            s[list[k]] = (int8_t)-s[list[k]];
+            member[list[k]] = 0;
+        }
+        for (uint32_t k = 0; k < c; ++k) m_after += s[list[k]];
+        e += orc_touching_bonds(dim, L, s, list, c) - before;
+        m += m_after - m_before;
+        if (rec) {
+            rec[u].C = c;
+            rec[u].levels = levels;
+            rec[u].E_bond = e;
+            rec[u].M = m;
+        }
+    }
+    if (em) { em[0] = e; em[1] = m; }
+    free(member);
+    free(list);
+    return 0;
+}
+
 /* ---- exact enumeration of all 2^N states --------------------------------
  *
  * Fills hist[(E_bond + D*N) * (2N+1) + (M + N)] with the number of
@@ -626,6 +697,76 @@ int orc_xy_run(int dim, uint32_t L, int bits, double kk, uint64_t seed, uint64_t
         if (rec) {
             int64_t obs[3];
             orc_xy_observables(dim, L, theta, obs);
+            rec[u].C = k;
+            rec[u].levels = levels;
+            rec[u].E = obs[0];
+            rec[u].Mx = obs[1];
+            rec[u].My = obs[2];
+        }
+    }
+    free(member);
+    free(list);
+    return 0;
+}
+
+/* XY updates as orc_xy_run, with the records kept by a local recount (the
+ * argument of orc_run_local): E, Mx and My are counted from their definitions
+ * before the first update; after that only the terms of the bonds and sites
+ * a reflection changes are recounted, before and after it.  Each bond
+ * touching a member is visited from each of its member ends, in the
+ * orientation of the definition (the forward bond (i, nb(i,d,+1)) as
+ * I(theta_i - theta_nb), the bond ending at i as I(theta_prev - theta_i)).
+ * A bond inside the cluster is visited twice, before and after alike, and
+ * keeps its term: the reflection theta -> c - theta maps theta_a - theta_b to
+ * theta_b - theta_a, and I is even (the table is extended by symmetry).  A
+ * bond with one end in the cluster is visited once. */
+static int64_t orc_xy_touching(int dim, uint32_t L, const uint16_t *theta, const uint32_t *list,
+                               uint32_t c)
+{
+    int64_t sum = 0;
+    for (uint32_t k = 0; k < c; ++k) {
+        uint32_t i = list[k];
+        for (int d = 0; d < dim; ++d) {
+            sum += orc_xy_cos_at((uint32_t)theta[i] - theta[orc_neighbour(dim, L, i, d, +1)]);
+            sum += orc_xy_cos_at((uint32_t)theta[orc_neighbour(dim, L, i, d, -1)] - theta[i]);
+        }
+    }
+    return sum;
+}
+
+int orc_xy_run_local(int dim, uint32_t L, int bits, double kk, uint64_t seed, uint64_t t0,
+                     uint64_t n, uint16_t *theta, orc_xy_record *rec)
+{
+    uint32_t sites = orc_sites(dim, L);
+    if (bits < 1 || bits > 15) return -1;
+    uint8_t *member = (uint8_t *)calloc(sites, 1);
+    uint32_t *list = (uint32_t *)malloc((size_t)sites * sizeof(uint32_t));
+    if (!member || !list) { free(member); free(list); return -1; }
+    int64_t obs[3];
+    orc_xy_observables(dim, L, theta, obs);
+    for (uint64_t u = 0; u < n; ++u) {
+        uint32_t levels = 0, phi = 0;
+        uint32_t k = orc_xy_cluster(dim, L, bits, kk, seed, t0 + u, theta, member, list, &levels,
+                                    &phi);
+        int64_t e_before = orc_xy_touching(dim, L, theta, list, k);
+        int64_t mx_before = 0, my_before = 0, mx_after = 0, my_after = 0;
+        for (uint32_t m = 0; m < k; ++m) {
+            mx_before += orc_xy_cos_at(theta[list[m]]);
+            my_before += orc_xy_cos_at((uint32_t)theta[list[m]] + 65536u - 16384u);
+        }
+        for (uint32_t m = 0; m < k; ++m) {
+            uint32_t i = list[m];
+            theta[i] = (uint16_t)((32768u + 2u * phi - theta[i]) & 0xFFFFu);
+            member[i] = 0;
+        }
+        for (uint32_t m = 0; m < k; ++m) {
+            mx_after += orc_xy_cos_at(theta[list[m]]);
+            my_after += orc_xy_cos_at((uint32_t)theta[list[m]] + 65536u - 16384u);
+        }
+        obs[0] += orc_xy_touching(dim, L, theta, list, k) - e_before;
+        obs[1] += mx_after - mx_before;
+        obs[2] += my_after - my_before;
+        if (rec) {
             rec[u].C = k;
             rec[u].levels = levels;
             rec[u].E = obs[0];

@@ -435,37 +435,38 @@ def check_run_window(w, dim, L, T, n, levels, cs, threads, seed, ref, s_ref):
     assert st["burst_updates"] > n // 4, (tag, st)
 
 
-@pytest.mark.parametrize("dim,L,T,seed,equil,sample", [(2, 4096, TC2, 2, 2000, 40),
-                                                      (3, 256, 4.5115, 3, 2000, 8)])
-def test_full_size_in_bench_configuration(dim, L, T, seed, equil, sample):
+@pytest.mark.parametrize("dim,L,T,seed", [(2, 4096, TC2, 2), (3, 256, 4.5115, 3)])
+def test_full_size_every_record_in_bench_configuration(dim, L, T, seed):
     """The workloads bench.py times, at full size and in its launch
     configuration (default schedule: one 16-CTA cluster, 512 threads, window
-    mode): after the specified equilibration the GPU runs one bench step, the
-    10^4 measured updates in one launch.  The oracle replays the first
-    `sample` updates from the GPU's snapshot and must match them bit for bit;
-    all 10^4 records must obey the update's invariants; the incremental E and
-    M must equal a full recount of the final lattice."""
+    mode): the specified equilibration in two launches of 1000 unrecorded
+    updates, then the bench's step -- the equilibrated lattice restored
+    through the bit-packed upload and the 10^4 measured updates in one
+    launch.  The lattice after equilibration, every one of the 10^4 records
+    (|C|, levels, E_bond, M) and the final lattice must equal the oracle's,
+    and the incremental E and M a full recount."""
     torch, w = require_cuda()
+    thr = oracle.bond_threshold(1.0, T)
     lat = w.WolffLattice(dim, L, T, seed=seed)
-    lat.step(equil, records=False)
+    for _ in range(2):
+        lat.step(1000, records=False)
     snap, t0 = lat.get_state()
-    assert t0 == equil
+    assert t0 == 2000
+    lat.set_state_bits(w.pack_spins(snap), t0)
     rec = lat.step(10000)
-    ref, _ = oracle_trajectory(dim, L, T, seed, sample, t0=t0, s=snap)
-    assert_records_equal(rec[:sample], ref, "full size %dD L=%d" % (dim, L))
-    N = L ** dim
-    E_prev, M_prev = oracle.energy_bond(dim, L, snap), oracle.magnetisation(dim, L, snap)
-    for r in rec:
-        C = int(r["C"])
-        assert 1 <= C <= N and r["levels"] >= 1
-        assert abs(int(r["M"]) - M_prev) == 2 * C
-        assert (int(r["E"]) - E_prev) % 2 == 0 and abs(int(r["E"])) <= dim * N
-        E_prev, M_prev = int(r["E"]), int(r["M"])
-    E, M, C = lat.measure()
-    assert (E, M) == lat.measure_full() == (int(rec["E"][-1]), int(rec["M"][-1]))
+    end, t1 = lat.get_state()
+    E, M, _ = lat.measure()
+    full = lat.measure_full()
     st = lat.stats()
-    assert st["burst_updates"] > 0   # the bench's burst path is the one exercised
     lat.close()
+    s = oracle.init_lattice(dim, L, seed)
+    oracle.run(dim, L, thr, seed, 0, 2000, s, records=False)
+    assert np.array_equal(s, snap), "lattice after the equilibration"
+    ref = oracle.run_local(dim, L, thr, seed, 2000, 10000, s)
+    assert_records_equal(rec, ref, "full size %dD L=%d, all 10^4 records" % (dim, L))
+    assert t1 == 12000 and np.array_equal(end, s)
+    assert (E, M) == full == (int(ref["E"][-1]), int(ref["M"][-1]))
+    assert st["burst_updates"] > 0   # the bench's window path is the one exercised
 
 
 @pytest.mark.parametrize("dim,L,T,seed", [(2, 4096, TC2, 2), (3, 256, 4.5115, 3)])
@@ -473,10 +474,10 @@ def test_whole_trajectory_in_segments(dim, L, T, seed):
     """The full specified runs (2000 equilibration + 10^4 measured updates, in
     the benchmark's launch configuration): the GPU snapshots its lattice every
     500 updates; the oracle replays every segment from the previous snapshot
-    and must reach the next one bit for bit (any wrong cluster anywhere in
-    the segment would change it); E_bond and M at every snapshot equal the
-    definitions; every record of the 10^4 measured updates obeys
-    |dM| = 2|C| and E changes by an even amount.  The benchmark's own step,
+    and must reach the next one bit for bit, every record of the 10^4
+    measured updates equal to its own; E_bond and M at every snapshot equal
+    the definitions; every record obeys |dM| = 2|C| and E changes by an even
+    amount.  The benchmark's own step,
     the 10^4 measured updates in one launch from the equilibrated lattice,
     must then give the same records and reach the oracle-checked end."""
     torch, w = require_cuda()
@@ -491,11 +492,13 @@ def test_whole_trajectory_in_segments(dim, L, T, seed):
         snaps.append(lat.get_state())
     E, M, _ = lat.measure()
     lat.close()
-    for (s_a, t_a), (s_b, t_b) in zip(snaps, snaps[1:]):
+    for k, ((s_a, t_a), (s_b, t_b)) in enumerate(zip(snaps, snaps[1:])):
         assert t_b == t_a + 500
         s = np.array(s_a, dtype=np.int8, copy=True)
-        oracle.run(dim, L, thr, seed, t_a, 500, s, records=False)
+        seg = oracle.run_local(dim, L, thr, seed, t_a, 500, s)
         assert np.array_equal(s, s_b), "segment starting at update %d" % t_a
+        if k >= 4:
+            assert_records_equal(recs[k - 4], seg, "segment starting at update %d" % t_a)
     assert (E, M) == (oracle.energy_bond(dim, L, snaps[-1][0]),
                       oracle.magnetisation(dim, L, snaps[-1][0]))
     rec = np.concatenate(recs)

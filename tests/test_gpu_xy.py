@@ -115,19 +115,42 @@ def test_ising_entry_points_refuse_xy():
     lat.close()
 
 
-def test_full_size_sampled():
-    """2D L=1024 near the BKT temperature from an ordered start: after 300
-    updates the oracle replays the next 5 from the GPU's snapshot."""
+@pytest.mark.parametrize("dim,L,T,seed", [(2, 1024, 0.89, 6), (3, 128, 2.2, 7)])
+def test_full_size_bench_step_every_record(dim, L, T, seed):
+    """The bench's XY workloads at full size (2D L=1024 near the BKT
+    temperature, 3D L=128 near its transition; ordered start, 200
+    equilibration updates): the bench's step of 1000 updates in one launch.
+    The same 1000 updates also run as ten launches of 100 with a snapshot
+    after each; the oracle replays every segment from its snapshot (one host
+    thread per segment; the oracle's calls release the interpreter lock), and
+    every record and every snapshot must match bit for bit.  The one-launch
+    records must equal the segmented ones."""
+    from concurrent.futures import ThreadPoolExecutor
     torch, w = require_cuda()
-    dim, L, T, seed = 2, 1024, 0.89, 21
+    N = L ** dim
     lat = w.WolffXY(dim, L, T, seed=seed)
-    lat.set_state(np.zeros(L * L, np.uint16), 0)
-    lat.step(300, records=False)
-    snap, t0 = lat.get_state()
-    rec = lat.step(5)
-    ref, th_ref = oracle_xy(dim, L, 15, T, seed, 5, t0=t0, theta=snap)
-    assert_xy_equal(rec, ref, "xy full size")
-    assert np.array_equal(lat.get_state()[0], th_ref)
+    lat.set_state(np.zeros(N, np.uint16), 0)
+    lat.step(200, records=False)
+    start, t0 = lat.get_state()
+    one = lat.step(1000)
+    lat.set_state(start, t0)
+    snaps, segs = [(start, t0)], []
+    for _ in range(10):
+        segs.append(lat.step(100))
+        snaps.append(lat.get_state())
     assert lat.measure()[:3] == lat.measure_full()
-    assert rec["C"].mean() > 1000
     lat.close()
+    assert np.array_equal(np.concatenate(segs), one)
+    kk = oracle.xy_coupling(1.0, T)
+    oracle.xy_cos(0)   # the oracle's cosine table is built once, before the threads
+
+    def replay(k):
+        th = np.array(snaps[k][0], np.uint16)
+        rec = oracle.xy_run_local(dim, L, 15, kk, seed, snaps[k][1], 100, th)
+        return rec, th
+    with ThreadPoolExecutor(max_workers=10) as ex:
+        out = list(ex.map(replay, range(10)))
+    for k, (rec, th) in enumerate(out):
+        assert_xy_equal(segs[k], rec, "xy full size %dD segment %d" % (dim, k))
+        assert np.array_equal(th, snaps[k + 1][0]), k
+    assert one["C"].mean() > 1000

@@ -1,13 +1,21 @@
 """Benchmark: flipped spins per second of the Wolff single-cluster update.
 
-Default workload (N=1): 2D square lattice L = 4096 (16.8M spins), periodic,
-J = 1, T = T_c = 2/ln(1+sqrt 2), int8 spins, Philox random start from seed 2,
-equilibrated for 2000 updates (untimed); every step then runs the 10^4
-measured updates (t = 2000 .. 11999) in one launch (the plain form), records
-written every update (the "+ measurement" form of the paper's Tables 1-2).
-Before each step the equilibrated lattice is restored (untimed), so every
-step repeats the same chain and must give the same records.  --workload 3d
-runs the simple-cubic L = 256 lattice at T = 4.5115, seed 3.
+Default run (N=1), one JSON line:
+  - headline: 2D square lattice L = 4096 (16.8M spins), periodic, J = 1,
+    T = T_c = 2/ln(1+sqrt 2), int8 spins, Philox random start from seed 2,
+    equilibrated for 2000 updates (untimed); every step then runs the 10^4
+    measured updates (t = 2000 .. 11999) in one launch (the plain form),
+    records written every update (the "+ measurement" form of the paper's
+    Tables 1-2).  Before each step the equilibrated lattice is restored
+    (untimed), so every step repeats the same chain and must give the same
+    records;
+  - "3d": the same for the simple-cubic L = 256 lattice at T = 4.5115, seed 3;
+  - "batched": 512 2D replicas (L in {64..1024}, T in [2.0, 2.6], seeds
+    1000+i), 10^4 updates each through the autotuned batched plan, against
+    the same replicas one lattice per launch, records compared;
+  - "served": the 200-request Poisson trace through the continuous-batching
+    server for a bounded window, latency percentiles over every request
+    (unfinished ones censored at the window's end).
 
 value = sum of cluster sizes over the timed updates / device time of the
 timed steps (CUDA events on the lattice's stream, an L2 flush of 256 MB
@@ -15,8 +23,8 @@ between steps, outside the events).  With torchrun (N > 1) every rank runs its
 own independent lattice (seed + rank): replicas only, no collective on the
 data path; value = all ranks' flips / the slowest rank's time.
 
---impl reference times the CPU oracle (single-threaded C) on the host cores on
-a bounded sample of the same workload.
+--impl reference times the CPU oracle (single-threaded C) on the host cores:
+each step is the same 10^4 measured updates with their records.
 """
 import argparse
 import ctypes
@@ -41,10 +49,12 @@ UNIT = "flipped spins/s"
 ALGO_BYTES_PER_FLIP = {2: 23.0, 3: 27.0}
 
 TC2 = 2.0 / math.log(1.0 + math.sqrt(2.0))
-# DRAM traffic of one timed k_team launch of the specified workloads, from the
+# Counters of one timed k_team launch of the specified workloads from the
 # committed ncu captures (profiles/k_team_2d_L4096_random_start.md and
 # profiles/k_team_3d_L256_random_start.md), valid only while the sources of
-# k_team hash to the captured value.
+# k_team hash to the captured value: DRAM bytes (dram__bytes_read.sum +
+# dram__bytes_write.sum), L2 bytes (lts__t_bytes.sum) and the fmaheavy pipe
+# (IMAD) activity.
 TRAFFIC_CAPTURES = {
     ("2d", 10000): {"src": "35704c4b61f6", "bytes_per_launch": 11246848 + 256},
     ("3d", 10000): {"src": "35704c4b61f6", "bytes_per_launch": 24329728 + 34560},
@@ -107,15 +117,20 @@ def parse():
     ap.add_argument("--t-up", type=int, default=None,
                     help="leader hands wave fronts above this size to all CTAs")
     ap.add_argument("--t-down", type=int, default=None)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0,
-                    help="bound of the oracle sample timed beside the GPU")
+    ap.add_argument("--cpu-seconds", type=float, default=5.0,
+                    help="bound of the oracle's full-recount sample timed beside the GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=120.0)
+    ap.add_argument("--no-3d", action="store_true",
+                    help="skip the 3D L=256 object in the default line")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-vs-plain comparison in the default line")
+    ap.add_argument("--batched-updates", type=int, default=10000,
+                    help="updates per replica of the batched comparison")
     ap.add_argument("--no-served", action="store_true",
                     help="skip the serving run in the default line")
+    ap.add_argument("--no-l2-probe", action="store_true")
     ap.add_argument("--embed-serve-seconds", type=float, default=30.0)
     return ap.parse_args()
 
@@ -126,6 +141,21 @@ def measured_peaks():
             return json.load(f), "measured"
     except OSError:
         return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def cpu_description():
+    """The host CPU: model name (lscpu) and the cores the OS reports."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model"):
+                model = ln.split(":", 1)[1].strip()
+                if ln.startswith("Model name"):
+                    break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count()}
 
 
 class ClockSampler:
@@ -200,79 +230,171 @@ def dist_setup(args):
     return world, rank, local
 
 
-def run_reference(args):
-    """CPU oracle on the host cores, bounded sample of the same workload."""
-    world, rank, _ = dist_setup(args)
-    if rank != 0:
-        return
+def reference_step_times(wl, steps, warmup):
+    """The oracle on the workload's measured run: the lattice after its own
+    equilibration (untimed), then every step replays the 10^4 measured
+    updates with their records (the local-recount form, the records the GPU
+    writes) from a restored copy; E_bond and M of the start are counted once,
+    untimed, as the GPU's restore does."""
     import numpy as np
 
     import oracle
-    wl = WORKLOADS[args.workload]
-    dim, L, T, seed = wl["dim"], wl["L"], wl["T"], wl["seed"]
-    q, ordered = wl.get("q"), wl["start"] == "ordered"
-    if wl.get("model") == "xy":
-        kk = oracle.xy_coupling(1.0, T)
-        s = oracle.xy_init(dim, L, oracle.XY_ANGLE_BITS, seed)
-        if ordered:
-            s[:] = 0
-
-        def run(t, n, records=True):
-            return oracle.xy_run(dim, L, oracle.XY_ANGLE_BITS, kk, seed, t, n, s, records)
-    elif q:
-        thr = oracle.potts_threshold(1.0, T)
-        s = oracle.potts_init(dim, L, q, seed)
-        if ordered:
-            s[:] = 0
-
-        def run(t, n, records=True):
-            return oracle.potts_run(dim, L, q, thr, seed, t, n, s, records)
-    else:
-        thr = oracle.bond_threshold(1.0, T)
-        s = oracle.init_lattice(dim, L, seed)
-        if ordered:
-            s[:] = 1
-
-        def run(t, n, records=True):
-            return oracle.run(dim, L, thr, seed, t, n, s, records)
-    # the configuration's equilibration, unrecorded (the oracle skips its full
-    # recount when no record is asked for)
-    equil = wl["equil"] if args.equil is None else args.equil
-    run(0, equil, records=False)
-    t = equil
-    per_step = 4
+    dim, L, T, seed, equil = wl["dim"], wl["L"], wl["T"], wl["seed"], wl["equil"]
+    U = wl["updates"]
+    thr = oracle.bond_threshold(1.0, T)
+    s0 = oracle.init_lattice(dim, L, seed)
+    oracle.run(dim, L, thr, seed, 0, equil, s0, records=False)
+    em0 = np.array([oracle.energy_bond(dim, L, s0), oracle.magnetisation(dim, L, s0)], np.int64)
     times, flips = [], []
-    for k in range(args.warmup + args.steps):
+    for k in range(warmup + steps):
+        s, em = s0.copy(), em0.copy()
         t0 = time.perf_counter()
-        rec = run(t, per_step)
+        rec = oracle.run_local(dim, L, thr, seed, equil, U, s, em)
         dt = time.perf_counter() - t0
-        t += per_step
-        if k >= args.warmup:
+        if k >= warmup:
             times.append(dt)
             flips.append(int(rec["C"].astype(np.int64).sum()))
-    value = sum(flips) / sum(times)
-    ms = 1000.0 * sum(times) / len(times)
+    return times, flips
+
+
+def run_reference(args):
+    """CPU oracle on the host cores, the same workload as the GPU arm."""
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    if args.workload not in ("2d", "3d"):
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "the reference arm times the specified 2d and 3d workloads"}))
+        return
+
+    def line_for(name):
+        wl = WORKLOADS[name]
+        times, flips = reference_step_times(wl, args.steps, args.warmup)
+        value = sum(flips) / sum(times)
+        cpu = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d steps, each the %d measured updates (t = %d .. %d) with records, "
+                         "from the oracle's own equilibrated lattice"
+                         % (args.steps, wl["updates"], wl["equil"],
+                            wl["equil"] + wl["updates"] - 1)}
+        cpu.update(cpu_description())
+        return {
+            "value": value, "ms_per_step": 1000.0 * sum(times) / len(times),
+            "config": {"workload": "%dD L=%d T=%.6g seed %d, oracle equilibrated %d updates, "
+                                   "per step the %d measured updates with records"
+                                   % (wl["dim"], wl["L"], wl["T"], wl["seed"], wl["equil"],
+                                      wl["updates"]),
+                       "dim": wl["dim"], "L": wl["L"], "T": wl["T"], "seed": wl["seed"]},
+            "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+        }
+    main_part = line_for(args.workload)
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
-        "data": "synthetic",
-        "config": {"workload": "%dD L=%d T=%.6g seed %d, oracle equilibrated %d updates, "
-                               "steps of %d recorded updates" % (dim, L, T, seed, equil, per_step),
-                   "dim": dim, "L": L, "T": T, "seed": seed},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "%d steps x %d updates after %d untimed updates"
-                                   % (args.steps, per_step, equil)},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "impl": "reference", "metric": METRIC, "value": main_part["value"], "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": main_part["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+        "config": main_part["config"], "cpu_baseline": main_part["cpu_baseline"],
+        "e2e": main_part["e2e"],
     }
+    if args.workload == "2d" and not args.no_3d:
+        line["3d"] = line_for("3d")
     print(json.dumps(line), flush=True)
+
+
+def l2_probe(sizes_mb=(16, 32, 64), passes=200):
+    """L2 bandwidth, measured with the library's probe kernel: a buffer that
+    fits in L2 streamed `passes` times in one launch (16-byte loads that skip
+    L1), CUDA events around the launch after a warm-up launch; the best of
+    three per size.  Returns GB/s figures."""
+    import torch
+
+    import paper_1110_0899_gb300 as w
+    out = {"read_gbs_by_mb": {}, "rmw_gbs_by_mb": {}}
+    sink = torch.zeros(4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for mode, key in ((0, "read_gbs_by_mb"), (1, "rmw_gbs_by_mb")):
+        for mb in sizes_mb:
+            buf = torch.zeros(mb << 20, dtype=torch.uint8, device="cuda")
+            w.wolff_l2_probe(buf, 2, mode, sink, stream)
+            best = None
+            for _ in range(3):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                w.wolff_l2_probe(buf, passes, mode, sink, stream)
+                b.record(stream)
+                b.synchronize()
+                ms = a.elapsed_time(b)
+                gbs = (2 if mode else 1) * passes * buf.numel() / (ms / 1000.0) / 1e9
+                best = gbs if best is None else max(best, gbs)
+            out[key][str(mb)] = best
+            del buf
+    out["read_gbs"] = max(out["read_gbs_by_mb"].values())
+    out["rmw_gbs"] = max(out["rmw_gbs_by_mb"].values())
+    out["how"] = ("library L2 probe: %s MB buffers streamed %d times per launch by a "
+                  "full-occupancy grid, 16-byte ld.global.cg, best of 3 launches after a warm-up"
+                  % ("/".join(str(m) for m in sizes_mb), passes))
+    return out
+
+
+def ising_cpu_baseline(wl, gpu_records, full_seconds):
+    """The oracle (single-threaded C) on the workload, in the paper's two
+    columns (section 5, Tables 1-2): "update" -- the 10^4 measured updates
+    alone, no observables (the whole run, repeated for at least a second) --
+    and "+ measurement" -- E_bond and M recounted from their definitions
+    after every update, as the paper's CPU code does (a bounded sample of
+    the same run).  Between them: the same updates with the records the GPU
+    writes, kept by the oracle's local recount.  The oracle starts from its
+    own equilibrated lattice; its records of the measured run are compared
+    with the GPU's."""
+    import numpy as np
+
+    import oracle
+    dim, L, T, seed, equil, U = wl["dim"], wl["L"], wl["T"], wl["seed"], wl["equil"], wl["updates"]
+    thr = oracle.bond_threshold(1.0, T)
+    s0 = oracle.init_lattice(dim, L, seed)
+    oracle.run(dim, L, thr, seed, 0, equil, s0, records=False)
+    em0 = np.array([oracle.energy_bond(dim, L, s0), oracle.magnetisation(dim, L, s0)], np.int64)
+    s, em = s0.copy(), em0.copy()
+    t0 = time.perf_counter()
+    ref = oracle.run_local(dim, L, thr, seed, equil, U, s, em)
+    t_rec = time.perf_counter() - t0
+    flips = int(ref["C"].astype(np.int64).sum())
+    reps, t_upd = 0, 0.0
+    while reps < 3 or t_upd < 1.0:
+        s = s0.copy()
+        t0 = time.perf_counter()
+        oracle.run(dim, L, thr, seed, equil, U, s, records=False)
+        t_upd += time.perf_counter() - t0
+        reps += 1
+    s, n, f_full, t_full = s0.copy(), 0, 0, 0.0
+    while t_full < full_seconds and n < U:
+        t0 = time.perf_counter()
+        r = oracle.run(dim, L, thr, seed, equil + n, 1, s)
+        t_full += time.perf_counter() - t0
+        f_full += int(r["C"][0])
+        n += 1
+    upd = reps * flips / t_upd
+    out = {"value": upd, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "update only: the whole measured run (%d updates, t = %d .. %d) from the "
+                     "oracle's own equilibrated lattice, %d times, %.2f s of one core"
+                     % (U, equil, equil + U - 1, reps, t_upd),
+           "update_only": upd,
+           "update_and_records": flips / t_rec,
+           "update_and_full_recount": f_full / t_full if t_full > 0 else None,
+           "full_recount_sample": "%d updates from t = %d, %.1f s of one core" % (n, equil, t_full),
+           "records_equal_gpu": (bool(np.array_equal(gpu_records, ref))
+                                 if gpu_records is not None else None)}
+    out.update(cpu_description())
+    return out
 
 
 def run_batched(args, n_replicas=512, updates=None, embed=False):
     """512 independent 2D replicas (L in {64..1024}, T in [2.0, 2.6], seeds
     1000+i) through the autotuned batched plan, against the same replicas run
-    one lattice per launch.  Both arms run the same updates from the same
-    random starts, so their records must agree bit for bit."""
+    one lattice per launch with the library's default settings.  Both arms
+    run the same updates from the same random starts, so their records must
+    agree bit for bit."""
     import numpy as np
     import torch
 
@@ -281,7 +403,9 @@ def run_batched(args, n_replicas=512, updates=None, embed=False):
     torch.cuda.set_device(0)
     U = updates or args.updates_per_step or 1000
     specs = workloads.batched_replicas(n_replicas)
+    t_tune = time.perf_counter()
     plan, table = batched.autotune(specs, probe_updates=max(10, U // 4))
+    t_tune = time.perf_counter() - t_tune
     lat_b = [w.WolffLattice(s["dim"], s["L"], s["T"], seed=s["seed"]) for s in specs]
     runner = batched.BatchedRunner(lat_b, plan)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -301,10 +425,10 @@ def run_batched(args, n_replicas=512, updates=None, embed=False):
     t_b = sum(a.elapsed_time(b) for a, b in ev) / 1000.0
     flips_b = sum(int(r["C"].astype(np.int64).sum()) for step in recs_b for r in step)
     runner.close()
-    # plain: one lattice per launch, the same updates
-    lat_p = [w.WolffLattice(s["dim"], s["L"], s["T"], seed=s["seed"],
-                            schedule=w.SCHED_CLUSTER, grid_blocks=1, block_threads=256)
-             for s in specs]
+    for x in lat_b:
+        x.close()
+    # plain: one lattice per launch (the library's default schedule), the same updates
+    lat_p = [w.WolffLattice(s["dim"], s["L"], s["T"], seed=s["seed"]) for s in specs]
     bufs_p = [x.record_buffer(U) for x in lat_p]
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -322,17 +446,22 @@ def run_batched(args, n_replicas=512, updates=None, embed=False):
             flips_p += int(r["C"].astype(np.int64).sum())
             same = same and np.array_equal(r, recs_b[k][i])
     t_p = sum(a.elapsed_time(b) for a, b in ev) / 1000.0
-    for x in lat_b + lat_p:
+    plain_info = lat_p[0].info() if lat_p else {}
+    for x in lat_p:
         x.close()
     out = {
         "workload": "%d 2D replicas, L in {64..1024}, T in [2.0, 2.6], seeds 1000+i, "
                     "%d x %d updates each" % (n_replicas, args.steps, U),
+        "updates_per_replica": U * args.steps,
         "batched_flips_per_s": flips_b / t_b, "plain_flips_per_s": flips_p / t_p,
         "speedup": (flips_b / t_b) / (flips_p / t_p),
         "batched_s": t_b, "plain_s": t_p, "records_identical": bool(same),
         "replica_latency_ms_p50": float(np.percentile(lat_ms, 50)),
         "replica_latency_ms_p99": float(np.percentile(lat_ms, 99)),
-        "plan": plan.to_json(), "autotune": table,
+        "plan": plan.to_json(), "autotune_s": t_tune, "autotune": table,
+        "plain_form": "one wolff_step launch per lattice, default schedule (%s, %s CTAs x %s "
+                      "threads)" % ("cluster", plain_info.get("grid_blocks"),
+                                     plain_info.get("block_threads")),
     }
     if embed:
         return out
@@ -353,7 +482,9 @@ def run_served(args, n_requests=200, embed=False):
     reqs, summary = srv.serve(trace, max_seconds=args.serve_seconds)
     srv.close()
     summary["workload"] = ("%d requests, Poisson 200 req/s, 70%% 2D L 32..2048, 30%% 3D L 16..128, "
-                           "T in [0.9, 1.1] Tc, 1e3..1e5 updates" % n_requests)
+                           "T in [0.9, 1.1] Tc, 1e3..1e5 updates; latency percentiles over every "
+                           "request, unfinished ones censored at the window's end (exact=false "
+                           "marks a lower bound)" % n_requests)
     if embed:
         return summary
     print(json.dumps({"metric": METRIC, "value": summary["flips_per_s"], "unit": UNIT,
@@ -387,25 +518,26 @@ def run_binder(args):
     print(json.dumps({"metric": "Binder ratio sweep", "binder": out}), flush=True)
 
 
-def cpu_baseline(dim, L, T, seed, spins, t, seconds, q=None):
-    """The oracle (single-threaded C) from the GPU's equilibrated lattice, a
-    few updates at a time until `seconds` of CPU work have run."""
+def potts_cpu_baseline(dim, L, q, T, seed, spins, t, seconds):
+    """The Potts oracle from the GPU's equilibrated lattice, one update at a
+    time until `seconds` of CPU work have run."""
     import numpy as np
 
     import oracle
-    thr = oracle.bond_threshold(1.0, T) if q is None else oracle.potts_threshold(1.0, T)
+    thr = oracle.potts_threshold(1.0, T)
     s = np.array(spins, dtype=np.int8, copy=True)
     flips, spent, n = 0, 0.0, 0
     while spent < seconds and n < 1000:
         t0 = time.perf_counter()
-        rec = (oracle.run(dim, L, thr, seed, t + n, 1, s) if q is None else
-               oracle.potts_run(dim, L, q, thr, seed, t + n, 1, s))
+        rec = oracle.potts_run(dim, L, q, thr, seed, t + n, 1, s)
         spent += time.perf_counter() - t0
         flips += int(rec["C"][0])
         n += 1
-    return {"value": flips / spent, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d updates from the GPU's equilibrated lattice (t=%d), %.1f s of one core"
-                      % (n, t, spent)}
+    out = {"value": flips / spent, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "%d updates from the GPU's equilibrated lattice (t=%d), %.1f s of one core"
+                     % (n, t, spent)}
+    out.update(cpu_description())
+    return out
 
 
 def run_xy(args):
@@ -541,36 +673,22 @@ def xy_cpu_baseline(dim, L, T, seed, theta, t, seconds):
         spent += time.perf_counter() - t0
         flips += int(rec["C"][0])
         n += 1
-    return {"value": flips / spent, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d updates from the GPU's equilibrated lattice (t=%d), %.1f s of one core"
-                      % (n, t, spent)}
+    out = {"value": flips / spent, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "%d updates from the GPU's equilibrated lattice (t=%d), %.1f s of one core"
+                     % (n, t, spent)}
+    out.update(cpu_description())
+    return out
 
 
-def main():
-    args = parse()
-    if args.impl == "reference":
-        return run_reference(args)
-    if WORKLOADS.get(args.workload, {}).get("model") == "xy":
-        return run_xy(args)
-    if args.workload == "batched":
-        return run_batched(args)
-    if args.workload == "served":
-        return run_served(args)
-    if args.workload == "binder":
-        return run_binder(args)
+def run_ising(args, name, stream_clocks=True):
+    """One Ising (or Potts) lattice per launch on workload `name`; returns the
+    bench line (not printed)."""
     import numpy as np
     import torch
 
-    world, rank, local = dist_setup(args)
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
     import paper_1110_0899_gb300 as w
-
-    wl = WORKLOADS[args.workload]
+    world, rank, local = dist_setup(args)
+    wl = WORKLOADS[name]
     dim, L, T = wl["dim"], wl["L"], wl["T"]
     seed = rank_seed(wl["seed"], rank)
     equil = wl["equil"] if args.equil is None else args.equil
@@ -670,39 +788,33 @@ def main():
                 repeat_identical = repeat_identical and np.array_equal(r, step_recs[0])
             e2e = {"value": e2e_flips / e2e_s, "unit": UNIT,
                    "h2d_bytes_per_step": int(snap_in.nbytes),
-                   "d2h_bytes_per_step": int(U * w.RECORD_BYTES)}
-
-    if rank != 0:
-        if world > 1:
-            torch.distributed.destroy_process_group()
-        return
+                   "d2h_bytes_per_step": int(U * w.RECORD_BYTES),
+                   "returns": "the %d records (|C|, levels, E_bond, M); the lattice stays on "
+                              "the device" % U}
+    lat.close()
     peaks, peak_kind = measured_peaks()
     per_launch_flips = flips / args.steps
     avg_launch_s = total_ms / args.steps / 1000.0
     achieved = ALGO_BYTES_PER_FLIP[dim] * per_launch_flips / avg_launch_s / 1e9
-    cap = TRAFFIC_CAPTURES.get((args.workload, U))
-    traffic = None
-    if cap and args.schedule in ("auto", "cluster") and kernel_source_hash() == cap["src"]:
-        traffic = cap["bytes_per_launch"]
+    cap = TRAFFIC_CAPTURES.get((name, U))
+    fresh = bool(cap and args.schedule in ("auto", "cluster") and not wl.get("q")
+                 and kernel_source_hash() == cap["src"])
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+            "frac": achieved / peaks["hbm_gbs"],
+            "traffic": cap["bytes_per_launch"] if fresh else None,
             "peak_kind": peak_kind,
             "kernel": {"persistent": "k_persistent<%d>", "graph": "k_graph_level<%d>",
                        "cluster": "k_team<%d>", "auto": "k_team<%d>"}[args.schedule] % dim}
-    lat.close()
-    batched_out = served_out = None
-    if world == 1 and args.workload in ("2d", "3d") and not args.no_batched:
-        class _A:   # a batched comparison beside the headline: 1000 updates per replica
-            steps, updates_per_step = 1, 1000
-        batched_out = run_batched(_A, embed=True)
-        batched_out.pop("autotune", None)
-    if world == 1 and args.workload in ("2d", "3d") and not args.no_served:
-        class _S:
-            serve_seconds = args.embed_serve_seconds
-        served_out = run_served(_S, embed=True)
+    if fresh and "l2_bytes_per_launch" in cap:
+        roof["l2_traffic"] = cap["l2_bytes_per_launch"]
+    if fresh and "imad" in cap:
+        roof["imad"] = dict(cap["imad"])
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline(dim, L, T, seed, snap, t_snap, args.cpu_seconds, q=wl.get("q"))
+        if wl.get("q"):
+            cpu = potts_cpu_baseline(dim, L, wl["q"], T, seed, snap, t_snap, args.cpu_seconds)
+        elif name in ("2d", "3d") and U == wl["updates"] and equil == wl["equil"]:
+            cpu = ising_cpu_baseline(wl, step_recs[0], args.cpu_seconds)
     # kernels per step: an L2 warm-up for lattices of 2^22 sites or more
     # (except on the Ising cluster path), the persistent schedule's pre-launch
     # reset, the update kernel (or, for the graph schedule, one call kernel and
@@ -715,7 +827,7 @@ def main():
         launches = args.steps * (2 + warm)
     else:
         launches = args.steps * (1 + warm)
-    line = {
+    return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
@@ -732,7 +844,7 @@ def main():
                    "l2": "256 MB buffer written between timed steps",
                    "parallelism": "replicas x%d" % world},
         "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
-        "clocks": clk, "batched": batched_out, "served": served_out,
+        "clocks": clk,
         "detail": {"mean_cluster": flips / len(records), "mean_levels": float(levels.mean()),
                    "max_levels": int(levels.max()), "ms_per_update": total_ms / len(records),
                    "steps_and_e2e_records_identical": bool(repeat_identical),
@@ -742,6 +854,72 @@ def main():
                    "step_ms_p99": float(np.percentile(step_ms, 99)),
                    "step_counters": {k: stats1[k] - stats0[k] for k in stats1}},
     }
+
+
+def add_l2_side(line, l2):
+    """The L2 side of a line's roofline: the same algorithmic bytes against
+    the probe's L2 read bandwidth, and the ncu L2 bytes when fresh."""
+    roof = line["roofline"]
+    ms = line["ms_per_step"]
+    l2_side = {"achieved": roof["achieved"], "peak": l2["read_gbs"], "unit": "GB/s",
+               "frac": roof["achieved"] / l2["read_gbs"], "peak_kind": "measured live: " + l2["how"]}
+    traffic = roof.pop("l2_traffic", None)
+    l2_side["traffic"] = traffic
+    if traffic is not None:
+        l2_side["traffic_gbs"] = traffic / (ms / 1000.0) / 1e9
+        l2_side["traffic_frac"] = l2_side["traffic_gbs"] / l2["read_gbs"]
+    roof["l2"] = l2_side
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    if WORKLOADS.get(args.workload, {}).get("model") == "xy":
+        return run_xy(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "served":
+        return run_served(args)
+    if args.workload == "binder":
+        return run_binder(args)
+    import torch
+
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import paper_1110_0899_gb300 as w   # noqa: F401  (fails loudly without the library)
+
+    line = run_ising(args, args.workload)
+    headline = world == 1 and args.workload == "2d"
+    l2 = None
+    if world == 1 and not args.no_l2_probe and not WORKLOADS[args.workload].get("q"):
+        l2 = l2_probe()
+        add_l2_side(line, l2)
+        line["l2_probe"] = l2
+    if headline and not args.no_3d:
+        d3 = run_ising(args, "3d")
+        if l2 is not None:
+            add_l2_side(d3, l2)
+        line["3d"] = {k: d3[k] for k in ("value", "unit", "ms_per_step", "config", "roofline",
+                                          "cpu_baseline", "e2e", "clocks", "gpu_launches",
+                                          "detail")}
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    if headline and not args.no_batched:
+        class _A:   # the specified batched workload: 10^4 updates per replica
+            steps, updates_per_step = 1, args.batched_updates
+        line["batched"] = run_batched(_A, updates=args.batched_updates, embed=True)
+    if headline and not args.no_served:
+        class _S:
+            serve_seconds = args.embed_serve_seconds
+        line["served"] = run_served(_S, embed=True)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -112,6 +112,10 @@ size_t wolff_workspace_bytes(int dim, int L, int layout);
 
 /* Creates a context on the current device and initialises the lattice from
  * Philox (update counter t = 0), then computes E_bond and M by a full pass.
+ * Paper: section 2 (the model H = -J sum S_i S_j on the periodic lattice,
+ * and the bond probability p = 1 - exp(-2J/T) of step (ii), whose threshold
+ * this computes on the host); the random start is the one of section 5's
+ * runs, drawn from Philox instead of the paper's generator.
  *   dim         2 or 3;  L >= 2, with dim*L^dim < 2^32 and L <= 1024 in 3D,
  *               L <= 32767 in 2D;
  *   J, T        coupling and temperature, J >= 0, T > 0 (T may be +inf);
@@ -211,7 +215,11 @@ wolff_status xy_set_state(wolff_ctx *ctx, const uint16_t *h_theta, uint64_t t);
 
 /* Enqueues n_updates single-cluster updates (t .. t+n-1), each: seed site,
  * level-synchronous growth with atomic claims and warp-aggregated appends to
- * the cluster list, boundary-bond energy change, unmark, record.  d_records
+ * the cluster list, boundary-bond energy change, unmark, record.
+ * Paper: section 2, steps (i)-(iv) and the ic/in list (the update), section
+ * 4, step (iii') (growth by parallel expansion of the wave-front spins), and
+ * section 5, Tables 1-2, "+ measurement" column (E and M after every
+ * update).  d_records
  * (nullable) receives n_updates wolff_record entries.  n_updates = 0 is a
  * no-op.  Asynchronous. */
 wolff_status wolff_step(wolff_ctx *ctx, uint64_t n_updates, void *d_records);
@@ -225,13 +233,14 @@ wolff_status wolff_run_host(wolff_ctx *ctx, const int8_t *h_spins_in,
                             wolff_record *h_records, int8_t *h_spins_out);
 
 /* Reads the incrementally tracked E_bond, M and the size of the last cluster
- * (0 before the first update).  Synchronises the stream; reports latched
+ * (0 before the first update).  Paper: section 2 (E and M of the
+ * Hamiltonian) and section 5 (measured after each update).  Synchronises the stream; reports latched
  * device errors.  Any output pointer may be NULL. */
 wolff_status measure(wolff_ctx *ctx, int64_t *E_bond, int64_t *M,
                      uint64_t *last_C);
 
 /* Recomputes E_bond and M by a full pass over the lattice (the verification
- * path).  Synchronises. */
+ * path; section 2's definitions summed directly).  Synchronises. */
 wolff_status measure_full(wolff_ctx *ctx, int64_t *E_bond, int64_t *M);
 
 /* Checkpoint: copies the lattice out as int8 +-1 (N entries, h_spins) and the
@@ -419,7 +428,31 @@ wolff_status wolff_batch_run_timed(wolff_batch *b, wolff_ctx *const *ctxs, int n
                                    const uint64_t *n_updates, void *const *d_records,
                                    int cluster_size, int block_threads, uint64_t budget_ns);
 
+/* Window slots per CTA of this batch's launches (window mode's queue of
+ * speculative updates, see wolff_set_burst): 16, 32, 64 (the default) or
+ * 128, or 0 to run the batch without window mode.  Larger windows hold more
+ * updates in flight and need more shared memory; a team shape whose window
+ * does not fit makes the next wolff_batch_run fail with WOLFF_ECUDA.  The
+ * levels per round come from each context's wolff_set_burst.  Results do not
+ * depend on the setting.  EINVAL for other values. */
+wolff_status wolff_batch_set_window(wolff_batch *b, int slots_per_cta);
+
 wolff_status wolff_batch_free(wolff_batch *b);
+
+/* ---- measurement aid ------------------------------------------------------
+ * L2 bandwidth probe (the paper has no counterpart; it gives the L2 side of
+ * the growth kernels' memory roofline, whose working set lives in L2).
+ * Streams the device buffer d_buf (`bytes` bytes, a multiple of 16, 16-byte
+ * aligned) `passes` times (1..100000) in one launch of a full-occupancy grid
+ * over all SMs, with 16-byte loads that skip L1; mode 0 only reads, mode 1
+ * also writes every vector back (its contents change).  d_sink: one
+ * 4-byte-aligned device word the kernel may write (so its loads stay live).
+ * With `bytes` well inside L2, every pass after the first is served by L2:
+ * passes * bytes (mode 1: twice that) over the launch's CUDA-event time is
+ * the L2 bandwidth.  EINVAL for bad arguments, ECUDA if a device query or the
+ * launch fails.  Asynchronous on stream (NULL = default stream). */
+wolff_status wolff_l2_probe(void *d_buf, size_t bytes, int passes, int mode, uint32_t *d_sink,
+                            void *stream);
 
 /* Releases the context (and the workspace if the library allocated it).
  * Synchronises the stream first. */

@@ -106,8 +106,10 @@ def load_library():
         "wolff_batch_run": (i, [v, v, i, v, v, i, i]),
         "wolff_batch_run_timed": (i, [v, v, i, v, v, i, i, u64]),
         "wolff_batch_free": (i, [v]),
+        "wolff_batch_set_window": (i, [v, i]),
         "wolff_step_static": (i, [i, i, d, d, u64, u64, u64, v, v, v]),
         "wolff_step_static_status": (i, [v, P(i), P(u32), P(u64)]),
+        "wolff_l2_probe": (i, [v, sz, i, i, v, v]),
         "wolff_bond_threshold": (u64, [d, d]),
         "wolff_philox": (i, [u32, u32, v, v, u64, v]),
         "wolff_selftest_wait_timeout": (i, [v, u64, P(i)]),
@@ -265,6 +267,21 @@ def wolff_philox(key0, key1, d_ctr, d_out, n, stream=None):
                                        _stream_handle(stream)))
 
 
+def wolff_l2_probe(d_buf, passes, mode=0, d_sink=None, stream=None):
+    """Enqueues the L2 bandwidth probe over the torch CUDA tensor d_buf (its
+    whole storage, a multiple of 16 bytes) `passes` times; mode 0 reads, 1
+    reads and writes back.  d_sink: a CUDA tensor of at least 4 bytes (made
+    here if None; keep it alive until the launch has run)."""
+    torch = _torch()
+    if d_sink is None:
+        d_sink = torch.zeros(1, dtype=torch.int32, device=d_buf.device)
+    nbytes = d_buf.numel() * d_buf.element_size()
+    _check(load_library().wolff_l2_probe(ctypes.c_void_p(d_buf.data_ptr()), nbytes, int(passes),
+                                         int(mode), ctypes.c_void_p(d_sink.data_ptr()),
+                                         _stream_handle(stream)))
+    return d_sink
+
+
 def records_to_numpy(d_records, n):
     """Device record buffer -> numpy structured array (synchronises)."""
     host = d_records[: n * RECORD_BYTES].cpu().numpy()
@@ -280,6 +297,8 @@ class WolffLattice:
         self.dim, self.L, self.J, self.T, self.seed = int(dim), int(L), float(J), float(T), int(seed)
         self.N = self.L ** self.dim
         self.q = q
+        # the CUDA stream the context enqueues on (its handle value)
+        self.stream = _stream_handle(stream).value
         if q is None:
             self.handle, self.workspace = ising_init(dim, L, J, T, seed, layout, stream=stream)
         else:
@@ -437,6 +456,11 @@ class WolffBatch:
         _check(load_library().wolff_batch_run_timed(self.handle, ctxs, n, nu, recs,
                                                     int(cluster_size), int(block_threads),
                                                     int(budget_ns)))
+
+    def set_window(self, slots_per_cta):
+        """Window slots per CTA of this batch's launches (16, 32, 64, 128; 0 =
+        window mode off)."""
+        _check(load_library().wolff_batch_set_window(self.handle, int(slots_per_cta)))
 
     def close(self):
         if self.handle is not None and self.handle.value:

@@ -1,12 +1,21 @@
 """Batched form: many independent lattices per launch, with an autotuner.
 
-A plan splits the lattices into groups; each group is launched through one
-wolff_batch (one thread-block cluster per lattice, the C ABI's batched entry
-point) on its own CUDA stream, so groups with different team shapes run
-concurrently.  The autotuner times candidate plans on throw-away copies of
-the workload (same shapes and temperatures, other seeds) and caches the
-winner per GPU and workload signature.  No plan changes any result: each
-lattice follows the chain it would follow alone.
+A plan splits the lattices into groups.  A group runs on one of two
+schedules:
+  - "batched": one persistent launch through a wolff_batch (one
+    thread-block cluster per lattice, the C ABI's batched entry point) on the
+    group's own CUDA stream, with the group's team shape (cluster size,
+    threads per CTA) and window-mode queue (window slots per CTA, growth
+    levels per commit round);
+  - "launches": one wolff_step launch per lattice with the library's default
+    schedule (the largest thread-block cluster, window mode), on the stream
+    the lattices were created on, concurrently with the batched groups.
+The autotuner times candidate plans on throw-away copies of the workload
+(same shapes and temperatures, other seeds): first the team shapes and the
+size split, then, around the best of those, the window slots, the levels
+per round and the schedule of the large lattices.  It caches the winner per
+GPU and workload signature.  No plan changes any result: each lattice
+follows the chain it would follow alone.
 """
 import hashlib
 import json
@@ -15,32 +24,69 @@ import time
 
 import numpy as np
 
-from . import (RECORD_BYTES, WolffBatch, WolffLattice, _build, records_to_numpy)
+from . import (RECORD_BYTES, WolffBatch, WolffLattice, _build, records_to_numpy, wolff_step)
+
+
+BATCHED, LAUNCHES = "batched", "launches"
+DEFAULT_SLOTS = 64
+
+
+class Group:
+    """Lattices `ix` on one schedule: BATCHED with team shape (cs, th),
+    `slots` window slots per CTA and `levels` growth levels per round (1 =
+    the library's default), or LAUNCHES (one default launch per lattice)."""
+
+    def __init__(self, ix, cs=1, th=256, slots=DEFAULT_SLOTS, levels=1, kind=BATCHED):
+        self.ix, self.cs, self.th = list(ix), int(cs), int(th)
+        self.slots, self.levels, self.kind = int(slots), int(levels), kind
+
+    def replace(self, **kw):
+        d = dict(ix=self.ix, cs=self.cs, th=self.th, slots=self.slots, levels=self.levels,
+                 kind=self.kind)
+        d.update(kw)
+        return Group(**d)
+
+    def to_json(self):
+        if self.kind == LAUNCHES:
+            return {"n": len(self.ix), "schedule": LAUNCHES}
+        return {"n": len(self.ix), "schedule": BATCHED, "cluster_size": self.cs,
+                "block_threads": self.th, "window_slots": self.slots,
+                "levels_per_round": self.levels if self.levels > 1 else "default"}
 
 
 class Plan:
-    """groups: list of (indices, cluster_size, block_threads)."""
+    """groups: list of Group (or of (indices, cluster_size, block_threads))."""
 
     def __init__(self, groups, label=""):
-        self.groups = [(list(ix), int(cs), int(th)) for ix, cs, th in groups]
+        self.groups = [g if isinstance(g, Group) else Group(*g) for g in groups]
         self.label = label
 
     def to_json(self):
-        return {"label": self.label,
-                "groups": [{"n": len(ix), "cluster_size": cs, "block_threads": th}
-                           for ix, cs, th in self.groups]}
+        return {"label": self.label, "groups": [g.to_json() for g in self.groups]}
 
 
 class BatchedRunner:
-    """Executes a plan over a list of lattices created on the caller's device."""
+    """Executes a plan over a list of lattices created on the caller's device
+    (the lattices of a LAUNCHES group on the stream that is current when
+    run() is called)."""
 
     def __init__(self, lattices, plan):
         import torch
         self.lattices = lattices
         self.plan = plan
-        self.streams = [torch.cuda.Stream() for _ in plan.groups]
-        self.batches = [WolffBatch(max(1, len(ix)), stream=st)
-                        for (ix, _, _), st in zip(plan.groups, self.streams)]
+        self.streams, self.batches = [], []
+        for g in plan.groups:
+            if g.kind == BATCHED:
+                st = torch.cuda.Stream()
+                b = WolffBatch(max(1, len(g.ix)), stream=st)
+                b.set_window(g.slots)
+                self.streams.append(st)
+                self.batches.append(b)
+            else:
+                self.streams.append(None)
+                self.batches.append(None)
+            for i in g.ix:
+                lattices[i].set_burst(g.levels if g.kind == BATCHED else 1)
         self._records = None
         self._rec_n = 0
 
@@ -60,15 +106,27 @@ class BatchedRunner:
         import torch
         bufs = self.record_buffers(n_updates) if records else None
         cur = torch.cuda.current_stream()
-        for (ix, cs, th), st, b in zip(self.plan.groups, self.streams, self.batches):
-            if not ix:
+        # the batched groups first, each on its stream once the current
+        # stream's earlier work is done ...
+        for g, st, b in zip(self.plan.groups, self.streams, self.batches):
+            if g.kind != BATCHED or not g.ix:
                 continue
             st.wait_stream(cur)
-            b.run([self.lattices[i] for i in ix], n_updates,
-                  None if bufs is None else [bufs[i] for i in ix], cluster_size=cs,
-                  block_threads=th)
+            b.run([self.lattices[i] for i in g.ix], n_updates,
+                  None if bufs is None else [bufs[i] for i in g.ix], cluster_size=g.cs,
+                  block_threads=g.th)
+        # ... then the per-lattice launches on the current stream, concurrently
+        for g in self.plan.groups:
+            if g.kind != LAUNCHES:
+                continue
+            for i in g.ix:
+                lat = self.lattices[i]
+                if (lat.stream or 0) != (cur.cuda_stream or 0):
+                    raise ValueError("a LAUNCHES group needs lattices made on the current stream")
+                wolff_step(lat.handle, n_updates, None if bufs is None else bufs[i])
         for st in self.streams:
-            cur.wait_stream(st)
+            if st is not None:
+                cur.wait_stream(st)
         return bufs
 
     def records_numpy(self, bufs, n_updates):
@@ -76,28 +134,57 @@ class BatchedRunner:
 
     def close(self):
         for b in self.batches:
-            b.close()
+            if b is not None:
+                b.close()
 
 
-def candidate_plans(specs):
-    """Single-launch plans over all lattices and size-split plans (large
-    lattices with bigger teams, concurrently with the small ones)."""
+def _size_split(specs):
     n = len(specs)
     allix = list(range(n))
-    plans = []
-    for cs in (1, 2, 4):
-        for th in (128, 256, 512):
-            plans.append(Plan([(allix, cs, th)], "all cs=%d th=%d" % (cs, th)))
     sizes = np.array([s["L"] ** s["dim"] for s in specs])
     cut = np.quantile(sizes, 0.75) if n else 0
     big = [i for i in allix if sizes[i] >= cut and sizes[i] > 100_000]
     small = [i for i in allix if i not in set(big)]
+    return big, small
+
+
+def candidate_plans(specs):
+    """First stage: single-launch plans over all lattices and size-split plans
+    (large lattices with bigger teams, concurrently with the small ones)."""
+    allix = list(range(len(specs)))
+    plans = []
+    for cs in (1, 2, 4):
+        for th in (128, 256, 512):
+            plans.append(Plan([Group(allix, cs, th)], "all cs=%d th=%d" % (cs, th)))
+    big, small = _size_split(specs)
     if big and small:
         for cs in (2, 4, 8):
             for th in (256, 512):
-                plans.append(Plan([(big, cs, th), (small, 1, 256)],
+                plans.append(Plan([Group(big, cs, th), Group(small, 1, 256)],
                                   "split big cs=%d th=%d / small cs=1 th=256" % (cs, th)))
     return plans
+
+
+def refine_plans(best, specs):
+    """Second stage, around the best first-stage plan: the window-mode queue
+    (slots per CTA 32 or 128 instead of 64; 12 or 32 growth levels per round
+    instead of the default) and the schedule of the large lattices (one
+    default launch each instead of a batched launch)."""
+    out = []
+    for slots in (32, 128):
+        out.append(Plan([g.replace(slots=slots) for g in best.groups],
+                        best.label + " / slots=%d" % slots))
+    for levels in (12, 32):
+        out.append(Plan([g.replace(levels=levels) for g in best.groups],
+                        best.label + " / levels=%d" % levels))
+    big, small = _size_split(specs)
+    if big and small:
+        small_g = [g for g in best.groups if set(g.ix) == set(small)]
+        small_g = small_g[0] if small_g else Group(small, 1, 256)
+        out.append(Plan([Group(big, kind=LAUNCHES), small_g],
+                        "big: one default launch each / small: %s" % (
+                            "cs=%d th=%d" % (small_g.cs, small_g.th))))
+    return out
 
 
 def _signature(specs, probe_updates):
@@ -110,36 +197,23 @@ def _cache_path():
     return os.path.join(_build.OUT_DIR, "autotune.json")
 
 
-def autotune(specs, probe_updates=40, seed_offset=10_000_000, use_cache=True, verbose=False):
-    """Times every candidate plan on fresh lattices of the same shapes (other
-    seeds) for probe_updates updates each; returns (best Plan, table)."""
+def _time_plan(p, specs, probe_updates, seed_offset):
     import torch
-    sig = _signature(specs, probe_updates)
-    cache = {}
-    if use_cache and os.path.exists(_cache_path()):
-        try:
-            with open(_cache_path()) as f:
-                cache = json.load(f)
-        except (OSError, ValueError):
-            cache = {}
-    plans = candidate_plans(specs)
-    if use_cache and sig in cache:
-        label = cache[sig]["best"]
-        for p in plans:
-            if p.label == label:
-                return p, cache[sig]["table"]
-    table = []
-    for k, p in enumerate(plans):
-        # every candidate runs the same updates from the same fresh lattices
-        lats = [WolffLattice(s["dim"], s["L"], s["T"], seed=s["seed"] + seed_offset)
-                for s in specs]
+    # every candidate runs the same updates from the same fresh lattices
+    lats = [WolffLattice(s["dim"], s["L"], s["T"], seed=s["seed"] + seed_offset)
+            for s in specs]
+    r = None
+    try:
         r = BatchedRunner(lats, p)
         # first launches of a team shape (kernel attributes, shared-memory
         # carve-out) happen outside the timing, on two throwaway lattices
         warm = [WolffLattice(2, 8, 2.0, seed=1) for _ in range(2)]
-        for _, cs, th in p.groups:
-            BatchedRunner(warm, Plan([([0, 1], cs, th)])).run(2, records=False)
-        torch.cuda.synchronize()
+        for g in p.groups:
+            if g.kind == BATCHED:
+                w = BatchedRunner(warm, Plan([g.replace(ix=[0, 1])]))
+                w.run(2, records=False)
+                torch.cuda.synchronize()
+                w.close()
         for x in warm:
             x.close()
         torch.cuda.synchronize()
@@ -149,16 +223,64 @@ def autotune(specs, probe_updates=40, seed_offset=10_000_000, use_cache=True, ve
         dt = time.perf_counter() - t0
         flips = sum(int(x["C"].astype(np.int64).sum())
                     for x in r.records_numpy(bufs, probe_updates))
-        r.close()
+        return {"plan": p.label, "groups": [g.to_json() for g in p.groups], "seconds": dt,
+                "flips_per_s": flips / dt}
+    except Exception as e:   # a window that does not fit a team shape, etc.
+        torch.cuda.synchronize()
+        return {"plan": p.label, "groups": [g.to_json() for g in p.groups], "seconds": None,
+                "error": str(e)[:200]}
+    finally:
+        if r is not None:
+            r.close()
         for lat in lats:
             lat.close()
-        table.append({"plan": p.label, "seconds": dt, "flips_per_s": flips / dt})
-        if verbose:
-            print("autotune %-45s %.4g flips/s" % (p.label, flips / dt))
-    best = min(range(len(plans)), key=lambda i: table[i]["seconds"])
+
+
+def autotune(specs, probe_updates=40, seed_offset=10_000_000, use_cache=True, verbose=False):
+    """Times the candidate plans on fresh lattices of the same shapes (other
+    seeds) for probe_updates updates each, in two stages (team shapes and
+    size split; then window queue, levels per round and the large lattices'
+    schedule around the best); returns (best Plan, table)."""
+    sig = _signature(specs, probe_updates)
+    cache = {}
+    if use_cache and os.path.exists(_cache_path()):
+        try:
+            with open(_cache_path()) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+    if use_cache and sig in cache and "plan" in cache[sig]:
+        return _plan_from_json(cache[sig]["plan"], specs), cache[sig]["table"]
+    table, plans = [], []
+
+    def run_stage(cands):
+        for p in cands:
+            row = _time_plan(p, specs, probe_updates, seed_offset)
+            table.append(row)
+            plans.append(p)
+            if verbose:
+                print("autotune %-60s %s" % (p.label, row.get("flips_per_s", row.get("error"))))
+
+    def best_index():
+        ok = [i for i in range(len(plans)) if table[i]["seconds"] is not None]
+        return min(ok, key=lambda i: table[i]["seconds"])
+    run_stage(candidate_plans(specs))
+    run_stage(refine_plans(plans[best_index()], specs))
+    best = plans[best_index()]
     if use_cache:
-        cache[sig] = {"best": plans[best].label, "table": table}
+        cache[sig] = {"best": best.label, "plan": _plan_to_cache(best), "table": table}
         os.makedirs(os.path.dirname(_cache_path()), exist_ok=True)
         with open(_cache_path(), "w") as f:
             json.dump(cache, f, indent=1)
-    return plans[best], table
+    return best, table
+
+
+def _plan_to_cache(p):
+    return {"label": p.label,
+            "groups": [{"ix": g.ix, "cs": g.cs, "th": g.th, "slots": g.slots,
+                        "levels": g.levels, "kind": g.kind} for g in p.groups]}
+
+
+def _plan_from_json(d, specs):
+    return Plan([Group(g["ix"], g["cs"], g["th"], g["slots"], g["levels"], g["kind"])
+                 for g in d["groups"]], d["label"])

@@ -854,6 +854,7 @@ const char *wolff_last_error(wolff_ctx *c) {
 
 struct wolff_batch {
     int capacity = 0;
+    int win_slots = kBatchWindowSlots;   // window slots per CTA (0 = window mode off)
     cudaStream_t stream = nullptr;
     StepParams *h_table = nullptr;   // pinned staging copy
     StepParams *d_table = nullptr;
@@ -928,13 +929,22 @@ wolff_status wolff_batch_run_timed(wolff_batch *b, wolff_ctx *const *ctxs, int n
     b->pending = true;
     StepParams none = {};
     if (n2)
-        e = launch_team(2, none, b->d_table, n2, cluster_size, block_threads, kBatchWindowSlots,
+        e = launch_team(2, none, b->d_table, n2, cluster_size, block_threads, b->win_slots,
                         b->stream);
     if (e == cudaSuccess && n3)
-        e = launch_team(3, none, b->d_table + n2, n3, cluster_size, block_threads,
-                        kBatchWindowSlots, b->stream);
+        e = launch_team(3, none, b->d_table + n2, n3, cluster_size, block_threads, b->win_slots,
+                        b->stream);
     if (e != cudaSuccess) return WOLFF_ECUDA;
     for (int i = 0; i < n; ++i) ctxs[i]->t_host += n_updates[i];
+    return WOLFF_OK;
+}
+
+wolff_status wolff_batch_set_window(wolff_batch *b, int slots_per_cta) {
+    if (!b) return WOLFF_EINVAL;
+    if (slots_per_cta != 0 && slots_per_cta != 16 && slots_per_cta != 32 && slots_per_cta != 64 &&
+        slots_per_cta != 128)
+        return WOLFF_EINVAL;
+    b->win_slots = slots_per_cta;
     return WOLFF_OK;
 }
 

@@ -25,7 +25,7 @@ from . import RECORD_BYTES, WolffBatch, WolffLattice, records_to_numpy, wolff_wo
 
 class Request:
     __slots__ = ("spec", "lattice", "records", "done", "admitted_s", "finished_s", "result",
-                 "ns_per_update", "quota", "updates_seen")
+                 "ns_per_update", "quota", "updates_seen", "first_update_s")
 
     def __init__(self, spec):
         self.spec = spec
@@ -38,6 +38,7 @@ class Request:
         self.ns_per_update = None
         self.quota = 0
         self.updates_seen = 0
+        self.first_update_s = None
 
     @property
     def remaining(self):
@@ -88,7 +89,7 @@ class WolffServer:
             q = min(q, 4 * max(r.quota, 1))
         return max(1, min(q, self.epoch_updates, r.remaining))
 
-    def _epoch(self, active):
+    def _epoch(self, active, t0=None):
         import torch
         cur = torch.cuda.current_stream()
         groups = [[], []]
@@ -118,6 +119,8 @@ class WolffServer:
                 per = dt / ran
                 r.ns_per_update = per if r.ns_per_update is None else 0.5 * (r.ns_per_update + per)
             r.quota = max(ran, 1)
+            if ran > 0 and r.done == 0 and t0 is not None:
+                r.first_update_s = time.perf_counter() - t0
             r.done += ran
 
     def _retire(self, req, now):
@@ -140,6 +143,7 @@ class WolffServer:
         mem_used = 0
         max_backlog = 0
         epochs = 0
+        active_per_epoch = []
         t0 = time.perf_counter()
         while pending or active:
             now = time.perf_counter() - t0
@@ -160,7 +164,8 @@ class WolffServer:
                     if delay > 0:
                         time.sleep(min(delay, 0.01))
                 continue
-            self._epoch(active)
+            active_per_epoch.append(len(active))
+            self._epoch(active, t0)
             epochs += 1
             now = time.perf_counter() - t0
             still = []
@@ -182,19 +187,70 @@ class WolffServer:
         flips = sum(r.result["flips"] or 0 for r in done) + partial_flips
         updates = sum(r.spec["n_updates"] for r in done) + sum(r.done for r in active)
         last_arrival = max((r.spec["arrival_s"] for r in everyone), default=0.0) * time_scale
+        # latency over every request: an unfinished one is censored at the end
+        # of the window (its latency is at least wall - arrival)
+        lat_all = censored_latencies(everyone, wall, time_scale)
+        first = np.array([r.first_update_s - r.spec["arrival_s"] * time_scale for r in everyone
+                          if r.first_update_s is not None])
         summary = {
             "requests": len(everyone), "completed": len(done), "epochs": epochs,
             "wall_s": wall, "flips": flips, "updates": updates,
             "flips_per_s": flips / wall if wall > 0 else 0.0,
             "updates_per_s": updates / wall if wall > 0 else 0.0,
-            "latency_p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
-            "latency_p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
+            "latency_p50_s": None, "latency_p99_s": None,
+            "latency_p50_exact": None, "latency_p99_exact": None,
+            "completed_latency_p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
+            "completed_latency_p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
+            "first_update_p50_s": float(np.percentile(first, 50)) if len(first) else None,
+            "first_update_p99_s": float(np.percentile(first, 99)) if len(first) else None,
+            "started": int(len(first)),
+            "active_per_epoch_median": (float(np.median(active_per_epoch))
+                                        if active_per_epoch else 0.0),
+            "active_per_epoch_max": int(max(active_per_epoch, default=0)),
             "max_backlog": max_backlog,
             "offered_span_s": last_arrival,
             "saturated": wall > 1.5 * last_arrival + 1.0,
         }
+        for q in (50, 99):
+            v, exact = censored_quantile(lat_all, q / 100.0)
+            summary["latency_p%d_s" % q] = v
+            summary["latency_p%d_exact" % q] = exact
         return everyone, summary
 
     def close(self):
         for b in self.batches:
             b.close()
+
+
+def censored_latencies(requests, wall, time_scale=1.0):
+    """(latency, finished) per request: completion - arrival for a finished
+    request, wall - arrival (a lower bound) for one still running or waiting
+    when the window ended."""
+    out = []
+    for r in requests:
+        arr = r.spec["arrival_s"] * time_scale
+        if r.finished_s is not None:
+            out.append((r.finished_s - arr, True))
+        else:
+            out.append((max(0.0, wall - arr), False))
+    return out
+
+
+def censored_quantile(values, q):
+    """Nearest-rank q-quantile of latencies some of which are censored lower
+    bounds.  Returns (value, exact): the quantile computed with the bounds in
+    place of the unknown latencies; it is exact when the k = ceil(q n)
+    smallest entries are all finished requests no larger than every bound
+    (then no unknown latency can move below it), else the true quantile is at
+    least the value returned."""
+    if not values:
+        return None, None
+    n = len(values)
+    k = max(1, int(np.ceil(q * n)))
+    srt = sorted(values, key=lambda x: x[0])
+    v = float(srt[k - 1][0])
+    exact = all(fin for _, fin in srt[:k])
+    bounds = [x for x, fin in values if not fin]
+    if bounds and v > min(bounds):
+        exact = False
+    return v, exact

@@ -55,8 +55,12 @@ def test_autotune_returns_a_working_plan():
     from paper_1110_0899_gb300 import batched
     specs = _small_specs(16)
     plan, table = batched.autotune(specs, probe_updates=8, use_cache=False)
-    assert len(table) == len(batched.candidate_plans(specs))
-    assert all(t["seconds"] > 0 for t in table)
+    # both stages: team shapes and split, then window slots and levels per
+    # round around the best
+    assert len(table) >= len(batched.candidate_plans(specs)) + 4
+    assert all(t["seconds"] is None or t["seconds"] > 0 for t in table)
+    assert any("slots=128" in t["plan"] for t in table)
+    assert any("levels=12" in t["plan"] for t in table)
     lats = [w.WolffLattice(s["dim"], s["L"], s["T"], seed=s["seed"]) for s in specs]
     r = batched.BatchedRunner(lats, plan)
     bufs = r.run(20)
@@ -66,6 +70,42 @@ def test_autotune_returns_a_working_plan():
     for i, s in enumerate(specs):
         ref, _ = oracle_trajectory(s["dim"], s["L"], s["T"], s["seed"], 20)
         assert_records_equal(got[i], ref, "autotuned plan replica %d" % i)
+        lats[i].close()
+
+
+@pytest.mark.parametrize("variant", ["slots32", "slots128", "no_window", "levels12",
+                                     "launches"])
+def test_every_plan_dimension_keeps_the_chains(variant):
+    """Each dimension the autotuner searches -- window slots per CTA, window
+    mode off, growth levels per round, and the large lattices run as one
+    default launch each beside a batched launch -- leaves every replica's
+    records equal to the oracle's, over two calls."""
+    torch, w = require_cuda()
+    from paper_1110_0899_gb300 import batched
+    specs = _small_specs(24)
+    lats = [w.WolffLattice(s["dim"], s["L"], s["T"], seed=s["seed"]) for s in specs]
+    big = [i for i, s in enumerate(specs) if s["L"] ** s["dim"] >= 48 * 48]
+    small = [i for i in range(len(specs)) if i not in big]
+    G = batched.Group
+    groups = {
+        "slots32": [G(big, 4, 256, slots=32), G(small, 1, 128, slots=32)],
+        "slots128": [G(big, 2, 256, slots=128), G(small, 1, 256, slots=128)],
+        "no_window": [G(big, 4, 256, slots=0), G(small, 1, 128, slots=0)],
+        "levels12": [G(big, 4, 512, levels=12), G(small, 1, 128, levels=3)],
+        "launches": [G(big, kind=batched.LAUNCHES), G(small, 1, 256)],
+    }[variant]
+    r = batched.BatchedRunner(lats, batched.Plan(groups, variant))
+    got = []
+    for n in (25, 35):
+        bufs = r.run(n)
+        torch.cuda.synchronize()
+        got.append(r.records_numpy(bufs, n))
+    r.close()
+    for i, s in enumerate(specs):
+        ref, s_ref = oracle_trajectory(s["dim"], s["L"], s["T"], s["seed"], 60)
+        assert_records_equal(np.concatenate([got[0][i], got[1][i]]), ref,
+                             "%s replica %d" % (variant, i))
+        assert np.array_equal(lats[i].get_state()[0], s_ref)
         lats[i].close()
 
 

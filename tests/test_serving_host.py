@@ -1,0 +1,41 @@
+"""Host logic of the serving summary: latency percentiles over every request
+when some requests were still unfinished at the end of the window (their
+latency is known only to be at least window end - arrival)."""
+import numpy as np
+
+from paper_1110_0899_gb300.serving import censored_latencies, censored_quantile
+
+
+class _R:
+    def __init__(self, arrival, finished):
+        self.spec = {"arrival_s": arrival}
+        self.finished_s = finished
+
+
+def test_censored_quantile_exact_when_no_bound_reaches_it():
+    vals = [(float(x), True) for x in range(1, 101)] + [(500.0, False)]
+    v, exact = censored_quantile(vals, 0.5)
+    assert v == 51.0 and exact          # the 51st of 101 is a finished request below the bound
+    v, exact = censored_quantile(vals, 0.99)
+    assert v == 100.0 and exact
+
+
+def test_censored_quantile_is_a_lower_bound_past_the_censoring():
+    vals = [(1.0, True), (2.0, True), (3.0, True), (4.0, False), (9.0, False)]
+    v, exact = censored_quantile(vals, 0.99)
+    assert v == 9.0 and not exact
+    # a bound below a finished latency: the true order is unknown
+    vals = [(1.0, True), (5.0, True), (2.0, False)]
+    v, exact = censored_quantile(vals, 0.6)
+    assert v == 2.0 and not exact
+    assert censored_quantile([], 0.5) == (None, None)
+
+
+def test_censored_latencies_counts_unfinished_requests():
+    reqs = [_R(0.0, 1.5), _R(1.0, None), _R(2.0, 2.5), _R(40.0, None)]
+    got = censored_latencies(reqs, wall=30.0)
+    assert got == [(1.5, True), (29.0, False), (0.5, True), (0.0, False)]
+    # with every request finished the quantile is the plain nearest-rank one
+    lat = np.array([3.0, 1.0, 2.0, 5.0, 4.0])
+    v, exact = censored_quantile([(x, True) for x in lat], 0.5)
+    assert v == 3.0 and exact

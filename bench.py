@@ -128,6 +128,9 @@ def parse():
                     help="skip the batched-vs-plain comparison in the default line")
     ap.add_argument("--batched-updates", type=int, default=10000,
                     help="updates per replica of the batched comparison")
+    ap.add_argument("--plain-every", type=int, default=16,
+                    help="the default line's batched comparison runs its plain arm on every "
+                         "k-th replica (--workload batched runs all)")
     ap.add_argument("--no-served", action="store_true",
                     help="skip the serving run in the default line")
     ap.add_argument("--no-l2-probe", action="store_true")
@@ -389,12 +392,15 @@ def ising_cpu_baseline(wl, gpu_records, full_seconds):
     return out
 
 
-def run_batched(args, n_replicas=512, updates=None, embed=False):
+def run_batched(args, n_replicas=512, updates=None, embed=False, plain_every=1):
     """512 independent 2D replicas (L in {64..1024}, T in [2.0, 2.6], seeds
     1000+i) through the autotuned batched plan, against the same replicas run
     one lattice per launch with the library's default settings.  Both arms
     run the same updates from the same random starts, so their records must
-    agree bit for bit."""
+    agree bit for bit.  plain_every = k > 1 runs the plain arm on every k-th
+    replica only (a stratified sample of the same table: one lattice per
+    launch takes minutes at 10^4 updates per replica), its throughput the
+    sample's flips over the sample's time."""
     import numpy as np
     import torch
 
@@ -428,7 +434,9 @@ def run_batched(args, n_replicas=512, updates=None, embed=False):
     for x in lat_b:
         x.close()
     # plain: one lattice per launch (the library's default schedule), the same updates
-    lat_p = [w.WolffLattice(s["dim"], s["L"], s["T"], seed=s["seed"]) for s in specs]
+    plain_ix = list(range(0, n_replicas, max(1, plain_every)))
+    lat_p = [w.WolffLattice(specs[i]["dim"], specs[i]["L"], specs[i]["T"], seed=specs[i]["seed"])
+             for i in plain_ix]
     bufs_p = [x.record_buffer(U) for x in lat_p]
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -441,7 +449,7 @@ def run_batched(args, n_replicas=512, updates=None, embed=False):
             w.wolff_step(x.handle, U, b)
         ev[k][1].record()
         torch.cuda.synchronize()
-        for i, (x, b) in enumerate(zip(lat_p, bufs_p)):
+        for i, x, b in zip(plain_ix, lat_p, bufs_p):
             r = w.records_to_numpy(b, U)
             flips_p += int(r["C"].astype(np.int64).sum())
             same = same and np.array_equal(r, recs_b[k][i])
@@ -462,6 +470,10 @@ def run_batched(args, n_replicas=512, updates=None, embed=False):
         "plain_form": "one wolff_step launch per lattice, default schedule (%s, %s CTAs x %s "
                       "threads)" % ("cluster", plain_info.get("grid_blocks"),
                                      plain_info.get("block_threads")),
+        "plain_sample": ("all %d replicas" % n_replicas if len(plain_ix) == n_replicas else
+                         "every %d-th replica (%d of %d), the full %d updates each; records "
+                         "compared with the batched arm's for those" % (
+                             plain_every, len(plain_ix), n_replicas, U)),
     }
     if embed:
         return out
@@ -585,6 +597,7 @@ def run_xy(args):
         torch.cuda.synchronize()
         clocks = ClockSampler(local)
         clocks.start()
+        time.sleep(0.5)   # the sampler's start-up stays out of the timed steps
         for k in range(args.steps):
             flush.fill_(k & 0xFF)
             starts[k].record(stream)
@@ -738,6 +751,7 @@ def run_ising(args, name, stream_clocks=True):
         torch.cuda.synchronize()
         clocks = ClockSampler(local)
         clocks.start()
+        time.sleep(0.5)   # the sampler's start-up stays out of the timed steps
         for k in range(args.steps):
             restore()
             flush.fill_(k & 0xFF)
@@ -915,7 +929,8 @@ def main():
     if headline and not args.no_batched:
         class _A:   # the specified batched workload: 10^4 updates per replica
             steps, updates_per_step = 1, args.batched_updates
-        line["batched"] = run_batched(_A, updates=args.batched_updates, embed=True)
+        line["batched"] = run_batched(_A, updates=args.batched_updates, embed=True,
+                                      plain_every=args.plain_every)
     if headline and not args.no_served:
         class _S:
             serve_seconds = args.embed_serve_seconds

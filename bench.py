@@ -55,9 +55,20 @@ TC2 = 2.0 / math.log(1.0 + math.sqrt(2.0))
 # k_team hash to the captured value: DRAM bytes (dram__bytes_read.sum +
 # dram__bytes_write.sum), L2 bytes (lts__t_bytes.sum) and the fmaheavy pipe
 # (IMAD) activity.
+# imad: the fmaheavy pipe (integer multiply-add, the Philox arithmetic) busy
+# cycles over its peak (4 per SM-cycle), on the SMs the launch kept active and
+# over the whole GPU, and its warp instructions per launch.
 TRAFFIC_CAPTURES = {
-    ("2d", 10000): {"src": "35704c4b61f6", "bytes_per_launch": 11246848 + 256},
-    ("3d", 10000): {"src": "35704c4b61f6", "bytes_per_launch": 24329728 + 34560},
+    ("2d", 10000): {"src": "35704c4b61f6", "bytes_per_launch": 11246592 + 768,
+                    "l2_bytes_per_launch": 54157952,
+                    "imad": {"pipe_frac_active_sms": 8441756 / (4 * 13959321),
+                             "pipe_frac_gpu": 8441756 / (4 * 133400676),
+                             "warp_insts": 3501302}},
+    ("3d", 10000): {"src": "35704c4b61f6", "bytes_per_launch": 24321536 + 27648,
+                    "l2_bytes_per_launch": 117727776,
+                    "imad": {"pipe_frac_active_sms": 10871650 / (4 * 22075326),
+                             "pipe_frac_gpu": 10871650 / (4 * 210482946),
+                             "warp_insts": 4538094}},
 }
 
 
@@ -117,6 +128,11 @@ def parse():
     ap.add_argument("--t-up", type=int, default=None,
                     help="leader hands wave fronts above this size to all CTAs")
     ap.add_argument("--t-down", type=int, default=None)
+    ap.add_argument("--levels", type=int, default=None,
+                    help="window mode: growth levels per commit round (0 = window mode off)")
+    ap.add_argument("--helpers", type=int, default=None,
+                    help="pre-growing helper teams of the cluster schedule (-1 = as many as "
+                         "fit, 0 = none)")
     ap.add_argument("--cpu-seconds", type=float, default=5.0,
                     help="bound of the oracle's full-recount sample timed beside the GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -128,7 +144,7 @@ def parse():
                     help="skip the batched-vs-plain comparison in the default line")
     ap.add_argument("--batched-updates", type=int, default=10000,
                     help="updates per replica of the batched comparison")
-    ap.add_argument("--plain-every", type=int, default=16,
+    ap.add_argument("--plain-every", type=int, default=8,
                     help="the default line's batched comparison runs its plain arm on every "
                          "k-th replica (--workload batched runs all)")
     ap.add_argument("--no-served", action="store_true",
@@ -433,8 +449,12 @@ def run_batched(args, n_replicas=512, updates=None, embed=False, plain_every=1):
     runner.close()
     for x in lat_b:
         x.close()
-    # plain: one lattice per launch (the library's default schedule), the same updates
-    plain_ix = list(range(0, n_replicas, max(1, plain_every)))
+    # plain: one lattice per launch (the library's default schedule), the same
+    # updates; a sample takes every k-th replica in (L, T) order (strata of
+    # size and temperature, which set a replica's cost)
+    order = sorted(range(n_replicas), key=lambda i: (specs[i]["L"], specs[i]["T"]))
+    k = max(1, plain_every)
+    plain_ix = sorted(order[k // 2::k]) if k > 1 else list(range(n_replicas))
     lat_p = [w.WolffLattice(specs[i]["dim"], specs[i]["L"], specs[i]["T"], seed=specs[i]["seed"])
              for i in plain_ix]
     bufs_p = [x.record_buffer(U) for x in lat_p]
@@ -471,8 +491,8 @@ def run_batched(args, n_replicas=512, updates=None, embed=False, plain_every=1):
                       "threads)" % ("cluster", plain_info.get("grid_blocks"),
                                      plain_info.get("block_threads")),
         "plain_sample": ("all %d replicas" % n_replicas if len(plain_ix) == n_replicas else
-                         "every %d-th replica (%d of %d), the full %d updates each; records "
-                         "compared with the batched arm's for those" % (
+                         "every %d-th replica in (L, T) order (%d of %d), the full %d updates "
+                         "each; records compared with the batched arm's for those" % (
                              plain_every, len(plain_ix), n_replicas, U)),
     }
     if embed:
@@ -716,6 +736,10 @@ def run_ising(args, name, stream_clocks=True):
         if args.t_up is not None:
             lat.set_local_thresholds(args.t_up, args.t_down if args.t_down is not None
                                      else args.t_up // 2)
+        if args.levels is not None:
+            lat.set_burst(args.levels)
+        if args.helpers is not None:
+            lat.set_helpers(args.helpers)
         info = lat.info()
         if wl["start"] == "ordered":
             lat.set_state(np.zeros(lat.N, dtype=np.int8) if wl.get("q") else
@@ -855,6 +879,7 @@ def run_ising(args, name, stream_clocks=True):
                    "schedule": args.schedule, "grid_blocks": info["grid_blocks"],
                    "t_up": args.t_up, "t_down": args.t_down,
                    "block_threads": info["block_threads"],
+                   "helper_clusters": info.get("helper_clusters"),
                    "l2": "256 MB buffer written between timed steps",
                    "parallelism": "replicas x%d" % world},
         "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,

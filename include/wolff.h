@@ -101,13 +101,17 @@ typedef struct {
     int      block_threads;
     int      sm_count;
     size_t   workspace_bytes;
+    int      helper_clusters;  /* pre-growing helper teams a wolff_step of the
+                                  cluster schedule launches beside the main one */
 } wolff_info;
 
 typedef struct wolff_ctx wolff_ctx;
 
 /* Bytes of device workspace a context of this shape needs (0 if the shape is
  * invalid).  The workspace holds the spin array, the cluster list (the ic/in
- * list of section 2, one 32-bit entry per site) and a small control block. */
+ * list of section 2, one 32-bit entry per site) and a small control block;
+ * lattices of 2^20 sites or more also get a 4 MiB ring of pre-grown updates
+ * (see wolff_set_helpers). */
 size_t wolff_workspace_bytes(int dim, int L, int layout);
 
 /* Creates a context on the current device and initialises the lattice from
@@ -296,6 +300,20 @@ wolff_status wolff_set_local_thresholds(wolff_ctx *ctx, uint32_t t_up, uint32_t 
  * (at most 64).  EINVAL if enable < 0. */
 wolff_status wolff_set_burst(wolff_ctx *ctx, int enable);
 
+/* Helper teams (cluster schedule, window mode on, lattices of 2^20 sites or
+ * more): a wolff_step launches, beside the cluster that runs the chain, as
+ * many more clusters of the same shape as the GPU holds at once.  They grow
+ * the launch's next updates ahead of it, on the lattice as they read it, into
+ * the workspace's ring; the main cluster takes such a result only if every
+ * spin its growth read -- the members, and each member's neighbours -- still
+ * has the value the growth saw, in which case it is the cluster the main
+ * cluster would grow itself (section 2's cluster depends only on those spins
+ * and on the counter-based bond draws); otherwise it grows the update.  The
+ * main cluster never waits for a helper, and results do not depend on the
+ * setting.  max_helpers: -1 = as many as fit (the default), 0 = none,
+ * k > 0 = at most k.  EINVAL if max_helpers < -1. */
+wolff_status wolff_set_helpers(wolff_ctx *ctx, int max_helpers);
+
 wolff_status wolff_get_info(wolff_ctx *ctx, wolff_info *info);
 
 /* Counters of the persistent and cluster schedules, accumulated since
@@ -319,6 +337,7 @@ typedef struct {
     uint64_t ns_win_check;     /*   conflict checks and the cut */
     uint64_t ns_win_commit;    /*   commits, records, regrowth queue */
     uint64_t win_levels;       /* growth levels run by all warps, discarded ones included */
+    uint64_t pregrown;         /* window updates taken from the helper teams' ring */
 } wolff_stats;
 
 /* Reads the counters above.  Synchronises. */

@@ -48,14 +48,15 @@ class _Info(ctypes.Structure):
                 ("thr", ctypes.c_uint64), ("seed", ctypes.c_uint64), ("t", ctypes.c_uint64),
                 ("schedule", ctypes.c_int), ("grid_blocks", ctypes.c_int),
                 ("block_threads", ctypes.c_int), ("sm_count", ctypes.c_int),
-                ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace_bytes", ctypes.c_size_t), ("helper_clusters", ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in
                 ("updates", "levels_local", "levels_grid", "ns_local", "ns_grid", "ns_finish",
                  "handoffs", "grid_finishes", "start_ns", "end_ns", "burst_updates", "bursts",
-                 "ns_win_grow", "ns_win_map", "ns_win_check", "ns_win_commit", "win_levels")]
+                 "ns_win_grow", "ns_win_map", "ns_win_check", "ns_win_commit", "win_levels",
+                 "pregrown")]
 
 
 _lib = None
@@ -102,6 +103,7 @@ def load_library():
         "wolff_set_local_thresholds": (i, [v, u32, u32]),
         "wolff_get_stats": (i, [v, P(_Stats)]),
         "wolff_set_burst": (i, [v, i]),
+        "wolff_set_helpers": (i, [v, i]),
         "wolff_batch_create": (i, [P(v), i, v]),
         "wolff_batch_run": (i, [v, v, i, v, v, i, i]),
         "wolff_batch_run_timed": (i, [v, v, i, v, v, i, i, u64]),
@@ -325,6 +327,11 @@ class WolffLattice:
         per commit round."""
         level = int(enable) if not isinstance(enable, bool) else (1 if enable else 0)
         _check(load_library().wolff_set_burst(self.handle, level), self.handle)
+
+    def set_helpers(self, max_helpers):
+        """Helper teams of the cluster schedule: -1 = as many as fit (the
+        default), 0 = none, k > 0 = at most k."""
+        _check(load_library().wolff_set_helpers(self.handle, int(max_helpers)), self.handle)
 
     def stats(self):
         st = _Stats()
@@ -556,6 +563,11 @@ class WolffXY:
             raise ValueError("need %d angles" % self.N)
         _check(load_library().xy_set_state(self.handle, theta.ctypes.data_as(ctypes.c_void_p),
                                            int(t)), self.handle)
+
+    def set_helpers(self, max_helpers):
+        """Helper teams of the cluster schedule: -1 = as many as fit (the
+        default), 0 = none, k > 0 = at most k."""
+        _check(load_library().wolff_set_helpers(self.handle, int(max_helpers)), self.handle)
 
     def stats(self):
         st = _Stats()

@@ -62,6 +62,12 @@ struct wolff_ctx {
     uint32_t t_up = 128, t_down = 64;
     bool thresholds_set = false;
     int win_levels = 0;   // window mode: growth levels per round (0 = off; set at init)
+    uint8_t *ring = nullptr;      // pre-grown updates (lattices of kRingMinSites or more)
+    int helpers_max = -1;         // helper teams: -1 = as many as fit, 0 = none, k = at most k
+    int helpers_fit = -1;         // clusters that fit beside the main team (-1 = not asked yet)
+    int helpers_fit_cluster = 0;  // ... for this cluster size and thread count
+    int helpers_fit_threads = 0;
+    uint32_t pg_epoch = 0;        // launches with helper teams so far
     int cluster = 8;
     int max_cluster = 8;
     std::string err;
@@ -119,6 +125,8 @@ StepParams make_params(const wolff_ctx *c) {
     p.t_up = c->t_up;
     p.t_down = c->t_down;
     p.win_levels = (uint32_t)c->win_levels;
+    p.ring = c->ring;
+    p.pg_epoch = c->pg_epoch;
     p.budget_ns = 0;
     p.q = c->q;
     p.xy_tab = c->xy_tab;
@@ -249,6 +257,25 @@ cudaError_t enqueue_ising_upload(wolff_ctx *c, const int8_t *h_spins, uint64_t t
     return e;
 }
 
+// Helper teams for a one-lattice cluster launch: the clusters that fit on the
+// GPU beside the main team, while window mode is on and the lattice has a
+// ring (and the launch's update count fits the helpers' 32-bit counters).
+int plain_helpers(wolff_ctx *c, uint64_t n_updates) {
+    if (!c->ring || c->potts || c->xy || c->win_levels == 0 || c->helpers_max == 0 ||
+        n_updates < 2 || n_updates >= (1ull << 31))
+        return 0;
+    if (c->helpers_fit < 0 || c->helpers_fit_cluster != c->cluster ||
+        c->helpers_fit_threads != c->threads) {
+        const int fit = team_max_active_clusters(c->dim, c->cluster, c->threads, kPlainWindowSlots);
+        c->helpers_fit = fit > 1 ? fit - 1 : 0;
+        c->helpers_fit_cluster = c->cluster;
+        c->helpers_fit_threads = c->threads;
+    }
+    int h = c->helpers_fit;
+    if (c->helpers_max > 0 && h > c->helpers_max) h = c->helpers_max;
+    return h;
+}
+
 int default_blocks(const wolff_ctx *c) {
     int b = (int)(c->N / 2048u);
     if (b < 1) b = 1;
@@ -279,10 +306,16 @@ uint64_t wolff_bond_threshold(double J, double T) {
     return (uint64_t)floor(ldexp(p, 32));
 }
 
+// The ring of pre-grown updates, on lattices large enough for helper teams.
+static size_t ring_bytes(size_t n) {
+    return n >= kRingMinSites ? (size_t)kRingSlots * kRingSlotBytes : 0;
+}
+
 size_t wolff_workspace_bytes(int dim, int L, int layout) {
     if (layout != WOLFF_LAYOUT_INT8 || !shape_ok(dim, L)) return 0;
     const size_t n = sites(dim, L);
-    return 2 * sizeof(DevCtl) + round_up(n, kAlign) + round_up(n * sizeof(uint32_t), kAlign);
+    return 2 * sizeof(DevCtl) + round_up(n, kAlign) + round_up(n * sizeof(uint32_t), kAlign) +
+           ring_bytes(n);
 }
 
 size_t wolff_xy_workspace_bytes(int dim, int L) {
@@ -391,6 +424,9 @@ static wolff_status init_common(wolff_ctx **out, int dim, int L, double J, doubl
     c->spins = reinterpret_cast<uint8_t *>(base + 2 * sizeof(DevCtl));
     const size_t spin_bytes = round_up(xy ? (size_t)c->N * sizeof(uint32_t) : c->N, kAlign);
     c->list = reinterpret_cast<uint32_t *>(base + 2 * sizeof(DevCtl) + spin_bytes);
+    if (!xy && ring_bytes(c->N))
+        c->ring = reinterpret_cast<uint8_t *>(base + 2 * sizeof(DevCtl) + spin_bytes +
+                                              round_up((size_t)c->N * sizeof(uint32_t), kAlign));
     if (xy) {
         char *tail = base + 2 * sizeof(DevCtl) + spin_bytes +
                      round_up((size_t)c->N * sizeof(uint32_t), kAlign);
@@ -406,6 +442,10 @@ static wolff_status init_common(wolff_ctx **out, int dim, int L, double J, doubl
     const StepParams p = make_params(c);
     e = cudaMemsetAsync(c->ws, 0, 2 * sizeof(DevCtl) + spin_bytes, c->stream);
     if (e == cudaSuccess) e = empty_list(c);
+    // no ring entry may survive from whatever used this memory before (a
+    // tag is unique only among this context's own launches)
+    if (e == cudaSuccess && c->ring)
+        e = cudaMemsetAsync(c->ring, 0, ring_bytes(c->N), c->stream);
     if (e == cudaSuccess) e = launch_reset_ctl(c->ctl, 0, c->stream);
     if (xy) {
         uint32_t *words = reinterpret_cast<uint32_t *>(c->spins);
@@ -496,6 +536,13 @@ wolff_status wolff_set_burst(wolff_ctx *c, int enable) {
     return WOLFF_OK;
 }
 
+wolff_status wolff_set_helpers(wolff_ctx *c, int max_helpers) {
+    if (!c) return WOLFF_EINVAL;
+    if (max_helpers < -1) return fail(c, WOLFF_EINVAL, "max_helpers must be >= -1");
+    c->helpers_max = max_helpers;
+    return WOLFF_OK;
+}
+
 wolff_status wolff_step(wolff_ctx *c, uint64_t n_updates, void *d_records) {
     if (!c) return WOLFF_EINVAL;
     if (n_updates == 0) return WOLFF_OK;
@@ -522,9 +569,13 @@ wolff_status wolff_step(wolff_ctx *c, uint64_t n_updates, void *d_records) {
         e = launch_potts_team(c->dim, p, c->cluster, c->threads, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "potts launch");
     } else if (c->schedule == WOLFF_SCHED_CLUSTER) {
-        e = launch_team(c->dim, p, nullptr, 1, c->cluster, c->threads, kPlainWindowSlots,
-                        c->stream);
+        const int helpers = plain_helpers(c, n_updates);
+        StepParams ph = p;
+        ph.pg_epoch = c->pg_epoch;
+        e = launch_team(c->dim, ph, nullptr, 1, c->cluster, c->threads, kPlainWindowSlots,
+                        c->stream, helpers);
         if (e != cudaSuccess) return cuda_fail(c, e, "cluster launch");
+        if (helpers) ++c->pg_epoch;
     } else if (c->schedule == WOLFF_SCHED_GRAPH) {
         if (!c->gexec) {
             e = build_update_graph(c->dim, p, c->blocks, c->threads, &c->gexec, &c->graph);
@@ -800,6 +851,7 @@ wolff_status wolff_get_info(wolff_ctx *c, wolff_info *info) {
     info->block_threads = c->threads;
     info->sm_count = c->sm_count;
     info->workspace_bytes = c->ws_bytes;
+    info->helper_clusters = plain_helpers(c, 2);
     return WOLFF_OK;
 }
 
@@ -825,6 +877,7 @@ wolff_status wolff_get_stats(wolff_ctx *c, wolff_stats *st) {
     st->ns_win_check = h.st_ns_win[2];
     st->ns_win_commit = h.st_ns_win[3];
     st->win_levels = h.st_win_levels;
+    st->pregrown = h.st_pregrown;
     return WOLFF_OK;
 }
 

@@ -215,6 +215,20 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned l
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// A spin byte read while another team of the launch may be writing it (the
+// pre-growing helpers read the lattice the main team commits to): relaxed
+// accesses at GPU scope, so each read returns a value some write stored.
+__device__ __forceinline__ uint32_t ld_relaxed_u8(const uint8_t *p) {
+    unsigned short v;
+    asm volatile("ld.relaxed.gpu.global.u8 %0, [%1];" : "=h"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u8(uint8_t *p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u8 [%0], %1;" ::"l"(p), "h"((unsigned short)v)
+                 : "memory");
+}
+
 __device__ __forceinline__ unsigned int ld_volatile_u32(const unsigned int *p) {
     return *reinterpret_cast<const volatile unsigned int *>(p);
 }

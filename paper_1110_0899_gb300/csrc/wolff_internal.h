@@ -85,6 +85,13 @@ struct alignas(256) DevCtl {
     // line 6: window-mode phase times (leader thread 0) and growth work
     alignas(128) unsigned long long st_ns_win[4];   // growth, map, check, commit
     unsigned long long st_win_levels;            // growth levels of all warps (incl. discarded)
+    unsigned long long st_pregrown;              // window updates taken pre-grown from the ring
+    // the pre-growing helper teams of a one-lattice launch, per launch parity
+    // (launch epoch & 1; a launch clears the other parity's words for the
+    // next one, which cannot start before it has ended)
+    unsigned int pg_next[2];                     // next update to pre-grow (atomic)
+    unsigned int pg_stop[2];                     // the launch's main team has finished
+    unsigned int pg_commit[2];                   // updates of the launch committed so far
 };
 static_assert(sizeof(DevCtl) % 256 == 0 && sizeof(DevCtl) <= 1024, "control block layout");
 
@@ -117,7 +124,30 @@ struct StepParams {
     double xy_kk;               // 2 J / T * 2^-60
     uint32_t xy_bits;           // angle grid: spins multiples of 2^(16-bits)
     wolff_xy_record *xy_records;
+    // pre-grown updates (one-lattice cluster launches with helper teams):
+    // ring of kRingSlots slots of kRingSlotBytes, nullable
+    uint8_t *ring;
+    uint32_t pg_epoch;          // launch counter of the context (its parity selects the words)
 };
+
+// The ring of pre-grown updates: update u of a launch (counted from the
+// launch's first update) goes to slot u mod kRingSlots.  A slot holds
+//   [0, 8)     tag: the launch's epoch << 32 | (u + 1), written last (release);
+//              the ring is zeroed when its context is created, so a tag is
+//              unique among the context's own launches
+//   [16, 32)   uint4 (|C|, levels, dE_bond / 2, seed spin); |C| = 0 marks an
+//              update too big to pre-grow
+//   [32, ...)  the members (packed coordinates, up to 128), then the three
+//              per-member bond masks of window mode (alignment, open, boundary),
+//              128 bytes each.
+constexpr uint32_t kRingSlots = 4096;
+constexpr uint32_t kRingSlotBytes = 1024;
+constexpr uint32_t kRingMembersOff = 32;
+constexpr uint32_t kRingMaxCap = 128;
+constexpr uint32_t kRingMasksOff = kRingMembersOff + 4 * kRingMaxCap;
+static_assert(kRingMasksOff + 3 * kRingMaxCap <= kRingSlotBytes, "ring slot layout");
+// lattices of at least this many sites get a ring (and helper teams)
+constexpr uint32_t kRingMinSites = 1u << 20;
 
 // Leader-local frontier capacity (shared memory) and the cluster-list prefix
 // kept in shared memory for the leader-only energy/unmark pass.
@@ -156,6 +186,8 @@ int persistent_max_blocks_per_sm(int dim, int threads, int *err);
 struct WinCfg {
     uint32_t slots;   // window slots per CTA (0: no window area, window mode off)
     uint32_t cap;     // members per speculative update
+    uint32_t helpers; // one-lattice launches: clusters after the first that pre-grow
+                      // updates into the ring (0 = none)
 };
 // Growth levels per warp between commit rounds, by dimension: the fastest of
 // 12, 16, 20, 24, 28, 32 and 48 on the 2D L=4096 and 3D L=256 random-start
@@ -168,7 +200,10 @@ cudaError_t ensure_team_dyn_smem(int dim, size_t bytes);
 uint32_t window_cap(int dim, int threads);
 size_t window_smem_bytes(int dim, int threads, int window_slots, int cluster_size);
 cudaError_t launch_team(int dim, const StepParams &single, const StepParams *d_table, int njobs,
-                        int cluster_size, int threads, int window_slots, cudaStream_t s);
+                        int cluster_size, int threads, int window_slots, cudaStream_t s,
+                        int helpers = 0);
+// Clusters of this shape that can be resident at once (0 if the query fails).
+int team_max_active_clusters(int dim, int cluster_size, int threads, int window_slots);
 
 // q-state Potts (wolff_potts.cu).
 cudaError_t launch_potts_init(uint8_t *spins, Geometry g, uint32_t q, uint32_t k0, uint32_t k1,

@@ -473,6 +473,8 @@ __global__ void k_reset_ctl(DevCtl *ctl, unsigned long long t) {
     ctl->st_bursts = 0;
     for (int k = 0; k < 4; ++k) ctl->st_ns_win[k] = 0;
     ctl->st_win_levels = 0;
+    ctl->st_pregrown = 0;
+    for (int k = 0; k < 2; ++k) ctl->pg_next[k] = ctl->pg_stop[k] = ctl->pg_commit[k] = 0;
 }
 
 // Before every persistent launch: command sequence, barrier word and

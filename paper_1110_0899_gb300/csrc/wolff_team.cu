@@ -361,19 +361,28 @@ __device__ __forceinline__ void prefetch_two_hop(const Geometry &g, const uint8_
     }
 }
 
+// A spin read of the growth: through L1 for the main team, whose lattice
+// changes only between its own cluster barriers; relaxed at GPU scope for a
+// pre-growing helper, which reads the lattice while the main team commits.
+template <bool kHelper>
+__device__ __forceinline__ uint32_t grow_read(const uint8_t *p) {
+    if constexpr (kHelper) return ld_relaxed_u8(p);
+    else return (uint32_t)__ldca(p);
+}
+
 // Warp: a fresh speculative growth of the update with seed site i0 (claimed
 // in the hash set).
-template <int DIM>
+template <int DIM, bool kHelper = false>
 __device__ __forceinline__ void win_start(const StepParams &p, uint32_t i0, uint32_t *members,
                                           uint32_t *hset, uint32_t hslots, uint32_t lane,
                                           uint32_t &n, uint32_t &lo, uint32_t &levels,
                                           uint32_t &sig0bit) {
     for (uint32_t k = lane; k < hslots; k += 32) hset[k] = kEmptyKey;
     __syncwarp();
-    sig0bit = __ldca(p.spins + i0) & 1u;
+    sig0bit = grow_read<kHelper>(p.spins + i0) & 1u;
     // the first level reads the rows next to the seed's (index +-L, and +-L^2
     // in 3D, taken mod N: a wrong line at a wrap only costs a prefetch)
-    if (lane < 2 * (DIM - 1)) {
+    if (!kHelper && lane < 2 * (DIM - 1)) {
         const uint32_t step = (lane >> 1) == 0 ? p.g.L : p.g.LL;
         const uint32_t N = p.g.N;
         const uint32_t nb = (lane & 1u) ? (i0 >= step ? i0 - step : i0 + N - step)
@@ -420,7 +429,7 @@ __device__ __forceinline__ void neighbour_of(const Geometry &g, uint32_t packed,
 // neighbour, evaluates the one Philox chain its bond draws from and tries
 // one claim, so a level costs the warp about one chain instead of D + 1.
 // Returns true when the cluster outgrew cap.
-template <int DIM>
+template <int DIM, bool kHelper = false>
 __device__ __forceinline__ bool win_level(const StepParams &p, uint32_t *members, uint8_t *amask,
                                           uint8_t *omask, uint32_t *hset, uint32_t hslots,
                                           uint32_t cap,
@@ -440,7 +449,7 @@ __device__ __forceinline__ bool win_level(const StepParams &p, uint32_t *members
         if (act) {
             uint32_t self, owner;
             neighbour_of<DIM>(p.g, members[k], s, self, j, pj, owner);
-            const uint8_t v = __ldca(p.spins + j);
+            const uint32_t v = grow_read<kHelper>(p.spins + j);
             Philox4 draw;
             philox4x32_10_lanes<1>(&owner, tlo, thi, kTagBond, p.key0, p.key1, &draw);
             const uint32_t d = s >> 1;
@@ -472,7 +481,7 @@ __device__ __forceinline__ bool win_level(const StepParams &p, uint32_t *members
             if (pos < cap) members[pos] = pj;
             // a member added along y or z expands next level into the row
             // beyond it (and, in 3D, the planes beside it): start those lines
-            if (s >= 2) prefetch_two_hop<DIM>(p.g, p.spins, j, s);
+            if (!kHelper && s >= 2) prefetch_two_hop<DIM>(p.g, p.spins, j, s);
         }
         n += __popc(fm);
         if (__any_sync(kFullMask, full) || n > cap) too_big = true;
@@ -516,6 +525,182 @@ __device__ __forceinline__ int win_boundary(const StepParams &p, const uint32_t 
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dE += __shfl_xor_sync(kFullMask, dE, o);
     return dE;
+}
+
+// ---- pre-grown updates -------------------------------------------------------
+// In a one-lattice launch the clusters after the first (the helpers) grow the
+// launch's updates ahead of the main team, in update order, on the lattice as
+// they read it while the main team commits, and leave each result in the ring
+// (see kRingSlots).  When the main team takes a fresh update it first looks
+// there: a result whose read set -- the members, which must still hold the
+// seed spin, and each member's neighbours, whose alignment with the seed spin
+// must still be what the growth read -- is unchanged on the lattice now is the
+// cluster the main team would grow (section 2's cluster depends only on those
+// spins and on the counter-based bond draws), with the same levels and
+// boundary sum.  The main team never waits for a helper; it grows whatever is
+// not there or no longer holds.
+
+__device__ __forceinline__ uint8_t *ring_slot(const StepParams &p, unsigned long long u) {
+    return p.ring + (size_t)(u % kRingSlots) * kRingSlotBytes;
+}
+
+// The tag of launch update u: the launch's epoch and u + 1, so that a result
+// left by an earlier launch (which may have run the same update indices from
+// a restored lattice) is never taken.
+__device__ __forceinline__ unsigned long long ring_tag(const StepParams &p, unsigned long long u) {
+    return ((unsigned long long)p.pg_epoch << 32) | (unsigned long long)(uint32_t)(u + 1);
+}
+
+// Warp (main team): takes the pre-grown result of launch update u into the
+// window slot (members, masks, meta) if it is there and its read set holds on
+// the current lattice.  Returns true if taken (every lane).
+template <int DIM>
+__device__ __forceinline__ bool take_pregrown(const StepParams &p, unsigned long long u,
+                                              uint32_t cap, uint32_t *members, uint8_t *amask,
+                                              uint8_t *omask, uint8_t *bmask, uint4 &meta,
+                                              uint32_t lane) {
+    constexpr uint32_t Z = 2 * DIM;
+    constexpr uint32_t PER = 32 / Z;
+    const uint8_t *slot = ring_slot(p, u);
+    unsigned long long tag = 0;
+    if (lane == 0) tag = ld_acquire_u64(reinterpret_cast<const unsigned long long *>(slot));
+    tag = __shfl_sync(kFullMask, tag, 0);
+    if (tag != ring_tag(p, u)) return false;
+    __syncwarp();   // every lane's reads below follow lane 0's acquire
+    meta = __ldcg(reinterpret_cast<const uint4 *>(slot + 16));
+    const uint32_t n = meta.x;
+    if (n == 0 || n > cap) return false;
+    const uint32_t *rm = reinterpret_cast<const uint32_t *>(slot + kRingMembersOff);
+    const uint8_t *ra = slot + kRingMasksOff;
+    for (uint32_t k = lane; k < n; k += 32) {
+        members[k] = __ldcg(rm + k);
+        amask[k] = __ldcg(ra + k);
+        omask[k] = __ldcg(ra + kRingMaxCap + k);
+        bmask[k] = __ldcg(ra + 2 * kRingMaxCap + k);
+    }
+    __syncwarp();
+    // the read set on the current lattice: one lane per (member, direction)
+    const uint32_t sig = meta.w;
+    const uint32_t km = lane / Z, s = lane % Z;
+    bool bad = false;
+    for (uint32_t b = 0; b < n; b += PER) {
+        const uint32_t k = b + km;
+        if (km < PER && k < n) {
+            uint32_t self, j, pj, owner;
+            neighbour_of<DIM>(p.g, members[k], s, self, j, pj, owner);
+            const bool par = (__ldca(p.spins + j) & 1u) == sig;
+            if (par != (((uint32_t)amask[k] >> s) & 1u)) bad = true;
+            if (s == 0 && (__ldca(p.spins + self) & 1u) != sig) bad = true;
+        }
+    }
+    return !__any_sync(kFullMask, bad);
+}
+
+// One thread (main team, at the start of a round): the same as take_pregrown
+// for a fresh update the round may hand out, so that the rounds' fresh
+// updates are taken side by side instead of one after another by each warp.
+// Clusters of more than kPrefillMax members are left to the warps.
+constexpr uint32_t kPrefillMax = 16;
+template <int DIM>
+__device__ __forceinline__ bool prefill_pregrown(const StepParams &p, unsigned long long u,
+                                                 uint32_t cap, uint32_t *members, uint8_t *amask,
+                                                 uint8_t *omask, uint8_t *bmask, uint4 &meta) {
+    const uint8_t *slot = ring_slot(p, u);
+    if (ld_acquire_u64(reinterpret_cast<const unsigned long long *>(slot)) != ring_tag(p, u))
+        return false;
+    meta = __ldcg(reinterpret_cast<const uint4 *>(slot + 16));
+    const uint32_t n = meta.x, sig = meta.w;
+    if (n == 0 || n > cap || n > kPrefillMax) return false;
+    const uint32_t *rm = reinterpret_cast<const uint32_t *>(slot + kRingMembersOff);
+    const uint8_t *ra = slot + kRingMasksOff;
+    bool bad = false;
+#pragma unroll 2
+    for (uint32_t k = 0; k < n; ++k) {
+        const uint32_t mk = __ldcg(rm + k);
+        const uint32_t a = __ldcg(ra + k);
+        members[k] = mk;
+        amask[k] = (uint8_t)a;
+        omask[k] = __ldcg(ra + kRingMaxCap + k);
+        bmask[k] = __ldcg(ra + 2 * kRingMaxCap + k);
+        uint32_t self;
+        Neighbours<DIM> nb;
+        neighbours<DIM>(p.g, mk, &self, nb);
+        uint32_t par = 0;
+#pragma unroll
+        for (int s = 0; s < 2 * DIM; ++s)
+            par |= (uint32_t)((__ldca(p.spins + nb.idx[s]) & 1u) == sig) << s;
+        if (par != a || (__ldca(p.spins + self) & 1u) != sig) bad = true;
+    }
+    return !bad;
+}
+
+// Helper teams: every warp pre-grows launch updates in order into the ring,
+// staying within kRingSlots updates of the main team's commits, until the
+// launch's updates are handed out or the main team has finished.  Waits are
+// bounded (the wait limit of the launch); a helper that gives up just stops:
+// nothing waits for it.
+template <int DIM>
+__device__ void team_helper(const StepParams &p, TeamShared &sh, const WinCfg &wc) {
+    extern __shared__ __align__(16) uint32_t win_dyn[];
+    const uint32_t W = min((uint32_t)(blockDim.x >> 5), (uint32_t)kWinMaxWarps);
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp >= W || p.ring == nullptr || wc.slots == 0) return;
+    const uint32_t cap = min(wc.cap, kRingMaxCap), hslots = 2 * wc.cap;
+    uint32_t *hset = &sh.front[0][0] + warp * hslots;
+    // per warp in the dynamic shared memory: members, then the three masks
+    const uint32_t stride = cap + (3 * cap + 3) / 4;
+    uint32_t *members = win_dyn + warp * stride;
+    uint8_t *am = reinterpret_cast<uint8_t *>(members + cap);
+    uint8_t *om = am + cap;
+    uint8_t *bm = om + cap;
+    DevCtl *ctl = p.ctl;
+    const uint32_t e = p.pg_epoch & 1u;
+    while (true) {
+        uint32_t u = 0, go = 1;
+        if (lane == 0) {
+            if (ld_volatile_u32(&ctl->pg_stop[e])) go = 0;
+            else u = atomicAdd(&ctl->pg_next[e], 1u);
+            if (go && u >= p.n) go = 0;
+            // stay within the ring: slot u mod R is free once the main team
+            // has committed update u - R
+            const unsigned long long w0 = global_ns();
+            while (go && u >= ld_volatile_u32(&ctl->pg_commit[e]) + kRingSlots) {
+                if (ld_volatile_u32(&ctl->pg_stop[e]) || global_ns() - w0 > p.wait_ns) go = 0;
+                else __nanosleep(8000);
+            }
+        }
+        go = __shfl_sync(kFullMask, go, 0);
+        if (!go) return;
+        u = __shfl_sync(kFullMask, u, 0);
+        const unsigned long long t = p.t0 + u;
+        uint32_t n, lo, levels, sig;
+        win_start<DIM, true>(p, seed_site(p, t), members, hset, hslots, lane, n, lo, levels, sig);
+        bool big = false;
+        while (lo < n && !big) {
+            big = win_level<DIM, true>(p, members, am, om, hset, hslots, cap, lane, lo, n, sig,
+                                       (uint32_t)t, (uint32_t)(t >> 32));
+            ++levels;
+        }
+        uint8_t *slot = ring_slot(p, u);
+        uint4 meta = make_uint4(0u, 0u, 0u, 0u);   // |C| = 0: too big to pre-grow
+        if (!big) {
+            const int dE = win_boundary<DIM>(p, members, am, bm, hset, hslots, n, lane);
+            meta = make_uint4(n, levels, (uint32_t)dE, sig);
+            uint32_t *rm = reinterpret_cast<uint32_t *>(slot + kRingMembersOff);
+            uint8_t *ra = slot + kRingMasksOff;
+            for (uint32_t k = lane; k < n; k += 32) {
+                rm[k] = members[k];
+                ra[k] = am[k];
+                ra[kRingMaxCap + k] = om[k];
+                ra[2 * kRingMaxCap + k] = bm[k];
+            }
+        }
+        if (lane == 0) *reinterpret_cast<uint4 *>(slot + 16) = meta;
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release_u64(reinterpret_cast<unsigned long long *>(slot), ring_tag(p, u));
+        __syncwarp();
+    }
 }
 
 // Lowest update index below `below` that flips a site of the closed
@@ -788,11 +973,26 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
             // (each slot a fresh update will take is free), their lines and
             // the rows their first level reads started towards L1, so that
             // a warp starting one finds them there
+            // With helper teams, a fresh update whose pre-grown result holds
+            // is taken here and then skipped by the warps.
             const uint32_t N = p.g.N, L = p.g.L;
             for (uint32_t q = v.scal[kScSeedLo] + threadIdx.x; q < v.scal[kScQEnd];
                  q += blockDim.x) {
-                const uint32_t i0 = seed_site(p, p.t0 + u0 + (unsigned long long)(q * cs + rank));
-                v.seed[q & (S - 1)] = i0;
+                const uint32_t jq = q * cs + rank, sq = q & (S - 1);
+                if (wc.helpers) {
+                    uint4 m;
+                    if (prefill_pregrown<DIM>(p, u0 + jq, cap, v.members + sq * cap,
+                                              v.amask + sq * cap, v.omask + sq * cap,
+                                              v.bmask + sq * cap, m)) {
+                        v.meta[sq] = m;
+                        v.j[sq] = jq;
+                        v.state[sq] = kSlotDone;
+                        atomicAdd(&p.ctl->st_pregrown, 1ull);
+                        continue;
+                    }
+                }
+                const uint32_t i0 = seed_site(p, p.t0 + u0 + (unsigned long long)jq);
+                v.seed[sq] = i0;
                 prefetch_l1(p.spins + i0);
                 prefetch_l1(p.spins + (i0 + L < N ? i0 + L : i0 + L - N));
                 prefetch_l1(p.spins + (i0 >= L ? i0 - L : i0 + N - L));
@@ -810,10 +1010,11 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
             rec_lo = rec_hi = 0;
         }
         if (warp < W) {
-            uint32_t steps = 0;
+            uint32_t steps = 0, pregrown = 0;
             while (steps < K) {
+                bool fresh = false;
                 if (!have) {
-                    uint32_t took = kNone, tj = 0;
+                    uint32_t took = kNone, tj = 0, fr = 0;
                     if (lane == 0) {
                         // the regrowth queue first (the queue only shrinks
                         // while warps grow, so a plain read may skip it)
@@ -833,9 +1034,15 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
                             while (q < q_end) {
                                 const uint32_t prev = atomicCAS(&v.scal[kScNextQ], q, q + 1);
                                 if (prev == q) {
-                                    took = q & (S - 1);
+                                    const uint32_t sq = q & (S - 1);
+                                    if (v.state[sq] == kSlotDone && v.j[sq] == q * cs + rank) {
+                                        ++q;   // taken pre-grown at the round's start
+                                        continue;
+                                    }
+                                    took = sq;
                                     tj = q * cs + rank;
                                     v.j[took] = tj;
+                                    fr = 1;
                                     break;
                                 }
                                 q = prev;
@@ -845,6 +1052,7 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
                     }
                     took = __shfl_sync(kFullMask, took, 0);
                     tj = __shfl_sync(kFullMask, tj, 0);
+                    fresh = __shfl_sync(kFullMask, fr, 0) != 0;
                     if (took == kNone) break;
                     g_slot = took;
                     g_j = tj;
@@ -853,6 +1061,23 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
                 }
                 const unsigned long long t = p.t0 + u0 + g_j;
                 uint32_t *members = v.members + g_slot * cap;
+                if (fresh && wc.helpers) {
+                    // a fresh update a helper has grown already, if it holds
+                    uint4 m;
+                    if (take_pregrown<DIM>(p, u0 + g_j, cap, members, v.amask + g_slot * cap,
+                                           v.omask + g_slot * cap, v.bmask + g_slot * cap, m,
+                                           lane)) {
+                        if (lane == 0) {
+                            v.meta[g_slot] = m;
+                            v.state[g_slot] = kSlotDone;
+                        }
+                        have = false;
+                        restart = false;
+                        ++steps;
+                        ++pregrown;
+                        continue;
+                    }
+                }
                 if (restart) {
                     win_start<DIM>(p, v.seed[g_slot], members, hset, hslots, lane, g_n, g_lo,
                                    g_levels, g_sig);
@@ -883,6 +1108,8 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
                 }
             }
             if (lane == 0 && steps) atomicAdd(&lead->wlevels, (unsigned long long)steps);
+            if (lane == 0 && pregrown)
+                atomicAdd(&p.ctl->st_pregrown, (unsigned long long)pregrown);
         }
         __syncthreads();
         // ---- flatten this CTA's finished updates: off[s] = members before slot s
@@ -946,13 +1173,16 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
         const uint32_t cut = ld_volatile_u32(&lead->wcut);
         const uint32_t wl = ld_volatile_u32(&lead->wlimit);
         const uint32_t stop = ld_volatile_u32(&lead->wstop);
+        if (wc.helpers && rank == 0 && threadIdx.x == 0)   // helpers may reuse slots below it
+            *reinterpret_cast<volatile unsigned int *>(&p.ctl->pg_commit[p.pg_epoch & 1u]) =
+                (uint32_t)(u0 + cut);
         // ---- commit [c, cut): flip the members (both bits), write records
         for (uint32_t f = threadIdx.x; f < total; f += blockDim.x) {
             const uint32_t s = flat_slot(v.off, S, f);
             if (v.j[s] < cut) {
                 uint32_t cc[DIM];
                 unpack<DIM>(v.members[s * cap + (f - v.off[s])], cc);
-                p.spins[site_index<DIM>(p.g, cc)] = v.meta[s].w ? 0x00 : 0x03;
+                st_relaxed_u8(p.spins + site_index<DIM>(p.g, cc), v.meta[s].w ? 0x00u : 0x03u);
             }
         }
         // the leader writes the records of [c, cut) at the start of the next
@@ -1082,8 +1312,18 @@ __device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_gro
     unsigned long long win_u0 = 0;
     uint32_t win_nrem = 0, win_next = 0;
     const unsigned long long launch_t0 = global_ns();
+    const uint32_t pg = p.pg_epoch & 1u;
+    if (wc.helpers && t0) {
+        // the next launch's helper words start from zero (it cannot start
+        // before this one has ended, helpers included)
+        ctl->pg_next[pg ^ 1u] = 0;
+        ctl->pg_stop[pg ^ 1u] = 0;
+        ctl->pg_commit[pg ^ 1u] = 0;
+    }
     unsigned long long u = 0;
     for (; u < p.n; ++u) {
+        if (wc.helpers && t0)
+            *reinterpret_cast<volatile unsigned int *>(&ctl->pg_commit[pg]) = (uint32_t)u;
         if (p.budget_ns && u > 0) {   // a time-budgeted job stops at an update boundary
             if (t0) sh.budget_stop = (global_ns() - launch_t0 > p.budget_ns) ? 1u : 0u;
             __syncthreads();
@@ -1290,6 +1530,7 @@ __device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_gro
         for (int k = 0; k < 4; ++k) ctl->st_ns_win[k] += win_ns[k];
         ctl->st_win_levels += win_ns[4];
         ctl->st_end_ns = global_ns();
+        if (wc.helpers) *reinterpret_cast<volatile unsigned int *>(&ctl->pg_stop[pg]) = 1u;
     }
     if (has_team) {
         announce(sh, cl, kTeamExit, 0, 0, 0, 0, 0);
@@ -1303,6 +1544,10 @@ __global__ void __launch_bounds__(512, 1) k_team(StepParams single, const StepPa
     cg::cluster_group cl = cg::this_cluster();
     __shared__ TeamShared sh;
     const unsigned int job = blockIdx.x / cl.num_blocks();
+    if (wc.helpers && job > 0) {   // a one-lattice launch's pre-growing helper team
+        team_helper<DIM>(single, sh, wc);
+        return;
+    }
     const StepParams p = table ? table[job] : single;
     if (cl.block_rank() != 0) {
         team_worker<DIM>(p, sh, cl, wc);
@@ -1361,8 +1606,12 @@ size_t window_smem_bytes(int dim, int threads, int window_slots, int cluster_siz
 }
 
 cudaError_t launch_team(int dim, const StepParams &single, const StepParams *d_table, int njobs,
-                        int cluster_size, int threads, int window_slots, cudaStream_t s) {
+                        int cluster_size, int threads, int window_slots, cudaStream_t s,
+                        int helpers) {
     if (njobs <= 0) return cudaSuccess;
+    if (helpers < 0 || (helpers > 0 && (d_table != nullptr || njobs != 1 || window_slots == 0 ||
+                                        single.ring == nullptr)))
+        return cudaErrorInvalidValue;
     if (window_slots < 0 || (window_slots & (window_slots - 1)) != 0 || window_slots > 1024)
         return cudaErrorInvalidValue;
     const void *fn = team_kernel(dim);
@@ -1382,13 +1631,14 @@ cudaError_t launch_team(int dim, const StepParams &single, const StepParams *d_t
     WinCfg wc;
     wc.slots = (uint32_t)window_slots;
     wc.cap = window_cap(dim, threads);
+    wc.helpers = (uint32_t)helpers;
     const size_t dyn = window_smem_bytes(dim, threads, window_slots, cluster_size);
     if (dyn > 0) {
         cudaError_t e = ensure_team_dyn_smem(dim, dyn);
         if (e != cudaSuccess) return e;
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(njobs * cluster_size));
+    cfg.gridDim = dim3((unsigned)((njobs + helpers) * cluster_size));
     cfg.blockDim = dim3((unsigned)threads);
     cfg.dynamicSmemBytes = dyn;
     cfg.stream = s;
@@ -1401,6 +1651,37 @@ cudaError_t launch_team(int dim, const StepParams &single, const StepParams *d_t
     cfg.numAttrs = 1;
     void *args[] = {const_cast<StepParams *>(&single), const_cast<StepParams **>(&d_table), &wc};
     return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+int team_max_active_clusters(int dim, int cluster_size, int threads, int window_slots) {
+    const void *fn = team_kernel(dim);
+    const size_t dyn = window_smem_bytes(dim, threads, window_slots, cluster_size);
+    if (cluster_size > 8 &&
+        cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (dyn > 0 && ensure_team_dyn_smem(dim, dyn) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)cluster_size);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = dyn;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cluster_size;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
 }
 
 }  // namespace wolff

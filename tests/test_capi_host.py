@@ -46,9 +46,15 @@ def test_threshold_matches_oracle(lib):
 def test_workspace_bytes(lib):
     import paper_1110_0899_gb300 as w
     n = 4096 * 4096
+    ring = 4096 * 1024   # pre-grown updates, lattices of 2^20 sites or more
     b = w.wolff_workspace_bytes(2, 4096)
-    assert b >= n + 4 * n and b <= n + 4 * n + 4096
+    assert b >= n + 4 * n + ring and b <= n + 4 * n + ring + 4096
     assert w.wolff_workspace_bytes(3, 256) == w.wolff_workspace_bytes(2, 4096)
+    small = 1023 * 1023
+    b = w.wolff_workspace_bytes(2, 1023)
+    assert small + 4 * small <= b <= small + 4 * small + 4096
+    b = w.wolff_workspace_bytes(2, 1024)
+    assert b >= 1024 * 1024 * 5 + ring
     for dim, L in ((1, 10), (4, 2), (2, 1), (2, 0), (3, 1025), (2, 40000)):
         assert w.wolff_workspace_bytes(dim, L) == 0
     assert w.wolff_workspace_bytes(2, 16, 7) == 0

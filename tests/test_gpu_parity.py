@@ -520,3 +520,42 @@ def test_whole_trajectory_in_segments(dim, L, T, seed):
     lat.close()
     assert t_end == snaps[-1][1] and np.array_equal(end, snaps[-1][0])
     assert np.array_equal(one, rec)
+
+
+@pytest.mark.parametrize("dim,L,T,seed,n", [(2, 1024, TC2, 41, 3000), (3, 102, 4.5115, 42, 3000),
+                                             (2, 2048, 2.4, 43, 2000), (2, 1024, 2.3, 44, 4000)])
+def test_helper_teams_keep_the_chain(dim, L, T, seed, n):
+    """One-lattice launches on lattices with a ring of pre-grown updates
+    (2^20 sites or more): the helper clusters grow updates ahead and the main
+    cluster takes those whose read set still holds.  Every record and the
+    final lattice must equal the oracle's; pre-grown results must have been
+    used; a second launch from the restored lattice (the benchmark's pattern:
+    the same update indices again) must give the same records without reusing
+    the first launch's results; and so must a launch without helpers."""
+    torch, w = require_cuda()
+    thr = oracle.bond_threshold(1.0, T)
+    s = oracle.init_lattice(dim, L, seed)
+    ref = oracle.run_local(dim, L, thr, seed, 0, n, s)
+    lat = w.WolffLattice(dim, L, T, seed=seed)
+    assert lat.info()["helper_clusters"] >= 1
+    start, _ = lat.get_state()
+    rec = lat.step(n)
+    st = lat.stats()
+    end, t_end = lat.get_state()
+    assert_records_equal(rec, ref, "helpers %dD L=%d T=%g" % (dim, L, T))
+    assert t_end == n and np.array_equal(end, s)
+    assert st["pregrown"] > 0 and st["burst_updates"] > 0, st
+    # the same updates again from the restored lattice
+    lat.set_state(start, 0)
+    rec2 = lat.step(n)
+    st2 = lat.stats()
+    assert np.array_equal(rec2, rec) and st2["pregrown"] > 0
+    # and without helper teams
+    lat.set_helpers(0)
+    assert lat.info()["helper_clusters"] == 0
+    lat.set_state(start, 0)
+    rec3 = lat.step(n)
+    assert lat.stats()["pregrown"] == 0
+    assert np.array_equal(rec3, rec)
+    assert np.array_equal(lat.get_state()[0], s)
+    lat.close()

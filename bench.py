@@ -59,16 +59,16 @@ TC2 = 2.0 / math.log(1.0 + math.sqrt(2.0))
 # cycles over its peak (4 per SM-cycle), on the SMs the launch kept active and
 # over the whole GPU, and its warp instructions per launch.
 TRAFFIC_CAPTURES = {
-    ("2d", 10000): {"src": "35704c4b61f6", "bytes_per_launch": 11246592 + 768,
-                    "l2_bytes_per_launch": 54157952,
-                    "imad": {"pipe_frac_active_sms": 8441756 / (4 * 13959321),
-                             "pipe_frac_gpu": 8441756 / (4 * 133400676),
-                             "warp_insts": 3501302}},
-    ("3d", 10000): {"src": "35704c4b61f6", "bytes_per_launch": 24321536 + 27648,
-                    "l2_bytes_per_launch": 117727776,
-                    "imad": {"pipe_frac_active_sms": 10871650 / (4 * 22075326),
-                             "pipe_frac_gpu": 10871650 / (4 * 210482946),
-                             "warp_insts": 4538094}},
+    ("2d", 10000): {"src": "c0c0630d03a7", "bytes_per_launch": 13850624 + 3328,
+                    "l2_bytes_per_launch": 78630976,
+                    "imad": {"pipe_frac_active_sms": 11390366 / (4 * 60469032),
+                             "pipe_frac_gpu": 11390366 / (4 * 105428630),
+                             "warp_insts": 4736445}},
+    ("3d", 10000): {"src": "c0c0630d03a7", "bytes_per_launch": 26904064 + 76288,
+                    "l2_bytes_per_launch": 142897984,
+                    "imad": {"pipe_frac_active_sms": 14415026 / (4 * 90865720),
+                             "pipe_frac_gpu": 14415026 / (4 * 192643526),
+                             "warp_insts": 6043087}},
 }
 
 

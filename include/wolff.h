@@ -338,6 +338,9 @@ typedef struct {
     uint64_t ns_win_commit;    /*   commits, records, regrowth queue */
     uint64_t win_levels;       /* growth levels run by all warps, discarded ones included */
     uint64_t pregrown;         /* window updates taken from the helper teams' ring */
+    uint64_t ns_win_first_grow; /* growth phase of each window's first round (leader's view) */
+    uint64_t win_regrown;      /* window updates grown again after a commit changed what they read */
+    uint64_t win_fresh_grown;  /* fresh window updates the main team grew itself */
 } wolff_stats;
 
 /* Reads the counters above.  Synchronises. */

@@ -56,7 +56,7 @@ class _Stats(ctypes.Structure):
                 ("updates", "levels_local", "levels_grid", "ns_local", "ns_grid", "ns_finish",
                  "handoffs", "grid_finishes", "start_ns", "end_ns", "burst_updates", "bursts",
                  "ns_win_grow", "ns_win_map", "ns_win_check", "ns_win_commit", "win_levels",
-                 "pregrown")]
+                 "pregrown", "ns_win_first_grow", "win_regrown", "win_fresh_grown")]
 
 
 _lib = None

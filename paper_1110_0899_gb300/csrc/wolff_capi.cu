@@ -276,6 +276,17 @@ int plain_helpers(wolff_ctx *c, uint64_t n_updates) {
     return h;
 }
 
+// How far ahead of the main team's commits the helpers grow: the whole ring.
+// Measured on the 10^4-update steps: a lead of the window plus a half or less
+// leaves helpers behind the main team (more updates grown twice), the full
+// ring was fastest in 2D and level in 3D.
+uint32_t helper_lead(const wolff_ctx *) { return kRingSlots; }
+
+// The main team's longest wait, at a launch's first window, for the helpers
+// to grow it (they start with the launch): 20 us, about their time for one
+// window's worth of updates.
+constexpr unsigned long long kHelperFirstWaitNs = 20000ull;
+
 int default_blocks(const wolff_ctx *c) {
     int b = (int)(c->N / 2048u);
     if (b < 1) b = 1;
@@ -572,6 +583,8 @@ wolff_status wolff_step(wolff_ctx *c, uint64_t n_updates, void *d_records) {
         const int helpers = plain_helpers(c, n_updates);
         StepParams ph = p;
         ph.pg_epoch = c->pg_epoch;
+        ph.pg_lead = helper_lead(c);
+        ph.pg_wait_ns = kHelperFirstWaitNs;
         e = launch_team(c->dim, ph, nullptr, 1, c->cluster, c->threads, kPlainWindowSlots,
                         c->stream, helpers);
         if (e != cudaSuccess) return cuda_fail(c, e, "cluster launch");
@@ -878,6 +891,9 @@ wolff_status wolff_get_stats(wolff_ctx *c, wolff_stats *st) {
     st->ns_win_commit = h.st_ns_win[3];
     st->win_levels = h.st_win_levels;
     st->pregrown = h.st_pregrown;
+    st->ns_win_first_grow = h.st_ns_win_first;
+    st->win_regrown = h.st_win_regrown;
+    st->win_fresh_grown = h.st_win_fresh_grown;
     return WOLFF_OK;
 }
 

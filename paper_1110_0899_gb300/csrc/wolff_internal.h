@@ -86,12 +86,16 @@ struct alignas(256) DevCtl {
     alignas(128) unsigned long long st_ns_win[4];   // growth, map, check, commit
     unsigned long long st_win_levels;            // growth levels of all warps (incl. discarded)
     unsigned long long st_pregrown;              // window updates taken pre-grown from the ring
+    unsigned long long st_ns_win_first;          // growth phase of each window's first round
+    unsigned long long st_win_regrown;           // window updates grown again (regrowth queue)
+    unsigned long long st_win_fresh_grown;       // fresh window updates the main team grew itself
     // the pre-growing helper teams of a one-lattice launch, per launch parity
     // (launch epoch & 1; a launch clears the other parity's words for the
     // next one, which cannot start before it has ended)
     unsigned int pg_next[2];                     // next update to pre-grow (atomic)
     unsigned int pg_stop[2];                     // the launch's main team has finished
     unsigned int pg_commit[2];                   // updates of the launch committed so far
+    unsigned int pg_done[2];                     // results the helpers have written (atomic)
 };
 static_assert(sizeof(DevCtl) % 256 == 0 && sizeof(DevCtl) <= 1024, "control block layout");
 
@@ -128,6 +132,8 @@ struct StepParams {
     // ring of kRingSlots slots of kRingSlotBytes, nullable
     uint8_t *ring;
     uint32_t pg_epoch;          // launch counter of the context (its parity selects the words)
+    uint32_t pg_lead;           // helpers grow update u only once u < committed + pg_lead
+    unsigned long long pg_wait_ns;  // main team: longest wait for the helpers' first window
 };
 
 // The ring of pre-grown updates: update u of a launch (counted from the

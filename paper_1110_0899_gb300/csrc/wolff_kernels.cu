@@ -474,7 +474,9 @@ __global__ void k_reset_ctl(DevCtl *ctl, unsigned long long t) {
     for (int k = 0; k < 4; ++k) ctl->st_ns_win[k] = 0;
     ctl->st_win_levels = 0;
     ctl->st_pregrown = 0;
-    for (int k = 0; k < 2; ++k) ctl->pg_next[k] = ctl->pg_stop[k] = ctl->pg_commit[k] = 0;
+    ctl->st_ns_win_first = ctl->st_win_regrown = ctl->st_win_fresh_grown = 0;
+    for (int k = 0; k < 2; ++k)
+        ctl->pg_next[k] = ctl->pg_stop[k] = ctl->pg_commit[k] = ctl->pg_done[k] = 0;
 }
 
 // Before every persistent launch: command sequence, barrier word and

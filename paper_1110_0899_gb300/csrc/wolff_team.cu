@@ -567,12 +567,24 @@ __device__ __forceinline__ bool take_pregrown(const StepParams &p, unsigned long
     tag = __shfl_sync(kFullMask, tag, 0);
     if (tag != ring_tag(p, u)) return false;
     __syncwarp();   // every lane's reads below follow lane 0's acquire
-    meta = __ldcg(reinterpret_cast<const uint4 *>(slot + 16));
-    const uint32_t n = meta.x;
-    if (n == 0 || n > cap) return false;
+    // the meta word and the first 32 members with their masks in one round
+    // trip (a lane past |C| reads bytes it then ignores)
     const uint32_t *rm = reinterpret_cast<const uint32_t *>(slot + kRingMembersOff);
     const uint8_t *ra = slot + kRingMasksOff;
-    for (uint32_t k = lane; k < n; k += 32) {
+    meta = __ldcg(reinterpret_cast<const uint4 *>(slot + 16));
+    const uint32_t mk = __ldcg(rm + lane);
+    const uint32_t ak = __ldcg(ra + lane);
+    const uint32_t ok = __ldcg(ra + kRingMaxCap + lane);
+    const uint32_t bk = __ldcg(ra + 2 * kRingMaxCap + lane);
+    const uint32_t n = meta.x;
+    if (n == 0 || n > cap) return false;
+    if (lane < n) {
+        members[lane] = mk;
+        amask[lane] = (uint8_t)ak;
+        omask[lane] = (uint8_t)ok;
+        bmask[lane] = (uint8_t)bk;
+    }
+    for (uint32_t k = lane + 32; k < n; k += 32) {
         members[k] = __ldcg(rm + k);
         amask[k] = __ldcg(ra + k);
         omask[k] = __ldcg(ra + kRingMaxCap + k);
@@ -585,53 +597,17 @@ __device__ __forceinline__ bool take_pregrown(const StepParams &p, unsigned long
     bool bad = false;
     for (uint32_t b = 0; b < n; b += PER) {
         const uint32_t k = b + km;
+        // the first pass takes the member from the lane that loaded it
+        const uint32_t mem = __shfl_sync(kFullMask, mk, km);
         if (km < PER && k < n) {
             uint32_t self, j, pj, owner;
-            neighbour_of<DIM>(p.g, members[k], s, self, j, pj, owner);
+            neighbour_of<DIM>(p.g, b == 0 ? mem : members[k], s, self, j, pj, owner);
             const bool par = (__ldca(p.spins + j) & 1u) == sig;
             if (par != (((uint32_t)amask[k] >> s) & 1u)) bad = true;
             if (s == 0 && (__ldca(p.spins + self) & 1u) != sig) bad = true;
         }
     }
     return !__any_sync(kFullMask, bad);
-}
-
-// One thread (main team, at the start of a round): the same as take_pregrown
-// for a fresh update the round may hand out, so that the rounds' fresh
-// updates are taken side by side instead of one after another by each warp.
-// Clusters of more than kPrefillMax members are left to the warps.
-constexpr uint32_t kPrefillMax = 16;
-template <int DIM>
-__device__ __forceinline__ bool prefill_pregrown(const StepParams &p, unsigned long long u,
-                                                 uint32_t cap, uint32_t *members, uint8_t *amask,
-                                                 uint8_t *omask, uint8_t *bmask, uint4 &meta) {
-    const uint8_t *slot = ring_slot(p, u);
-    if (ld_acquire_u64(reinterpret_cast<const unsigned long long *>(slot)) != ring_tag(p, u))
-        return false;
-    meta = __ldcg(reinterpret_cast<const uint4 *>(slot + 16));
-    const uint32_t n = meta.x, sig = meta.w;
-    if (n == 0 || n > cap || n > kPrefillMax) return false;
-    const uint32_t *rm = reinterpret_cast<const uint32_t *>(slot + kRingMembersOff);
-    const uint8_t *ra = slot + kRingMasksOff;
-    bool bad = false;
-#pragma unroll 2
-    for (uint32_t k = 0; k < n; ++k) {
-        const uint32_t mk = __ldcg(rm + k);
-        const uint32_t a = __ldcg(ra + k);
-        members[k] = mk;
-        amask[k] = (uint8_t)a;
-        omask[k] = __ldcg(ra + kRingMaxCap + k);
-        bmask[k] = __ldcg(ra + 2 * kRingMaxCap + k);
-        uint32_t self;
-        Neighbours<DIM> nb;
-        neighbours<DIM>(p.g, mk, &self, nb);
-        uint32_t par = 0;
-#pragma unroll
-        for (int s = 0; s < 2 * DIM; ++s)
-            par |= (uint32_t)((__ldca(p.spins + nb.idx[s]) & 1u) == sig) << s;
-        if (par != a || (__ldca(p.spins + self) & 1u) != sig) bad = true;
-    }
-    return !bad;
 }
 
 // Helper teams: every warp pre-grows launch updates in order into the ring,
@@ -664,9 +640,9 @@ __device__ void team_helper(const StepParams &p, TeamShared &sh, const WinCfg &w
             // stay within the ring: slot u mod R is free once the main team
             // has committed update u - R
             const unsigned long long w0 = global_ns();
-            while (go && u >= ld_volatile_u32(&ctl->pg_commit[e]) + kRingSlots) {
+            while (go && u >= ld_volatile_u32(&ctl->pg_commit[e]) + p.pg_lead) {
                 if (ld_volatile_u32(&ctl->pg_stop[e]) || global_ns() - w0 > p.wait_ns) go = 0;
-                else __nanosleep(8000);
+                else __nanosleep(4000);
             }
         }
         go = __shfl_sync(kFullMask, go, 0);
@@ -698,7 +674,10 @@ __device__ void team_helper(const StepParams &p, TeamShared &sh, const WinCfg &w
         if (lane == 0) *reinterpret_cast<uint4 *>(slot + 16) = meta;
         __threadfence();
         __syncwarp();
-        if (lane == 0) st_release_u64(reinterpret_cast<unsigned long long *>(slot), ring_tag(p, u));
+        if (lane == 0) {
+            st_release_u64(reinterpret_cast<unsigned long long *>(slot), ring_tag(p, u));
+            atomicAdd(&ctl->pg_done[e], 1u);
+        }
         __syncwarp();
     }
 }
@@ -932,6 +911,14 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
         if (warp == 0) win_queue(v, S, c, rank, cs, lane);
     }
     if (threadIdx.x == 0) v.off[S] = 0;   // no stamps to clear before the first round
+    if (wc.helpers && u0 == 0 && !resume && threadIdx.x == 0) {
+        // the launch's first window: give the helpers a moment (bounded) to
+        // grow it, instead of growing all of it here while they start
+        const unsigned int want = min(n_rem, S * cs);
+        const unsigned int *done = &p.ctl->pg_done[p.pg_epoch & 1u];
+        const unsigned long long w0 = global_ns();
+        while (ld_volatile_u32(done) < want && global_ns() - w0 < p.pg_wait_ns) __nanosleep(500);
+    }
     __syncthreads();
     // this warp's update in progress (registers, kept across rounds)
     bool have = false, restart = false;
@@ -939,6 +926,7 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
     const bool timer = win_ns != nullptr && rank == 0 && threadIdx.x == 0;
     unsigned long long tick = timer ? global_ns() : 0;
     uint32_t stall = 0;
+    bool first_round = true;
     uint32_t rec_lo = 0, rec_hi = 0;   // committed updates whose records are pending
     resumable = false;
     while (true) {
@@ -973,26 +961,11 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
             // (each slot a fresh update will take is free), their lines and
             // the rows their first level reads started towards L1, so that
             // a warp starting one finds them there
-            // With helper teams, a fresh update whose pre-grown result holds
-            // is taken here and then skipped by the warps.
             const uint32_t N = p.g.N, L = p.g.L;
             for (uint32_t q = v.scal[kScSeedLo] + threadIdx.x; q < v.scal[kScQEnd];
                  q += blockDim.x) {
-                const uint32_t jq = q * cs + rank, sq = q & (S - 1);
-                if (wc.helpers) {
-                    uint4 m;
-                    if (prefill_pregrown<DIM>(p, u0 + jq, cap, v.members + sq * cap,
-                                              v.amask + sq * cap, v.omask + sq * cap,
-                                              v.bmask + sq * cap, m)) {
-                        v.meta[sq] = m;
-                        v.j[sq] = jq;
-                        v.state[sq] = kSlotDone;
-                        atomicAdd(&p.ctl->st_pregrown, 1ull);
-                        continue;
-                    }
-                }
-                const uint32_t i0 = seed_site(p, p.t0 + u0 + (unsigned long long)jq);
-                v.seed[sq] = i0;
+                const uint32_t i0 = seed_site(p, p.t0 + u0 + (unsigned long long)(q * cs + rank));
+                v.seed[q & (S - 1)] = i0;
                 prefetch_l1(p.spins + i0);
                 prefetch_l1(p.spins + (i0 + L < N ? i0 + L : i0 + L - N));
                 prefetch_l1(p.spins + (i0 >= L ? i0 - L : i0 + N - L));
@@ -1010,7 +983,7 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
             rec_lo = rec_hi = 0;
         }
         if (warp < W) {
-            uint32_t steps = 0, pregrown = 0;
+            uint32_t steps = 0, pregrown = 0, regrown = 0, grown = 0;
             while (steps < K) {
                 bool fresh = false;
                 if (!have) {
@@ -1034,12 +1007,7 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
                             while (q < q_end) {
                                 const uint32_t prev = atomicCAS(&v.scal[kScNextQ], q, q + 1);
                                 if (prev == q) {
-                                    const uint32_t sq = q & (S - 1);
-                                    if (v.state[sq] == kSlotDone && v.j[sq] == q * cs + rank) {
-                                        ++q;   // taken pre-grown at the round's start
-                                        continue;
-                                    }
-                                    took = sq;
+                                    took = q & (S - 1);
                                     tj = q * cs + rank;
                                     v.j[took] = tj;
                                     fr = 1;
@@ -1054,6 +1022,7 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
                     tj = __shfl_sync(kFullMask, tj, 0);
                     fresh = __shfl_sync(kFullMask, fr, 0) != 0;
                     if (took == kNone) break;
+                    if (!fresh) ++regrown;
                     g_slot = took;
                     g_j = tj;
                     have = true;
@@ -1079,6 +1048,7 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
                     }
                 }
                 if (restart) {
+                    if (fresh) ++grown;
                     win_start<DIM>(p, v.seed[g_slot], members, hset, hslots, lane, g_n, g_lo,
                                    g_levels, g_sig);
                     restart = false;
@@ -1110,6 +1080,10 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
             if (lane == 0 && steps) atomicAdd(&lead->wlevels, (unsigned long long)steps);
             if (lane == 0 && pregrown)
                 atomicAdd(&p.ctl->st_pregrown, (unsigned long long)pregrown);
+            if (lane == 0 && regrown)
+                atomicAdd(&p.ctl->st_win_regrown, (unsigned long long)regrown);
+            if (lane == 0 && grown)
+                atomicAdd(&p.ctl->st_win_fresh_grown, (unsigned long long)grown);
         }
         __syncthreads();
         // ---- flatten this CTA's finished updates: off[s] = members before slot s
@@ -1120,7 +1094,12 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
             v.dcorr[k] = 0;
         }
         cl.sync();   // every stamp is clear, every CTA has grown and flattened
-        if (timer) win_tick(win_ns[0], tick);
+        if (timer) {
+            const unsigned long long before = win_ns[0];
+            win_tick(win_ns[0], tick);
+            if (first_round) win_ns[5] += win_ns[0] - before;
+        }
+        first_round = false;
         // ---- stamp the flips of the finished updates: list[i] = lowest one
         const uint32_t total = v.off[S];
         for (uint32_t f = threadIdx.x; f < total; f += blockDim.x) {
@@ -1305,7 +1284,8 @@ __device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_gro
     // recent clusters are small; a cluster too big for one pauses them
     unsigned int cooldown = 0, fail_streak = 0, skip_next = 0;
     unsigned long long window_updates = 0, window_rounds = 0;
-    unsigned long long win_ns[5] = {0, 0, 0, 0, 0};
+    // growth, map, check, commit, growth levels, first round's growth
+    unsigned long long win_ns[6] = {0, 0, 0, 0, 0, 0};
     // an open window (left for an update too big for it) resumes at
     // update win_u0 + win_next
     bool win_open = false;
@@ -1319,6 +1299,7 @@ __device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_gro
         ctl->pg_next[pg ^ 1u] = 0;
         ctl->pg_stop[pg ^ 1u] = 0;
         ctl->pg_commit[pg ^ 1u] = 0;
+        ctl->pg_done[pg ^ 1u] = 0;
     }
     unsigned long long u = 0;
     for (; u < p.n; ++u) {
@@ -1529,6 +1510,7 @@ __device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_gro
         ctl->st_bursts += window_rounds;
         for (int k = 0; k < 4; ++k) ctl->st_ns_win[k] += win_ns[k];
         ctl->st_win_levels += win_ns[4];
+        ctl->st_ns_win_first += win_ns[5];
         ctl->st_end_ns = global_ns();
         if (wc.helpers) *reinterpret_cast<volatile unsigned int *>(&ctl->pg_stop[pg]) = 1u;
     }

@@ -523,7 +523,10 @@ def test_whole_trajectory_in_segments(dim, L, T, seed):
 
 
 @pytest.mark.parametrize("dim,L,T,seed,n", [(2, 1024, TC2, 41, 3000), (3, 102, 4.5115, 42, 3000),
-                                             (2, 2048, 2.4, 43, 2000), (2, 1024, 2.3, 44, 4000)])
+                                             (2, 2048, 2.4, 43, 2000), (2, 1024, 2.3, 44, 4000),
+                                             # larger clusters: pre-grown updates are often
+                                             # invalidated by earlier commits and grown again
+                                             (2, 1024, 2.29, 45, 12000), (3, 102, 4.45, 46, 8000)])
 def test_helper_teams_keep_the_chain(dim, L, T, seed, n):
     """One-lattice launches on lattices with a ring of pre-grown updates
     (2^20 sites or more): the helper clusters grow updates ahead and the main

@@ -59,16 +59,16 @@ TC2 = 2.0 / math.log(1.0 + math.sqrt(2.0))
 # cycles over its peak (4 per SM-cycle), on the SMs the launch kept active and
 # over the whole GPU, and its warp instructions per launch.
 TRAFFIC_CAPTURES = {
-    ("2d", 10000): {"src": "c0c0630d03a7", "bytes_per_launch": 13850624 + 3328,
-                    "l2_bytes_per_launch": 78630976,
-                    "imad": {"pipe_frac_active_sms": 11390366 / (4 * 60469032),
-                             "pipe_frac_gpu": 11390366 / (4 * 105428630),
-                             "warp_insts": 4736445}},
-    ("3d", 10000): {"src": "c0c0630d03a7", "bytes_per_launch": 26904064 + 76288,
-                    "l2_bytes_per_launch": 142897984,
-                    "imad": {"pipe_frac_active_sms": 14415026 / (4 * 90865720),
-                             "pipe_frac_gpu": 14415026 / (4 * 192643526),
-                             "warp_insts": 6043087}},
+    ("2d", 10000): {"src": "51eb3b4790d5", "bytes_per_launch": 13852672 + 3584,
+                    "l2_bytes_per_launch": 78752704,
+                    "imad": {"pipe_frac_active_sms": 11430974 / (4 * 58708693),
+                             "pipe_frac_gpu": 11430974 / (4 * 104286586),
+                             "warp_insts": 4756479}},
+    ("3d", 10000): {"src": "51eb3b4790d5", "bytes_per_launch": 26899200 + 68352,
+                    "l2_bytes_per_launch": 143025376,
+                    "imad": {"pipe_frac_active_sms": 14462874 / (4 * 86595258),
+                             "pipe_frac_gpu": 14462874 / (4 * 177619726),
+                             "warp_insts": 6066481}},
 }
 
 

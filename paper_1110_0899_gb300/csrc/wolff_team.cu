@@ -984,7 +984,16 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
         }
         if (warp < W) {
             uint32_t steps = 0, pregrown = 0, regrown = 0, grown = 0;
+            // an update far beyond the window's head is not needed for this
+            // round's commit (rounds commit about 800 updates): its warp
+            // pauses after K / 3 levels and goes on next round, so that one
+            // deep update far out does not make the whole round wait.  "Far"
+            // is past 3/4 of the window in 2D and past half of it in 3D, the
+            // fastest of 1/2, 3/4 and 5/4 on the 10^4-update steps
+            const uint32_t far_from = c + (DIM == 2 ? (3u * P) / 4u : P / 2u);
+            const uint32_t k_far = max(K / 3u, 2u);
             while (steps < K) {
+                if (have && g_j >= far_from && steps >= k_far) break;
                 bool fresh = false;
                 if (!have) {
                     uint32_t took = kNone, tj = 0, fr = 0;

@@ -15,7 +15,9 @@ Default run (N=1), one JSON line:
     the same replicas one lattice per launch, records compared;
   - "served": the 200-request Poisson trace through the continuous-batching
     server for a bounded window, latency percentiles over every request
-    (unfinished ones censored at the window's end).
+    (unfinished ones censored at the window's end);
+  - "small": 2D L=16, seed 1, the whole 10^4-update run on the GPU and by
+    the oracle, records compared.
 
 value = sum of cluster sizes over the timed updates / device time of the
 timed steps (CUDA events on the lattice's stream, an L2 flush of 256 MB
@@ -895,6 +897,48 @@ def run_ising(args, name, stream_clocks=True):
     }
 
 
+def run_small(args):
+    """The small configuration, whole run on both sides: 2D L=16, J=1,
+    T = T_c, Philox random start from seed 1, 10^4 updates with every record,
+    timed on the GPU (one launch, CUDA events, after warm-up runs from the
+    same start) and by the oracle (one core); the records are compared."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1110_0899_gb300 as w
+    dim, L, T, seed, n = 2, 16, TC2, 1, 10000
+    lat = w.WolffLattice(dim, L, T, seed=seed)
+    start, _ = lat.get_state()
+    buf = lat.record_buffer(n)
+    stream_times = []
+    for k in range(max(3, args.warmup) + max(3, args.steps)):
+        lat.set_state(start, 0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        w.wolff_step(lat.handle, n, buf)
+        b.record()
+        b.synchronize()
+        if k >= max(3, args.warmup):
+            stream_times.append(a.elapsed_time(b) / 1000.0)
+    rec = w.records_to_numpy(buf, n)
+    lat.close()
+    thr = oracle.bond_threshold(1.0, T)
+    s = oracle.init_lattice(dim, L, seed)
+    t0 = time.perf_counter()
+    ref = oracle.run(dim, L, thr, seed, 0, n, s)
+    t_orc = time.perf_counter() - t0
+    flips = int(rec["C"].astype(np.int64).sum())
+    t_gpu = float(np.median(stream_times))
+    return {"workload": "2D L=16 T=%.6g J=1 seed 1, random start, 10^4 updates with records, "
+                        "the whole run on both sides" % T,
+            "gpu_flips_per_s": flips / t_gpu, "gpu_ms": 1000.0 * t_gpu,
+            "oracle_flips_per_s": flips / t_orc, "oracle_ms": 1000.0 * t_orc,
+            "oracle": "E_bond and M recounted from their definitions after every update, one core",
+            "records_equal_oracle": bool(np.array_equal(rec, ref)),
+            "mean_cluster": flips / n}
+
+
 def add_l2_side(line, l2):
     """The L2 side of a line's roofline: the same algorithmic bytes against
     the probe's L2 read bandwidth, and the ncu L2 bytes when fresh."""
@@ -951,6 +995,8 @@ def main():
         if world > 1:
             torch.distributed.destroy_process_group()
         return
+    if headline:
+        line["small"] = run_small(args)
     if headline and not args.no_batched:
         class _A:   # the specified batched workload: 10^4 updates per replica
             steps, updates_per_step = 1, args.batched_updates

@@ -682,6 +682,18 @@ __device__ void team_helper(const StepParams &p, TeamShared &sh, const WinCfg &w
     }
 }
 
+// Warp: a finished update j stamps its flips into the site map,
+// list[i] = lowest finished update of the window that flips i.
+template <int DIM>
+__device__ __forceinline__ void win_stamp(const StepParams &p, const uint32_t *members, uint32_t n,
+                                          uint32_t j, uint32_t lane) {
+    for (uint32_t k = lane; k < n; k += 32) {
+        uint32_t cc[DIM];
+        unpack<DIM>(members[k], cc);
+        atomicMin(p.list + site_index<DIM>(p.g, cc), j);
+    }
+}
+
 // Lowest update index below `below` that flips a site of the closed
 // neighbourhood of the member `packed` (kNone if none).  The flips of the
 // finished updates are stamped into the cluster-list array, which window mode
@@ -910,7 +922,7 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
         __syncthreads();
         if (warp == 0) win_queue(v, S, c, rank, cs, lane);
     }
-    if (threadIdx.x == 0) v.off[S] = 0;   // no stamps to clear before the first round
+
     if (wc.helpers && u0 == 0 && !resume && threadIdx.x == 0) {
         // the launch's first window: give the helpers a moment (bounded) to
         // grow it, instead of growing all of it here while they start
@@ -931,15 +943,18 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
     resumable = false;
     while (true) {
         const uint32_t lim = min(n_rem, c + P);
-        // ---- clear the previous round's stamps (every read of them ended at
-        // the last cluster barrier; the slots keep their members until taken)
+        // ---- the finished updates still in the window stamp their flips
+        // again (the last commit phase cleared every stamp); updates that
+        // finish during this round's growth stamp theirs when they finish
+        if (warp == 0) win_flatten(v, S, lane);
+        __syncthreads();
         {
             const uint32_t total = v.off[S];
             for (uint32_t f = threadIdx.x; f < total; f += blockDim.x) {
                 const uint32_t s = flat_slot(v.off, S, f);
                 uint32_t cc[DIM];
                 unpack<DIM>(v.members[s * cap + (f - v.off[s])], cc);
-                p.list[site_index<DIM>(p.g, cc)] = kEmptySlot;
+                atomicMin(p.list + site_index<DIM>(p.g, cc), v.j[s]);
             }
         }
         // ---- growth: K levels per warp; fresh updates stop at the first
@@ -984,13 +999,17 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
         }
         if (warp < W) {
             uint32_t steps = 0, pregrown = 0, regrown = 0, grown = 0;
-            // an update far beyond the window's head is not needed for this
-            // round's commit (rounds commit about 800 updates): its warp
-            // pauses after K / 3 levels and goes on next round, so that one
-            // deep update far out does not make the whole round wait.  "Far"
-            // is past 3/4 of the window in 2D and past half of it in 3D, the
-            // fastest of 1/2, 3/4 and 5/4 on the 10^4-update steps
-            const uint32_t far_from = c + (DIM == 2 ? (3u * P) / 4u : P / 2u);
+            // with helper teams, an update far beyond the window's head is not
+            // needed for this round's commit (rounds commit about 800
+            // updates): its warp pauses after K / 3 levels and goes on next
+            // round, so that one deep update far out -- typically a pre-grown
+            // result a commit invalidated -- does not make the whole round
+            // wait.  "Far" is past 3/4 of the window in 2D and past half of it
+            // in 3D, the fastest of 1/2, 3/4 and 5/4 on the 10^4-update steps.
+            // Without helpers every update is grown here and pausing the far
+            // ones only leaves them unfinished when the cut reaches them.
+            const uint32_t far_from =
+                wc.helpers ? c + (DIM == 2 ? (3u * P) / 4u : P / 2u) : 0xFFFFFFFFu;
             const uint32_t k_far = max(K / 3u, 2u);
             while (steps < K) {
                 if (have && g_j >= far_from && steps >= k_far) break;
@@ -1049,6 +1068,7 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
                             v.meta[g_slot] = m;
                             v.state[g_slot] = kSlotDone;
                         }
+                        win_stamp<DIM>(p, members, m.x, g_j, lane);
                         have = false;
                         restart = false;
                         ++steps;
@@ -1082,6 +1102,7 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
                         v.meta[g_slot] = make_uint4(g_n, g_levels, (uint32_t)dE, g_sig);
                         v.state[g_slot] = kSlotDone;
                     }
+                    win_stamp<DIM>(p, members, g_n, g_j, lane);
                     have = false;
                     ++steps;
                 }
@@ -1102,23 +1123,15 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
             v.amin[k] = kNone;
             v.dcorr[k] = 0;
         }
-        cl.sync();   // every stamp is clear, every CTA has grown and flattened
+        cl.sync();   // every finished update has stamped its flips, every CTA has flattened
         if (timer) {
             const unsigned long long before = win_ns[0];
             win_tick(win_ns[0], tick);
             if (first_round) win_ns[5] += win_ns[0] - before;
         }
         first_round = false;
-        // ---- stamp the flips of the finished updates: list[i] = lowest one
+        if (timer) win_tick(win_ns[1], tick);   // (no separate stamping phase)
         const uint32_t total = v.off[S];
-        for (uint32_t f = threadIdx.x; f < total; f += blockDim.x) {
-            const uint32_t s = flat_slot(v.off, S, f);
-            uint32_t cc[DIM];
-            unpack<DIM>(v.members[s * cap + (f - v.off[s])], cc);
-            atomicMin(p.list + site_index<DIM>(p.g, cc), v.j[s]);
-        }
-        cl.sync();
-        if (timer) win_tick(win_ns[1], tick);
         // ---- conflicts: the lowest earlier update whose flips change each
         // finished update's cluster, and the corrections of its boundary sum
         for (uint32_t f = threadIdx.x; f < total; f += blockDim.x) {
@@ -1132,6 +1145,15 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
             if (rel != kNone) atomicMin(&v.cmin[s], rel);
             if (any != kNone) atomicMin(&v.amin[s], any);
             if (delta) atomicAdd(&v.dcorr[s], delta);
+        }
+        // an update still growing: the lowest update that flips a site it
+        // read (it starts again if that one commits)
+        uint32_t g_min = kNone;
+        if (warp < W && have && !restart) {
+            const uint32_t *members = v.members + g_slot * cap;
+            for (uint32_t k = lane; k < g_n && k < cap; k += 32)
+                g_min = min(g_min, read_conflict<DIM>(p, members[k], kNone));
+            g_min = __reduce_min_sync(kFullMask, g_min);
         }
         __syncthreads();
         {
@@ -1164,14 +1186,16 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
         if (wc.helpers && rank == 0 && threadIdx.x == 0)   // helpers may reuse slots below it
             *reinterpret_cast<volatile unsigned int *>(&p.ctl->pg_commit[p.pg_epoch & 1u]) =
                 (uint32_t)(u0 + cut);
-        // ---- commit [c, cut): flip the members (both bits), write records
+        // ---- commit [c, cut): flip the members (both bits), write records;
+        // every stamp is cleared (every read of them ended at the last cluster
+        // barrier); the finished updates that stay stamp again next round
         for (uint32_t f = threadIdx.x; f < total; f += blockDim.x) {
             const uint32_t s = flat_slot(v.off, S, f);
-            if (v.j[s] < cut) {
-                uint32_t cc[DIM];
-                unpack<DIM>(v.members[s * cap + (f - v.off[s])], cc);
-                st_relaxed_u8(p.spins + site_index<DIM>(p.g, cc), v.meta[s].w ? 0x00u : 0x03u);
-            }
+            uint32_t cc[DIM];
+            unpack<DIM>(v.members[s * cap + (f - v.off[s])], cc);
+            const uint32_t site = site_index<DIM>(p.g, cc);
+            p.list[site] = kEmptySlot;
+            if (v.j[s] < cut) st_relaxed_u8(p.spins + site, v.meta[s].w ? 0x00u : 0x03u);
         }
         // the leader writes the records of [c, cut) at the start of the next
         // round (or on leaving), off this phase's critical path, from the
@@ -1197,13 +1221,7 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
             }
         }
         // an update still growing that read a committed flip starts again
-        if (warp < W && have && !restart && cut > c) {
-            bool hit = false;
-            const uint32_t *members = v.members + g_slot * cap;
-            for (uint32_t k = lane; k < g_n && k < cap; k += 32)
-                if (read_conflict<DIM>(p, members[k], cut) != kNone) hit = true;
-            if (__any_sync(kFullMask, hit)) restart = true;
-        }
+        if (warp < W && have && !restart && cut > c && g_min < cut) restart = true;
         __syncthreads();
         if (warp == 0) win_queue(v, S, cut, rank, cs, lane);
         ++rounds;
@@ -1235,16 +1253,8 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
     }
     if (rank == 0 && rec_hi > rec_lo)
         win_records(p, sh, cl, v, S, cs, u0, rec_lo, rec_hi, E, M, total_C, last_C, last_levels);
-    // leave the cluster list empty, and ordered before whatever uses it next
-    {
-        const uint32_t total = v.off[S];
-        for (uint32_t f = threadIdx.x; f < total; f += blockDim.x) {
-            const uint32_t s = flat_slot(v.off, S, f);
-            uint32_t cc[DIM];
-            unpack<DIM>(v.members[s * cap + (f - v.off[s])], cc);
-            p.list[site_index<DIM>(p.g, cc)] = kEmptySlot;
-        }
-    }
+    // the cluster list is empty (the last commit phase cleared every stamp);
+    // order that before whatever uses it next
     cl.sync();
     if (timer) win_ns[4] += sh.wlevels;
     return c;

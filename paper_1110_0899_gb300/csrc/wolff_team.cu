@@ -66,6 +66,15 @@ constexpr uint32_t kWinCap = 64;            // members per speculative update (s
 constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint32_t kWinMaxStall = 4096;     // rounds without a commit before giving up
+// Windows that commit fewer than kWinLowYield updates per round are left for
+// the ordinary path, with the longest back-off: judged over kWinLowRounds
+// rounds in a row within one call, and over the rounds of all windows since
+// the last back-off (halved every 64 rounds, so that recent ones weigh most)
+// once those reach kWinLowRounds.  This is the regime of small lattices near
+// T_c, where nearly every update conflicts with the one before it and most
+// windows soon stop at an update too big for them.
+constexpr uint32_t kWinLowYield = 2;
+constexpr uint32_t kWinLowRounds = 8;
 enum : uint32_t { kSlotFree = 0, kSlotGrowing = 1, kSlotDone = 2, kSlotTooBig = 3, kSlotRegrow = 4 };
 
 struct TeamShared {
@@ -80,6 +89,7 @@ struct TeamShared {
     unsigned int wlimit;        // lowest update found too big (atomic)
     unsigned int wstop;         // time budget spent
     unsigned int wflag;         // leader: this update starts (or resumes) a window
+    unsigned int wlowy;         // leader: the last window was left for committing too little
     unsigned int budget_stop;   // leader: the time budget stops the launch here
     unsigned int wlast[2];      // |C| and levels of the last committed update
     unsigned long long wlevels; // growth levels of all warps (atomic)
@@ -937,7 +947,7 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
     uint32_t g_slot = 0, g_j = 0, g_lo = 0, g_n = 0, g_levels = 0, g_sig = 0;
     const bool timer = win_ns != nullptr && rank == 0 && threadIdx.x == 0;
     unsigned long long tick = timer ? global_ns() : 0;
-    uint32_t stall = 0;
+    uint32_t stall = 0, low_rounds = 0;
     bool first_round = true;
     uint32_t rec_lo = 0, rec_hi = 0;   // committed updates whose records are pending
     resumable = false;
@@ -1235,11 +1245,14 @@ __device__ uint32_t team_window(const StepParams &p, TeamShared &sh, cg::cluster
         const bool finished = cut >= n_rem;
         const bool blocked = !finished && (cut == wl || stuck);
         const bool stopped = stop != 0 && u0 + cut > 0;
+        low_rounds = cut - c < kWinLowYield ? low_rounds + 1 : 0;
+        const bool low = !finished && !blocked && low_rounds >= kWinLowRounds;
         cl.sync();   // commits visible, every read of the stamps done
         if (timer) win_tick(win_ns[3], tick);
         c = cut;
-        if (finished || blocked || stopped) {
+        if (finished || blocked || stopped || low) {
             resumable = blocked && !stuck && !stopped;
+            if (rank == 0 && threadIdx.x == 0) sh.wlowy = low ? 1u : 0u;
             break;
         }
     }
@@ -1310,6 +1323,7 @@ __device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_gro
     bool win_open = false;
     unsigned long long win_u0 = 0;
     uint32_t win_nrem = 0, win_next = 0;
+    unsigned long long life_rounds = 0, life_done = 0;   // windows' rounds and commits since the last back-off
     const unsigned long long launch_t0 = global_ns();
     const uint32_t pg = p.pg_epoch & 1u;
     if (wc.helpers && t0) {
@@ -1344,6 +1358,7 @@ __device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_gro
                     sh.wlimit = kNone;
                     sh.wstop = 0;
                     sh.wlevels = 0;
+                    sh.wlowy = 0;
                 }
                 if (has_team)
                     announce(sh, cl, kTeamWindow, (uint32_t)u0w, (uint32_t)(u0w >> 32), n_rem,
@@ -1351,13 +1366,27 @@ __device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_gro
                 else
                     __syncthreads();
                 bool resumable = false;
+                const unsigned long long rounds0 = window_rounds;
                 const uint32_t c =
                     team_window<DIM>(p, sh, cl, wc, u0w, n_rem, launch_t0, E, M, total_C, last_C,
                                      last_levels, window_rounds, win_ns, c_start, resume,
                                      resumable);
                 const uint32_t done = c - c_start;
-                // a resumed window that commits nothing is closed
-                win_open = resumable && !(resume && done == 0);
+                life_rounds += window_rounds - rounds0;
+                life_done += done;
+                const bool low_life = life_rounds >= kWinLowRounds &&
+                                      life_done < (unsigned long long)kWinLowYield * life_rounds;
+                if (low_life) {
+                    life_rounds = life_done = 0;
+                } else if (life_rounds >= 64) {   // recent windows weigh most
+                    life_rounds >>= 1;
+                    life_done >>= 1;
+                }
+                if (t0 && low_life) sh.wlowy = 1u;
+                __syncthreads();
+                // a resumed window that commits nothing is closed, and so is
+                // one that commits too little per round
+                win_open = resumable && !(resume && done == 0) && !sh.wlowy;
                 win_u0 = u0w;
                 win_nrem = n_rem;
                 win_next = c + 1;
@@ -1365,8 +1394,14 @@ __device__ void team_leader(const StepParams &p, TeamShared &sh, cg::cluster_gro
                     window_updates += done;
                     if (done > 0 && c < n_rem && !sh.wstop) skip_next = 1;
                     // back off only while fresh windows keep failing at their
-                    // first update (the large-cluster regime): 0, 1, 3, ..., 63
-                    if (done == 0 && !resume) {
+                    // first update (the large-cluster regime): 0, 1, 3, ..., 63;
+                    // a window left for committing too little per round backs
+                    // off the longest way at once
+                    if (sh.wlowy) {
+                        fail_streak = 7u;
+                        cooldown = 63u;
+                        skip_next = 0;
+                    } else if (done == 0 && !resume) {
                         fail_streak = min(fail_streak + 1u, 7u);
                         cooldown = (1u << (fail_streak - 1u)) - 1u;
                     } else if (done > 0) {

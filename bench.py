@@ -61,16 +61,16 @@ TC2 = 2.0 / math.log(1.0 + math.sqrt(2.0))
 # cycles over its peak (4 per SM-cycle), on the SMs the launch kept active and
 # over the whole GPU, and its warp instructions per launch.
 TRAFFIC_CAPTURES = {
-    ("2d", 10000): {"src": "51eb3b4790d5", "bytes_per_launch": 13852672 + 3584,
-                    "l2_bytes_per_launch": 78752704,
-                    "imad": {"pipe_frac_active_sms": 11430974 / (4 * 58708693),
-                             "pipe_frac_gpu": 11430974 / (4 * 104286586),
-                             "warp_insts": 4756479}},
-    ("3d", 10000): {"src": "51eb3b4790d5", "bytes_per_launch": 26899200 + 68352,
-                    "l2_bytes_per_launch": 143025376,
-                    "imad": {"pipe_frac_active_sms": 14462874 / (4 * 86595258),
-                             "pipe_frac_gpu": 14462874 / (4 * 177619726),
-                             "warp_insts": 6066481}},
+    ("2d", 10000): {"src": "33841569bb9d", "bytes_per_launch": 13863680 + 3840,
+                    "l2_bytes_per_launch": 77944608,
+                    "imad": {"pipe_frac_active_sms": 11263374 / (4 * 59999668),
+                             "pipe_frac_gpu": 11263374 / (4 * 105378528),
+                             "warp_insts": 4664897}},
+    ("3d", 10000): {"src": "33841569bb9d", "bytes_per_launch": 26908160 + 73216,
+                    "l2_bytes_per_launch": 142192224,
+                    "imad": {"pipe_frac_active_sms": 13885302 / (4 * 83580008),
+                             "pipe_frac_gpu": 13885302 / (4 * 171567756),
+                             "warp_insts": 5771816}},
 }
 
 
@@ -152,6 +152,8 @@ def parse():
     ap.add_argument("--no-served", action="store_true",
                     help="skip the serving run in the default line")
     ap.add_argument("--no-l2-probe", action="store_true")
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the small configuration (2D L=16) in the default line")
     ap.add_argument("--embed-serve-seconds", type=float, default=30.0)
     return ap.parse_args()
 
@@ -995,7 +997,7 @@ def main():
         if world > 1:
             torch.distributed.destroy_process_group()
         return
-    if headline:
+    if headline and not args.no_small:
         line["small"] = run_small(args)
     if headline and not args.no_batched:
         class _A:   # the specified batched workload: 10^4 updates per replica

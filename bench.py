@@ -911,6 +911,7 @@ def run_small(args):
     import paper_1110_0899_gb300 as w
     dim, L, T, seed, n = 2, 16, TC2, 1, 10000
     lat = w.WolffLattice(dim, L, T, seed=seed)
+    info = lat.info()
     start, _ = lat.get_state()
     buf = lat.record_buffer(n)
     stream_times = []
@@ -938,7 +939,12 @@ def run_small(args):
             "oracle_flips_per_s": flips / t_orc, "oracle_ms": 1000.0 * t_orc,
             "oracle": "E_bond and M recounted from their definitions after every update, one core",
             "records_equal_oracle": bool(np.array_equal(rec, ref)),
-            "mean_cluster": flips / n}
+            "mean_cluster": flips / n,
+            "mean_levels": float(rec["levels"].mean()),
+            "gpu_us_per_update": 1e6 * t_gpu / n,
+            "schedule": {w.SCHED_TINY: "tiny: one CTA of %d threads, the lattice in shared "
+                                       "memory as bit planes" % info["block_threads"]}.get(
+                info["schedule"], "schedule %d" % info["schedule"])}
 
 
 def add_l2_side(line, l2):

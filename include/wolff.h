@@ -69,16 +69,36 @@ enum { WOLFF_LAYOUT_INT8 = 0 };
  *   CLUSTER     one thread-block cluster (1..16 CTAs) per lattice: CTA 0
  *               grows small fronts alone, larger ones are shared by the
  *               cluster with the hardware cluster barrier between levels;
- *   AUTO        the library's choice: CLUSTER with the largest cluster the
- *               GPU launches (16 where non-portable sizes are allowed, else
- *               8), 512 threads, t_up = 128, t_down = 64, window mode on (the
- *               default). */
+ *   TINY        Ising lattices of at most WOLFF_TINY_MAX_SITES sites: one CTA
+ *               holds the whole lattice in shared memory for the launch, as
+ *               bit planes (each row of L sites in ceil(L/32) 32-bit words);
+ *               a breadth-first level computes the next wave front of every
+ *               word with shifts and masks, and E_bond, M are recounted with
+ *               population counts after each flip.  Lattices of at most 64
+ *               words (2D L <= 32, 3D L <= 8) with 64 threads or more: warp 0
+ *               runs the update alone (__syncwarp per level) while the
+ *               other warps draw the next update's bond randomness; larger
+ *               ones: every thread grows one or two words (__syncthreads per
+ *               level).  The paper's CPU/GPU hybrid (section 5) starts small
+ *               clusters on the CPU; here a small lattice never leaves one
+ *               SM.  grid_blocks must be 0 or 1; block_threads from 32 to
+ *               1024, at least half the lattice's words unless warp 0 runs
+ *               alone (EINVAL otherwise);
+ *   AUTO        the library's choice: TINY for Ising lattices of at most
+ *               WOLFF_TINY_MAX_SITES sites (it was the fastest at every such
+ *               size measured), else CLUSTER with the largest cluster the GPU
+ *               launches (16 where non-portable sizes are allowed, else 8),
+ *               512 threads, t_up = 128, t_down = 64, window mode on.  A new
+ *               context starts on AUTO's choice; AUTO with grid_blocks > 1 or
+ *               a block_threads TINY cannot use means CLUSTER. */
 enum {
     WOLFF_SCHED_AUTO = 0,
     WOLFF_SCHED_PERSISTENT = 1,
     WOLFF_SCHED_GRAPH = 2,
-    WOLFF_SCHED_CLUSTER = 3
+    WOLFF_SCHED_CLUSTER = 3,
+    WOLFF_SCHED_TINY = 4
 };
+#define WOLFF_TINY_MAX_SITES 32768
 
 /* One record per update, written after the update's flip
  * (section 5, the "+ measurement" column of Tables 1-2). */
@@ -273,8 +293,11 @@ wolff_status wolff_run_host_bits(wolff_ctx *ctx, const uint32_t *h_bits_in, uint
  * library default).  For PERSISTENT and GRAPH grid_blocks is the number of
  * CTAs (PERSISTENT caps it at what can be co-resident); for CLUSTER it is the
  * cluster size (1, 2, 4, 8 or 16; 16 needs a GPU that allows non-portable
- * cluster sizes).  block_threads: a multiple of 32, at most 512 for PERSISTENT
- * and CLUSTER, 1024 for GRAPH.  Results do not depend on the choice. */
+ * cluster sizes); for TINY it must be 0 or 1.  block_threads: a multiple of
+ * 32, at most 512 for PERSISTENT and CLUSTER, 1024 for GRAPH and TINY (see
+ * TINY above for its lower bound).  TINY on a Potts or XY context, or on a
+ * lattice of more than WOLFF_TINY_MAX_SITES sites, is EUNSUPPORTED.  Results
+ * do not depend on the choice. */
 wolff_status wolff_set_schedule(wolff_ctx *ctx, int schedule, int grid_blocks,
                                 int block_threads);
 

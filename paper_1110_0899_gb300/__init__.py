@@ -21,7 +21,8 @@ WOLFF_OK, WOLFF_EINVAL, WOLFF_ENOMEM, WOLFF_ECUDA, WOLFF_ETIMEOUT, WOLFF_EUNSUPP
 STATUS_NAMES = {0: "WOLFF_OK", 1: "WOLFF_EINVAL", 2: "WOLFF_ENOMEM", 3: "WOLFF_ECUDA",
                 4: "WOLFF_ETIMEOUT", 5: "WOLFF_EUNSUPPORTED"}
 LAYOUT_INT8 = 0
-SCHED_AUTO, SCHED_PERSISTENT, SCHED_GRAPH, SCHED_CLUSTER = 0, 1, 2, 3
+SCHED_AUTO, SCHED_PERSISTENT, SCHED_GRAPH, SCHED_CLUSTER, SCHED_TINY = 0, 1, 2, 3, 4
+TINY_MAX_SITES = 32768     # WOLFF_TINY_MAX_SITES
 
 RECORD_DTYPE = np.dtype([("C", "<u4"), ("levels", "<u4"), ("E", "<i8"), ("M", "<i8")])
 RECORD_BYTES = RECORD_DTYPE.itemsize  # 24

@@ -51,6 +51,7 @@ struct wolff_ctx {
     int sm_count = 0;
     int schedule = WOLFF_SCHED_CLUSTER;
     int blocks = 0, threads = 256;
+    int tiny_threads = 256;        // CTA size of the tiny schedule
     int graph_blocks = 0, graph_threads = 0;
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
@@ -80,6 +81,18 @@ constexpr size_t kAlign = 256;
 // cluster size 16; the batched form keeps its CTAs small
 constexpr int kPlainWindowSlots = 128;
 constexpr int kBatchWindowSlots = 64;
+// tiny schedule default CTA, the fastest of 32..1024 threads on 2D L = 16..181
+// and 3D L = 8..32 at T_c: warp 0 and three drawing warps for lattices of at
+// most 64 words; else 256 threads up to 192 words, 512 up to 1024 words (two
+// words per thread beyond 512: fewer warps at the level barrier beat one
+// word per thread), and the fewest that hold two words each beyond that
+int tiny_default_threads(int dim, int L) {
+    const uint32_t nw = tiny_words_of(dim, L);
+    if (nw <= 64u) return 128;
+    if (nw <= 192u) return 256;
+    if (nw <= 1024u) return 512;
+    return (int)(((nw + 1u) / 2u + 31u) / 32u * 32u);
+}
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -93,6 +106,12 @@ uint32_t sites(int dim, int L) {
     uint64_t n = 1;
     for (int d = 0; d < dim; ++d) n *= (uint64_t)L;
     return (uint32_t)n;
+}
+
+// AUTO's choice: the tiny schedule for small Ising lattices, else CLUSTER.
+int auto_schedule(const wolff_ctx *c) {
+    return (!c->potts && !c->xy && c->N <= WOLFF_TINY_MAX_SITES) ? WOLFF_SCHED_TINY
+                                                               : WOLFF_SCHED_CLUSTER;
 }
 
 wolff_status fail(wolff_ctx *c, wolff_status s, const char *msg) {
@@ -449,6 +468,10 @@ static wolff_status init_common(wolff_ctx **out, int dim, int L, double J, doubl
     c->threads = 512;
     c->max_cluster = max_cluster_size(dim, c->threads);
     c->cluster = c->max_cluster;
+    if (auto_schedule(c) == WOLFF_SCHED_TINY) {
+        c->schedule = WOLFF_SCHED_TINY;
+        c->tiny_threads = tiny_default_threads(dim, L);
+    }
 
     const StepParams p = make_params(c);
     e = cudaMemsetAsync(c->ws, 0, 2 * sizeof(DevCtl) + spin_bytes, c->stream);
@@ -494,7 +517,7 @@ static wolff_status init_common(wolff_ctx **out, int dim, int L, double J, doubl
 
 wolff_status wolff_set_schedule(wolff_ctx *c, int schedule, int grid_blocks, int block_threads) {
     if (!c) return WOLFF_EINVAL;
-    if (schedule < WOLFF_SCHED_AUTO || schedule > WOLFF_SCHED_CLUSTER)
+    if (schedule < WOLFF_SCHED_AUTO || schedule > WOLFF_SCHED_TINY)
         return fail(c, WOLFF_EINVAL, "unknown schedule");
     if (schedule == WOLFF_SCHED_CLUSTER && grid_blocks != 0 && grid_blocks != 1 &&
         grid_blocks != 2 && grid_blocks != 4 && grid_blocks != 8 && grid_blocks != 16)
@@ -502,7 +525,26 @@ wolff_status wolff_set_schedule(wolff_ctx *c, int schedule, int grid_blocks, int
     if (block_threads != 0 && (block_threads < 32 || block_threads > 1024 || block_threads % 32))
         return fail(c, WOLFF_EINVAL, "block_threads must be a multiple of 32 in [32, 1024]");
     if (grid_blocks < 0) return fail(c, WOLFF_EINVAL, "grid_blocks must be >= 0");
-    const int sched_eff = schedule == WOLFF_SCHED_AUTO ? WOLFF_SCHED_CLUSTER : schedule;
+    // AUTO keeps to CLUSTER when the shape asked for is not a tiny one
+    const bool tiny_shape = grid_blocks <= 1 &&
+                            (block_threads == 0 || tiny_shape_ok(c->dim, c->L, block_threads));
+    const int sched_eff = schedule != WOLFF_SCHED_AUTO ? schedule
+                          : tiny_shape               ? auto_schedule(c)
+                                                     : WOLFF_SCHED_CLUSTER;
+    if (sched_eff == WOLFF_SCHED_TINY) {
+        if (c->potts || c->xy)
+            return fail(c, WOLFF_EUNSUPPORTED, "the tiny schedule runs the Ising update only");
+        if (c->N > kTinyMaxSites)
+            return fail(c, WOLFF_EUNSUPPORTED, "the tiny schedule takes at most 32768 sites");
+        if (grid_blocks > 1) return fail(c, WOLFF_EINVAL, "the tiny schedule runs one CTA");
+        const int thr = block_threads ? block_threads : tiny_default_threads(c->dim, c->L);
+        if (!tiny_shape_ok(c->dim, c->L, thr))
+            return fail(c, WOLFF_EINVAL,
+                        "the tiny schedule needs a thread per two words of the lattice");
+        c->schedule = WOLFF_SCHED_TINY;
+        c->tiny_threads = thr;
+        return WOLFF_OK;
+    }
     if (c->potts && sched_eff != WOLFF_SCHED_CLUSTER)
         return fail(c, WOLFF_EUNSUPPORTED, "the Potts update runs on the cluster schedule only");
     if (c->xy && sched_eff != WOLFF_SCHED_CLUSTER)
@@ -579,6 +621,9 @@ wolff_status wolff_step(wolff_ctx *c, uint64_t n_updates, void *d_records) {
     } else if (c->potts) {
         e = launch_potts_team(c->dim, p, c->cluster, c->threads, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "potts launch");
+    } else if (c->schedule == WOLFF_SCHED_TINY) {
+        e = launch_tiny(c->dim, p, nullptr, 1, c->L, c->tiny_threads, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "tiny launch");
     } else if (c->schedule == WOLFF_SCHED_CLUSTER) {
         const int helpers = plain_helpers(c, n_updates);
         StepParams ph = p;
@@ -860,8 +905,10 @@ wolff_status wolff_get_info(wolff_ctx *c, wolff_info *info) {
     info->seed = c->seed;
     info->t = c->t_host;
     info->schedule = c->schedule;
-    info->grid_blocks = c->schedule == WOLFF_SCHED_CLUSTER ? c->cluster : c->blocks;
-    info->block_threads = c->threads;
+    info->grid_blocks = c->schedule == WOLFF_SCHED_CLUSTER ? c->cluster
+                        : c->schedule == WOLFF_SCHED_TINY  ? 1
+                                                           : c->blocks;
+    info->block_threads = c->schedule == WOLFF_SCHED_TINY ? c->tiny_threads : c->threads;
     info->sm_count = c->sm_count;
     info->workspace_bytes = c->ws_bytes;
     info->helper_clusters = plain_helpers(c, 2);

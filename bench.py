@@ -152,6 +152,8 @@ def parse():
     ap.add_argument("--no-served", action="store_true",
                     help="skip the serving run in the default line")
     ap.add_argument("--no-l2-probe", action="store_true")
+    ap.add_argument("--no-tiny-engine", action="store_true",
+                    help="served form: run every lattice on the team engine (no tiny engine)")
     ap.add_argument("--no-small", action="store_true",
                     help="skip the small configuration (2D L=16) in the default line")
     ap.add_argument("--embed-serve-seconds", type=float, default=30.0)
@@ -478,7 +480,13 @@ def run_batched(args, n_replicas=512, updates=None, embed=False, plain_every=1):
             flips_p += int(r["C"].astype(np.int64).sum())
             same = same and np.array_equal(r, recs_b[k][i])
     t_p = sum(a.elapsed_time(b) for a, b in ev) / 1000.0
-    plain_info = lat_p[0].info() if lat_p else {}
+    plain_scheds = {}
+    for x in lat_p:
+        inf = x.info()
+        key = ("tiny (one CTA of %d threads)" % inf["block_threads"]
+               if inf["schedule"] == w.SCHED_TINY else
+               "cluster (%d CTAs x %d threads)" % (inf["grid_blocks"], inf["block_threads"]))
+        plain_scheds[key] = plain_scheds.get(key, 0) + 1
     for x in lat_p:
         x.close()
     out = {
@@ -491,9 +499,8 @@ def run_batched(args, n_replicas=512, updates=None, embed=False, plain_every=1):
         "replica_latency_ms_p50": float(np.percentile(lat_ms, 50)),
         "replica_latency_ms_p99": float(np.percentile(lat_ms, 99)),
         "plan": plan.to_json(), "autotune_s": t_tune, "autotune": table,
-        "plain_form": "one wolff_step launch per lattice, default schedule (%s, %s CTAs x %s "
-                      "threads)" % ("cluster", plain_info.get("grid_blocks"),
-                                     plain_info.get("block_threads")),
+        "plain_form": "one wolff_step launch per lattice, the library's default schedule: " +
+                      ", ".join("%s for %d" % (k, v) for k, v in sorted(plain_scheds.items())),
         "plain_sample": ("all %d replicas" % n_replicas if len(plain_ix) == n_replicas else
                          "every %d-th replica in (L, T) order (%d of %d), the full %d updates "
                          "each; records compared with the batched arm's for those" % (
@@ -514,7 +521,7 @@ def run_served(args, n_requests=200, embed=False):
     from paper_1110_0899_gb300 import serving, workloads
     torch.cuda.set_device(0)
     trace = workloads.serving_trace(n_requests)
-    srv = serving.WolffServer(keep_records=True)
+    srv = serving.WolffServer(keep_records=True, tiny=not getattr(args, "no_tiny_engine", False))
     reqs, summary = srv.serve(trace, max_seconds=args.serve_seconds)
     srv.close()
     summary["workload"] = ("%d requests, Poisson 200 req/s, 70%% 2D L 32..2048, 30%% 3D L 16..128, "
@@ -1013,6 +1020,7 @@ def main():
     if headline and not args.no_served:
         class _S:
             serve_seconds = args.embed_serve_seconds
+            no_tiny_engine = args.no_tiny_engine
         line["served"] = run_served(_S, embed=True)
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -456,7 +456,8 @@ wolff_status wolff_batch_create(wolff_batch **out, int capacity, void *stream);
  * records to d_records[i] (nullable entries).  The contexts must be distinct,
  * live on the batch's device, and have no work pending on other streams.
  * Larger lattices are launched first.  cluster_size (1..16) and
- * block_threads (multiple of 32, <= 512) set the team shape.  Asynchronous
+ * block_threads (multiple of 32, <= 512) set the team shape (a TINY batch:
+ * see wolff_batch_set_schedule).  Asynchronous
  * on the batch's stream; device errors are reported by each context's next
  * synchronising call. */
 wolff_status wolff_batch_run(wolff_batch *b, wolff_ctx *const *ctxs, int n,
@@ -481,6 +482,17 @@ wolff_status wolff_batch_run_timed(wolff_batch *b, wolff_ctx *const *ctxs, int n
  * levels per round come from each context's wolff_set_burst.  Results do not
  * depend on the setting.  EINVAL for other values. */
 wolff_status wolff_batch_set_window(wolff_batch *b, int slots_per_cta);
+
+/* The engine of this batch's launches: WOLFF_SCHED_CLUSTER (the default: one
+ * thread-block cluster per context, window mode) or WOLFF_SCHED_TINY (one
+ * CTA per context holding its lattice in shared memory as bit planes, see
+ * the TINY schedule; one launch per dimension).  On a TINY batch every
+ * context must be an Ising lattice of at most WOLFF_TINY_MAX_SITES sites
+ * (wolff_batch_run: EUNSUPPORTED otherwise), cluster_size must be 1, and
+ * block_threads is 0 (each launch takes TINY's default for its largest
+ * lattice) or a CTA size that lattice can use (EINVAL otherwise).  Results
+ * do not depend on the engine.  EINVAL for other values. */
+wolff_status wolff_batch_set_schedule(wolff_batch *b, int schedule);
 
 wolff_status wolff_batch_free(wolff_batch *b);
 

@@ -110,6 +110,7 @@ def load_library():
         "wolff_batch_run_timed": (i, [v, v, i, v, v, i, i, u64]),
         "wolff_batch_free": (i, [v]),
         "wolff_batch_set_window": (i, [v, i]),
+        "wolff_batch_set_schedule": (i, [v, i]),
         "wolff_step_static": (i, [i, i, d, d, u64, u64, u64, v, v, v]),
         "wolff_step_static_status": (i, [v, P(i), P(u32), P(u64)]),
         "wolff_l2_probe": (i, [v, sz, i, i, v, v]),
@@ -438,14 +439,24 @@ class WolffLattice:
 
 class WolffBatch:
     """Runs the next updates of many WolffLattice objects in one launch (one
-    thread-block cluster per lattice).  Each lattice's chain is the one it
-    would follow alone."""
+    thread-block cluster per lattice, or with schedule=SCHED_TINY one CTA per
+    lattice of at most TINY_MAX_SITES sites).  Each lattice's chain is the one
+    it would follow alone."""
 
-    def __init__(self, capacity, stream=None):
+    def __init__(self, capacity, stream=None, schedule=SCHED_CLUSTER):
         self.handle = ctypes.c_void_p()
         _check(load_library().wolff_batch_create(ctypes.byref(self.handle), int(capacity),
                                                  _stream_handle(stream)))
         self.capacity = int(capacity)
+        if schedule != SCHED_CLUSTER:
+            self.set_schedule(schedule)
+
+    def set_schedule(self, schedule):
+        """SCHED_CLUSTER (teams, the default) or SCHED_TINY (one CTA per
+        lattice; run() then takes cluster_size=1 and block_threads=0 for the
+        default CTA size)."""
+        _check(load_library().wolff_batch_set_schedule(self.handle, int(schedule)))
+        self.schedule = int(schedule)
 
     def run(self, lattices, n_updates, records=None, cluster_size=1, block_threads=256,
             budget_ns=0):

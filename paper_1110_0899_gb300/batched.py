@@ -1,19 +1,24 @@
 """Batched form: many independent lattices per launch, with an autotuner.
 
-A plan splits the lattices into groups.  A group runs on one of two
+A plan splits the lattices into groups.  A group runs on one of three
 schedules:
   - "batched": one persistent launch through a wolff_batch (one
     thread-block cluster per lattice, the C ABI's batched entry point) on the
     group's own CUDA stream, with the group's team shape (cluster size,
     threads per CTA) and window-mode queue (window slots per CTA, growth
     levels per commit round);
+  - "tiny": a wolff_batch on the tiny engine (one CTA per lattice of at most
+    TINY_MAX_SITES sites, the lattice in shared memory as bit planes) on the
+    group's own stream; lattices of at most 64 words and larger ones form
+    separate groups, so that each launch has the CTA size its lattices want;
   - "launches": one wolff_step launch per lattice with the library's default
     schedule (the largest thread-block cluster, window mode), on the stream
     the lattices were created on, concurrently with the batched groups.
 The autotuner times candidate plans on throw-away copies of the workload
 (same shapes and temperatures, other seeds): first the team shapes and the
 size split, then, around the best of those, the window slots, the levels
-per round and the schedule of the large lattices.  It caches the winner per
+per round, the schedule of the large lattices and the tiny engine for the
+lattices it takes.  It caches the winner per
 GPU and workload signature.  No plan changes any result: each lattice
 follows the chain it would follow alone.
 """
@@ -24,17 +29,39 @@ import time
 
 import numpy as np
 
-from . import (RECORD_BYTES, WolffBatch, WolffLattice, _build, records_to_numpy, wolff_step)
+from . import (RECORD_BYTES, SCHED_TINY, TINY_MAX_SITES, WolffBatch, WolffLattice, _build,
+               records_to_numpy, wolff_step)
 
 
-BATCHED, LAUNCHES = "batched", "launches"
+BATCHED, LAUNCHES, TINY = "batched", "launches", "tiny"
 DEFAULT_SLOTS = 64
+
+
+def tiny_words(dim, L):
+    """32-bit words of a lattice's bit planes: (N / L) ceil(L / 32)."""
+    return L ** (dim - 1) * ((L + 31) // 32)
+
+
+def tiny_split(specs, ix):
+    """The lattices of ix the tiny engine takes, as (at most 64 words, more),
+    and the rest."""
+    small, large, rest = [], [], []
+    for i in ix:
+        s = specs[i]
+        if s["L"] ** s["dim"] > TINY_MAX_SITES:
+            rest.append(i)
+        elif tiny_words(s["dim"], s["L"]) <= 64:
+            small.append(i)
+        else:
+            large.append(i)
+    return small, large, rest
 
 
 class Group:
     """Lattices `ix` on one schedule: BATCHED with team shape (cs, th),
     `slots` window slots per CTA and `levels` growth levels per round (1 =
-    the library's default), or LAUNCHES (one default launch per lattice)."""
+    the library's default), LAUNCHES (one default launch per lattice), or
+    TINY (one CTA per lattice, th threads, 0 = the engine's default)."""
 
     def __init__(self, ix, cs=1, th=256, slots=DEFAULT_SLOTS, levels=1, kind=BATCHED):
         self.ix, self.cs, self.th = list(ix), int(cs), int(th)
@@ -49,6 +76,9 @@ class Group:
     def to_json(self):
         if self.kind == LAUNCHES:
             return {"n": len(self.ix), "schedule": LAUNCHES}
+        if self.kind == TINY:
+            return {"n": len(self.ix), "schedule": TINY,
+                    "block_threads": self.th if self.th else "default"}
         return {"n": len(self.ix), "schedule": BATCHED, "cluster_size": self.cs,
                 "block_threads": self.th, "window_slots": self.slots,
                 "levels_per_round": self.levels if self.levels > 1 else "default"}
@@ -82,6 +112,10 @@ class BatchedRunner:
                 b.set_window(g.slots)
                 self.streams.append(st)
                 self.batches.append(b)
+            elif g.kind == TINY:
+                st = torch.cuda.Stream()
+                self.streams.append(st)
+                self.batches.append(WolffBatch(max(1, len(g.ix)), stream=st, schedule=SCHED_TINY))
             else:
                 self.streams.append(None)
                 self.batches.append(None)
@@ -109,12 +143,12 @@ class BatchedRunner:
         # the batched groups first, each on its stream once the current
         # stream's earlier work is done ...
         for g, st, b in zip(self.plan.groups, self.streams, self.batches):
-            if g.kind != BATCHED or not g.ix:
+            if g.kind == LAUNCHES or not g.ix:
                 continue
             st.wait_stream(cur)
             b.run([self.lattices[i] for i in g.ix], n_updates,
-                  None if bufs is None else [bufs[i] for i in g.ix], cluster_size=g.cs,
-                  block_threads=g.th)
+                  None if bufs is None else [bufs[i] for i in g.ix],
+                  cluster_size=1 if g.kind == TINY else g.cs, block_threads=g.th)
         # ... then the per-lattice launches on the current stream, concurrently
         for g in self.plan.groups:
             if g.kind != LAUNCHES:
@@ -184,6 +218,16 @@ def refine_plans(best, specs):
         out.append(Plan([Group(big, kind=LAUNCHES), small_g],
                         "big: one default launch each / small: %s" % (
                             "cs=%d th=%d" % (small_g.cs, small_g.th))))
+    # the tiny engine for the lattices it takes, the rest as in the best plan
+    tw, tl, _ = tiny_split(specs, range(len(specs)))
+    if tw or tl:
+        taken = set(tw) | set(tl)
+        groups = [Group(x, th=0, kind=TINY) for x in (tw, tl) if x]
+        for g in best.groups:
+            keep = [i for i in g.ix if i not in taken]
+            if keep:
+                groups.append(g.replace(ix=keep))
+        out.append(Plan(groups, best.label + " / tiny engine for %d lattices" % len(taken)))
     return out
 
 
@@ -209,7 +253,7 @@ def _time_plan(p, specs, probe_updates, seed_offset):
         # carve-out) happen outside the timing, on two throwaway lattices
         warm = [WolffLattice(2, 8, 2.0, seed=1) for _ in range(2)]
         for g in p.groups:
-            if g.kind == BATCHED:
+            if g.kind in (BATCHED, TINY):
                 w = BatchedRunner(warm, Plan([g.replace(ix=[0, 1])]))
                 w.run(2, records=False)
                 torch.cuda.synchronize()

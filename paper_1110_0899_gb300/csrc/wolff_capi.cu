@@ -81,18 +81,6 @@ constexpr size_t kAlign = 256;
 // cluster size 16; the batched form keeps its CTAs small
 constexpr int kPlainWindowSlots = 128;
 constexpr int kBatchWindowSlots = 64;
-// tiny schedule default CTA, the fastest of 32..1024 threads on 2D L = 16..181
-// and 3D L = 8..32 at T_c: warp 0 and three drawing warps for lattices of at
-// most 64 words; else 256 threads up to 192 words, 512 up to 1024 words (two
-// words per thread beyond 512: fewer warps at the level barrier beat one
-// word per thread), and the fewest that hold two words each beyond that
-int tiny_default_threads(int dim, int L) {
-    const uint32_t nw = tiny_words_of(dim, L);
-    if (nw <= 64u) return 128;
-    if (nw <= 192u) return 256;
-    if (nw <= 1024u) return 512;
-    return (int)(((nw + 1u) / 2u + 31u) / 32u * 32u);
-}
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -971,6 +959,7 @@ const char *wolff_last_error(wolff_ctx *c) {
 struct wolff_batch {
     int capacity = 0;
     int win_slots = kBatchWindowSlots;   // window slots per CTA (0 = window mode off)
+    int schedule = WOLFF_SCHED_CLUSTER;  // CLUSTER (teams) or TINY (one CTA per lattice)
     cudaStream_t stream = nullptr;
     StepParams *h_table = nullptr;   // pinned staging copy
     StepParams *d_table = nullptr;
@@ -1007,10 +996,14 @@ wolff_status wolff_batch_run_timed(wolff_batch *b, wolff_ctx *const *ctxs, int n
                                    const uint64_t *n_updates, void *const *d_records,
                                    int cluster_size, int block_threads, uint64_t budget_ns) {
     if (!b || n < 0 || n > b->capacity || (n && (!ctxs || !n_updates))) return WOLFF_EINVAL;
-    if (cluster_size != 1 && cluster_size != 2 && cluster_size != 4 && cluster_size != 8 &&
-        cluster_size != 16)
+    const bool tiny = b->schedule == WOLFF_SCHED_TINY;
+    if (cluster_size != 1 && (tiny || (cluster_size != 2 && cluster_size != 4 &&
+                                       cluster_size != 8 && cluster_size != 16)))
         return WOLFF_EINVAL;
-    if (block_threads < 32 || block_threads > 512 || block_threads % 32) return WOLFF_EINVAL;
+    if (tiny ? (block_threads != 0 && (block_threads < 32 || block_threads > 1024 ||
+                                       block_threads % 32))
+             : (block_threads < 32 || block_threads > 512 || block_threads % 32))
+        return WOLFF_EINVAL;
     if (b->pending) {   // the previous staging copy must have been consumed
         if (cudaEventSynchronize(b->copied) != cudaSuccess) return WOLFF_ECUDA;
         b->pending = false;
@@ -1020,6 +1013,7 @@ wolff_status wolff_batch_run_timed(wolff_batch *b, wolff_ctx *const *ctxs, int n
     for (int i = 0; i < n; ++i) {
         if (!ctxs[i]) return WOLFF_EINVAL;
         if (ctxs[i]->potts || ctxs[i]->xy) return WOLFF_EUNSUPPORTED;
+        if (tiny && ctxs[i]->N > kTinyMaxSites) return WOLFF_EUNSUPPORTED;
         if (n_updates[i] == 0) continue;
         (ctxs[i]->dim == 2 ? n2 : n3) += 1;
     }
@@ -1044,12 +1038,26 @@ wolff_status wolff_batch_run_timed(wolff_batch *b, wolff_ctx *const *ctxs, int n
     if (e != cudaSuccess) return WOLFF_ECUDA;
     b->pending = true;
     StepParams none = {};
-    if (n2)
-        e = launch_team(2, none, b->d_table, n2, cluster_size, block_threads, b->win_slots,
-                        b->stream);
-    if (e == cudaSuccess && n3)
-        e = launch_team(3, none, b->d_table + n2, n3, cluster_size, block_threads, b->win_slots,
-                        b->stream);
+    if (tiny) {
+        // one CTA per lattice, one launch per dimension, shaped for the
+        // largest lattice of that dimension (the table's first)
+        for (int d = 2; d <= 3 && e == cudaSuccess; ++d) {
+            const int cnt = d == 2 ? n2 : n3;
+            if (!cnt) continue;
+            const StepParams &first = b->h_table[d == 2 ? 0 : n2];
+            const int maxL = (int)first.g.L;
+            const int thr = block_threads ? block_threads : tiny_default_threads(d, maxL);
+            if (!tiny_shape_ok(d, maxL, thr)) return WOLFF_EINVAL;
+            e = launch_tiny(d, none, b->d_table + (d == 2 ? 0 : n2), cnt, maxL, thr, b->stream);
+        }
+    } else {
+        if (n2)
+            e = launch_team(2, none, b->d_table, n2, cluster_size, block_threads, b->win_slots,
+                            b->stream);
+        if (e == cudaSuccess && n3)
+            e = launch_team(3, none, b->d_table + n2, n3, cluster_size, block_threads,
+                            b->win_slots, b->stream);
+    }
     if (e != cudaSuccess) return WOLFF_ECUDA;
     for (int i = 0; i < n; ++i) ctxs[i]->t_host += n_updates[i];
     return WOLFF_OK;
@@ -1061,6 +1069,13 @@ wolff_status wolff_batch_set_window(wolff_batch *b, int slots_per_cta) {
         slots_per_cta != 128)
         return WOLFF_EINVAL;
     b->win_slots = slots_per_cta;
+    return WOLFF_OK;
+}
+
+wolff_status wolff_batch_set_schedule(wolff_batch *b, int schedule) {
+    if (!b) return WOLFF_EINVAL;
+    if (schedule != WOLFF_SCHED_CLUSTER && schedule != WOLFF_SCHED_TINY) return WOLFF_EINVAL;
+    b->schedule = schedule;
     return WOLFF_OK;
 }
 

@@ -221,6 +221,8 @@ bool tiny_warp_mode(int dim, int L, int threads);
 // a CTA of `threads` threads can run the lattice (each grower owns <= 2 words)
 bool tiny_shape_ok(int dim, int L, int threads);
 size_t tiny_smem_bytes(int dim, int L);
+// the CTA size the tiny schedule takes by default for this lattice
+int tiny_default_threads(int dim, int L);
 cudaError_t launch_tiny(int dim, const StepParams &single, const StepParams *d_table, int njobs,
                         int max_L, int threads, cudaStream_t s);
 

@@ -441,6 +441,19 @@ static int tiny_J(int dim, int L, int threads) {
 
 bool tiny_shape_ok(int dim, int L, int threads) { return tiny_J(dim, L, threads) != 0; }
 
+// The default CTA, the fastest of 32..1024 threads on 2D L = 16..181
+// and 3D L = 8..32 at T_c: warp 0 and three drawing warps for lattices of at
+// most 64 words; else 256 threads up to 192 words, 512 up to 1024 words (two
+// words per thread beyond 512: fewer warps at the level barrier beat one
+// word per thread), and the fewest that hold two words each beyond that
+int tiny_default_threads(int dim, int L) {
+    const uint32_t nw = tiny_words_of(dim, L);
+    if (nw <= 64u) return 128;
+    if (nw <= 192u) return 256;
+    if (nw <= 1024u) return 512;
+    return (int)(((nw + 1u) / 2u + 31u) / 32u * 32u);
+}
+
 size_t tiny_smem_bytes(int dim, int L) {
     uint64_t n = 1;
     for (int d = 0; d < dim; ++d) n *= (uint64_t)L;

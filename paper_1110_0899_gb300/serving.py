@@ -5,11 +5,12 @@ back its per-update records (|C|, levels, E_bond, M) and final E, M.  The
 server keeps every admitted lattice resident on the device and works in
 epochs: at each epoch boundary it admits the requests that have arrived, as
 long as their memory (workspace + record buffer) fits the budget, then runs
-updates of every active request in shared batched launches (one
-thread-block cluster per lattice; large lattices get larger teams on a second
-stream) -- each request's share sized from its measured cost per update and
-capped on the device by a time budget -- and retires the requests that are
-done.
+updates of every active request in shared batched launches (lattices of at
+most TINY_MAX_SITES sites one CTA each on the tiny engine, in two groups by
+size; the others one thread-block cluster each, large lattices with larger
+teams; each group on its own stream) -- each request's share sized from its
+measured cost per update and capped on the device by a time budget -- and
+retires the requests that are done.
 Requests that arrive while others are on the GPU therefore join at the next
 epoch and their work overlaps on the device.  A request's chain does not
 depend on what it shares the GPU with: its records equal those of the same
@@ -20,7 +21,12 @@ import time
 
 import numpy as np
 
-from . import RECORD_BYTES, WolffBatch, WolffLattice, records_to_numpy, wolff_workspace_bytes
+from . import (RECORD_BYTES, SCHED_CLUSTER, SCHED_TINY, TINY_MAX_SITES, WolffBatch, WolffLattice,
+               records_to_numpy, wolff_workspace_bytes)
+
+
+def _tiny_words(dim, L):
+    return L ** (dim - 1) * ((L + 31) // 32)
 
 
 class Request:
@@ -52,7 +58,7 @@ class Request:
 class WolffServer:
     def __init__(self, memory_budget=None, epoch_updates=1 << 20, big_sites=1 << 18,
                  small_team=(1, 256), big_team=(4, 256), max_active=4096, keep_records=True,
-                 epoch_seconds=0.02, first_quota=16):
+                 epoch_seconds=0.02, first_quota=16, tiny=True):
         import torch
         if memory_budget is None:
             free, _ = torch.cuda.mem_get_info()
@@ -68,8 +74,13 @@ class WolffServer:
         # update so that one slow lattice does not hold the others back
         self.epoch_seconds = float(epoch_seconds)
         self.first_quota = int(first_quota)
-        self.streams = [torch.cuda.Stream(), torch.cuda.Stream()]
-        self.batches = [WolffBatch(max_active, stream=s) for s in self.streams]
+        # groups: tiny engine (<= 64 words), tiny engine (larger), small
+        # teams, large teams -- each on its own stream
+        self.tiny = bool(tiny)
+        self.streams = [torch.cuda.Stream() for _ in range(4)]
+        self.batches = [WolffBatch(max_active, stream=s,
+                                   schedule=SCHED_TINY if k < 2 else SCHED_CLUSTER)
+                        for k, s in enumerate(self.streams)]
 
     def _admit(self, req, now):
         import torch
@@ -92,11 +103,15 @@ class WolffServer:
     def _epoch(self, active, t0=None):
         import torch
         cur = torch.cuda.current_stream()
-        groups = [[], []]
+        groups = [[], [], [], []]
         for r in active:
-            groups[1 if r.lattice.N >= self.big_sites else 0].append(r)
-        for g, (cs, th), st, b in zip(groups, (self.small_team, self.big_team), self.streams,
-                                      self.batches):
+            s = r.spec
+            if self.tiny and r.lattice.N <= TINY_MAX_SITES:
+                groups[0 if _tiny_words(s["dim"], s["L"]) <= 64 else 1].append(r)
+            else:
+                groups[3 if r.lattice.N >= self.big_sites else 2].append(r)
+        shapes = ((1, 0), (1, 0), self.small_team, self.big_team)
+        for g, (cs, th), st, b in zip(groups, shapes, self.streams, self.batches):
             if not g:
                 continue
             st.wait_stream(cur)

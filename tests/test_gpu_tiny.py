@@ -196,3 +196,102 @@ def test_schedule_choice_and_refusals():
         potts.set_schedule(w.SCHED_TINY)
     assert ei.value.status == w.WOLFF_EUNSUPPORTED
     potts.close()
+
+
+# (dim, L, T, seed): 2D and 3D, from L=2 to the largest lattices the engine
+# takes, at and around T_c
+BATCH = [(2, 2, 1.0, 5), (2, 16, TC2, 6), (2, 33, 2.2, 7), (2, 100, TC2, 8), (2, 181, 2.5, 9),
+         (3, 2, 4.0, 10), (3, 8, 4.5115, 11), (3, 13, 4.3, 12), (3, 32, 4.6, 13),
+         (2, 64, 2.0, 14), (3, 5, 4.5115, 15)]
+
+
+def test_tiny_batch_keeps_every_chain():
+    """Every lattice of a tiny-engine batch (one CTA each, one launch per
+    dimension, mixed sizes) follows the oracle's chain across calls."""
+    torch, w = require_cuda()
+    lats = [w.WolffLattice(d, L, T, seed=s) for d, L, T, s in BATCH]
+    batch = w.WolffBatch(len(lats), schedule=w.SCHED_TINY)
+    got = [[] for _ in lats]
+    for n in (30, 1, 45):
+        bufs = [lat.record_buffer(n) for lat in lats]
+        batch.run(lats, n, bufs, cluster_size=1, block_threads=0)
+        torch.cuda.synchronize()
+        for k, lat in enumerate(lats):
+            got[k].append(w.records_to_numpy(bufs[k], n))
+    batch.close()
+    for k, (d, L, T, s) in enumerate(BATCH):
+        ref, s_ref = oracle_trajectory(d, L, T, s, 76)
+        assert_records_equal(np.concatenate(got[k]), ref, "tiny batch %dD L=%d" % (d, L))
+        spins, t = lats[k].get_state()
+        assert t == 76 and np.array_equal(spins, s_ref)
+        assert lats[k].measure()[:2] == lats[k].measure_full()
+        lats[k].close()
+
+
+def test_tiny_batch_time_budget_and_refusals():
+    torch, w = require_cuda()
+    specs = [(2, 96, 2.0, 5), (3, 12, 4.0, 6), (2, 40, 2.3, 7), (2, 20, 2.1, 8)]
+    lats = [w.WolffLattice(d, L, T, seed=s) for d, L, T, s in specs]
+    for lat in lats:
+        lat.set_state(np.ones(lat.N, np.int8), 0)   # ordered: large clusters, slow updates
+    batch = w.WolffBatch(len(lats), schedule=w.SCHED_TINY)
+    got = [[] for _ in lats]
+    seen = [0] * len(lats)
+    for call in range(6):
+        bufs = [lat.record_buffer(400) for lat in lats]
+        batch.run(lats, 400, bufs, cluster_size=1, block_threads=0, budget_ns=20_000)
+        torch.cuda.synchronize()
+        for k, lat in enumerate(lats):
+            ran = lat.stats()["updates"] - seen[k]
+            seen[k] += ran
+            assert 1 <= ran <= 400
+            got[k].append(w.records_to_numpy(bufs[k], ran))
+    assert any(sum(len(x) for x in g) < 6 * 400 for g in got)   # the budget did stop some
+    for k, (dim, L, T, seed) in enumerate(specs):
+        rec = np.concatenate(got[k])
+        ref, s_ref = oracle_trajectory(dim, L, T, seed, len(rec), s=np.ones(L ** dim, np.int8))
+        assert_records_equal(rec, ref, "budgeted tiny lattice %d" % k)
+        spins, t = lats[k].get_state()
+        assert t == len(rec) and np.array_equal(spins, s_ref)
+    # refusals: a team shape, a CTA too small for the largest lattice, a
+    # lattice the engine does not take, a Potts lattice
+    for cs, th in ((2, 0), (1, 48)):
+        with pytest.raises(w.WolffError) as ei:
+            batch.run(lats, 1, None, cluster_size=cs, block_threads=th)
+        assert ei.value.status == w.WOLFF_EINVAL
+    with pytest.raises(w.WolffError) as ei:
+        batch.run(lats[:1], 1, None, cluster_size=1, block_threads=32)   # 2D L=96: 288 words
+    assert ei.value.status == w.WOLFF_EINVAL
+    big = w.WolffLattice(2, 200, TC2, seed=1)
+    potts = w.WolffLattice(2, 16, 1.0, seed=1, q=3)
+    for other in (big, potts):
+        with pytest.raises(w.WolffError) as ei:
+            batch.run([lats[0], other], 1, None, cluster_size=1, block_threads=0)
+        assert ei.value.status == w.WOLFF_EUNSUPPORTED
+    for x in lats + [big, potts]:
+        x.close()
+    batch.close()
+
+
+def test_runner_with_tiny_groups_matches_alone():
+    torch, w = require_cuda()
+    from paper_1110_0899_gb300 import batched
+    specs = [dict(dim=d, L=L, T=T, seed=s) for d, L, T, s in BATCH]
+    specs += [dict(dim=2, L=256, T=TC2, seed=40), dict(dim=3, L=40, T=4.5115, seed=41)]
+    tw, tl, rest = batched.tiny_split(specs, range(len(specs)))
+    assert tw and tl and rest == [len(BATCH), len(BATCH) + 1]
+    plan = batched.Plan([batched.Group(tw, th=0, kind=batched.TINY),
+                         batched.Group(tl, th=0, kind=batched.TINY),
+                         batched.Group(rest, 2, 256)], "tiny groups + team")
+    lats = [w.WolffLattice(s["dim"], s["L"], s["T"], seed=s["seed"]) for s in specs]
+    r = batched.BatchedRunner(lats, plan)
+    bufs = r.run(40)
+    torch.cuda.synchronize()
+    got = r.records_numpy(bufs, 40)
+    r.close()
+    for i, s in enumerate(specs):
+        alone = w.WolffLattice(s["dim"], s["L"], s["T"], seed=s["seed"])
+        alone.set_schedule(w.SCHED_CLUSTER)
+        assert_records_equal(got[i], alone.step(40), "runner lattice %d vs alone" % i)
+        alone.close()
+        lats[i].close()

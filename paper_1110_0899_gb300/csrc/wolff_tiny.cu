@@ -199,6 +199,98 @@ __device__ __forceinline__ void count_word(const WordNb<DIM> &n, const uint32_t 
     up += __popc(s & n.vm);
 }
 
+// ---- warp mode: warp 0 alone, one word per row (W = 1 whenever a lattice
+// has at most 64 words), its words' state in registers; a neighbour row
+// comes from the lane holding it by a shuffle, so a level costs no shared
+// memory traffic and no barrier beyond the vote that ends it.
+
+// Row k of a lattice whose rows are spread over the lanes as v[k / 32] of
+// lane k % 32 (every lane calls it; each asks for its own k).
+template <int J>
+__device__ __forceinline__ uint32_t row_of(const uint32_t (&v)[J], uint32_t k) {
+    uint32_t out = __shfl_sync(kFullMask, v[0], k & 31u);
+    if (J == 2) {
+        const uint32_t hi = __shfl_sync(kFullMask, v[J - 1], k & 31u);
+        if (k >> 5) out = hi;
+    }
+    return out;
+}
+
+// One update on warp 0: grows the cluster of seed site i0 level by level,
+// flips it in Sr (the warp's rows, kept in registers between updates) and
+// returns |C|, the anti-parallel bonds and the up spins after the flip (warp
+// sums) and the number of generations.
+template <int DIM, int J>
+__device__ __forceinline__ void warp_update(const TinyGeo &g, const WordNb<DIM> (&nb)[J],
+                                            const bool (&own)[J], uint32_t (&Sr)[J],
+                                            const uint32_t *B, uint32_t i0, uint32_t &C,
+                                            uint32_t &anti, uint32_t &up, uint32_t &level) {
+    const uint32_t x0 = i0 % g.L, r0 = i0 / g.L;
+    const uint32_t sig0bit = (row_of<J>(Sr, r0) >> x0) & 1u;
+    const uint32_t hb = g.hb;
+    uint32_t A[J], V[J], F[J], ox[J], oy[J], oym[J], oz[J], ozm[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const uint32_t k = nb[j].k;
+        A[j] = own[j] ? (sig0bit ? Sr[j] : ~Sr[j]) & nb[j].vm : 0u;
+        V[j] = F[j] = (own[j] && k == r0) ? 1u << x0 : 0u;
+        ox[j] = B[k];
+        oy[j] = B[g.NW + k];
+        oym[j] = B[g.NW + nb[j].ym];
+        oz[j] = ozm[j] = 0u;
+        if (DIM == 3) {
+            oz[j] = B[2u * g.NW + k];
+            ozm[j] = B[2u * g.NW + nb[j].zm];
+        }
+    }
+    level = 0;
+    for (;;) {
+        uint32_t nf[J];
+        uint32_t any = 0;
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const uint32_t gx = F[j] & ox[j];
+            // +x across the bond of site x-1, -x across the site's own (a
+            // rotation within the row's L bits)
+            uint32_t G = ((gx << 1) | ((gx >> hb) & 1u)) |
+                         (((F[j] >> 1) | ((F[j] & 1u) << hb)) & ox[j]);
+            G |= (row_of<J>(F, nb[j].ym) & oym[j]) | (row_of<J>(F, nb[j].yp) & oy[j]);
+            if (DIM == 3)
+                G |= (row_of<J>(F, nb[j].zm) & ozm[j]) | (row_of<J>(F, nb[j].zp) & oz[j]);
+            nf[j] = G & A[j] & ~V[j];
+        }
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            V[j] |= nf[j];
+            F[j] = nf[j];
+            any |= nf[j];
+        }
+        ++level;
+        if (!__any_sync(kFullMask, any != 0u)) break;
+    }
+    uint32_t c = 0, a = 0, u = 0;
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        Sr[j] ^= V[j];
+        c += __popc(V[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const uint32_t sp = Sr[j];
+        const uint32_t sn = (sp >> 1) | ((sp & 1u) << hb);   // site x+1's spin at bit x
+        uint32_t aa = __popc((sp ^ sn) & nb[j].vm) +
+                      __popc((sp ^ row_of<J>(Sr, nb[j].yp)) & nb[j].vm);
+        if (DIM == 3) aa += __popc((sp ^ row_of<J>(Sr, nb[j].zp)) & nb[j].vm);
+        if (own[j]) {
+            a += aa;
+            u += __popc(sp & nb[j].vm);
+        }
+    }
+    C = __reduce_add_sync(kFullMask, c);
+    anti = __reduce_add_sync(kFullMask, a);
+    up = __reduce_add_sync(kFullMask, u);
+}
+
 // two words per grower in 3D only occur in warp mode (3D lattices have at
 // most 1024 words): those CTAs are capped at 512 threads so that the two
 // words' state stays in registers
@@ -218,7 +310,10 @@ __global__ void __launch_bounds__(DIM == 3 && J == 2 ? 512 : 1024, 1) k_tiny(Ste
     const uint32_t nwarps = T >> 5;
     const uint32_t bstride = DIM * g.NW;     // one parity's bond planes
     DevCtl *ctl = p.ctl;
-    const bool wm = warp_mode != 0u;
+    // warp mode only ever needs two words per lane in 3D (a 2D lattice of at
+    // most 64 words has at most 32 rows): the 2D two-word kernel omits it
+    constexpr bool kWarpPath = !(DIM == 2 && J == 2);
+    const bool wm = kWarpPath && warp_mode != 0u;
     // the words this thread grows: warp mode: lane + 32 j (warp 0 only);
     // otherwise tid + T j
     const bool grower = !wm || warp == 0u;
@@ -257,6 +352,9 @@ __global__ void __launch_bounds__(DIM == 3 && J == 2 ? 512 : 1024, 1) k_tiny(Ste
         for (int q = 0; q < 8; ++q) sums[q] = 0u;
     }
     __syncthreads();
+    uint32_t Sr[J];   // warp mode: warp 0's rows of spins
+#pragma unroll
+    for (int j = 0; j < J; ++j) Sr[j] = (wm && own[j]) ? S[nb[j].k] : 0u;
 
     unsigned long long u = 0;
     while (u < p.n) {
@@ -271,11 +369,13 @@ __global__ void __launch_bounds__(DIM == 3 && J == 2 ? 512 : 1024, 1) k_tiny(Ste
         }
         const uint32_t *B = Bb + par * bstride;
         const uint32_t i0 = s_seed[par];
-        const uint32_t x0 = i0 % g.L, r0 = i0 / g.L;
-        const uint32_t seedk = r0 * g.W + (x0 >> 5), seedbit = 1u << (x0 & 31u);
-        const uint32_t sig0bit = (S[seedk] & seedbit) ? 1u : 0u;
         uint32_t level = 0, C = 0, anti = 0, up = 0;
-        if (grower) {
+        if (kWarpPath && wm && warp == 0u) {
+            if constexpr (kWarpPath) warp_update<DIM, J>(g, nb, own, Sr, B, i0, C, anti, up, level);
+        } else if (grower) {
+            const uint32_t x0 = i0 % g.L, r0 = i0 / g.L;
+            const uint32_t seedk = r0 * g.W + (x0 >> 5), seedbit = 1u << (x0 & 31u);
+            const uint32_t sig0bit = (S[seedk] & seedbit) ? 1u : 0u;
             WordState ws[J];
 #pragma unroll
             for (int j = 0; j < J; ++j) {
@@ -285,7 +385,7 @@ __global__ void __launch_bounds__(DIM == 3 && J == 2 ? 512 : 1024, 1) k_tiny(Ste
                 }
             }
             uint32_t cur = 0;
-            if (wm) __syncwarp(); else __syncthreads();
+            __syncthreads();
             for (;;) {
                 const uint32_t *Fc = Fb + cur * g.NW;
                 uint32_t *Fn = Fb + (cur ^ 1u) * g.NW;
@@ -302,14 +402,7 @@ __global__ void __launch_bounds__(DIM == 3 && J == 2 ? 512 : 1024, 1) k_tiny(Ste
                 }
                 ++level;
                 // the level barrier; it also tells whether the front is empty
-                bool more;
-                if (wm) {
-                    __syncwarp();
-                    more = __any_sync(kFullMask, any != 0u);
-                } else {
-                    more = __syncthreads_or(any != 0u) != 0;
-                }
-                if (!more) break;
+                if (!__syncthreads_or(any != 0u)) break;
                 cur ^= 1u;
             }
             // flip the cluster
@@ -320,14 +413,14 @@ __global__ void __launch_bounds__(DIM == 3 && J == 2 ? 512 : 1024, 1) k_tiny(Ste
                     C += __popc(ws[j].V);
                 }
             }
-            if (wm) __syncwarp(); else __syncthreads();
+            __syncthreads();
 #pragma unroll
             for (int j = 0; j < J; ++j)
                 if (own[j]) count_word<DIM>(nb[j], S, anti, up);
             C = __reduce_add_sync(kFullMask, C);
             anti = __reduce_add_sync(kFullMask, anti);
             up = __reduce_add_sync(kFullMask, up);
-            if (!wm && lane == 0) {
+            if (lane == 0) {
                 atomicAdd(&sums[0], C);
                 atomicAdd(&sums[1], anti);
                 atomicAdd(&sums[2], up);
@@ -368,6 +461,11 @@ __global__ void __launch_bounds__(DIM == 3 && J == 2 ? 512 : 1024, 1) k_tiny(Ste
         // the sums are read by thread 0 above before anyone adds again: the
         // next update's adds come after its draw barrier (or, in warp mode,
         // are not made)
+    }
+    if (wm && warp == 0u) {
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+            if (own[j]) S[nb[j].k] = Sr[j];
     }
     __syncthreads();
     for (uint32_t i = tid; i < g.N; i += T) {
@@ -441,14 +539,15 @@ static int tiny_J(int dim, int L, int threads) {
 
 bool tiny_shape_ok(int dim, int L, int threads) { return tiny_J(dim, L, threads) != 0; }
 
-// The default CTA, the fastest of 32..1024 threads on 2D L = 16..181
-// and 3D L = 8..32 at T_c: warp 0 and three drawing warps for lattices of at
-// most 64 words; else 256 threads up to 192 words, 512 up to 1024 words (two
-// words per thread beyond 512: fewer warps at the level barrier beat one
-// word per thread), and the fewest that hold two words each beyond that
+// The default CTA, the fastest of 32..1024 threads on 2D L = 16..181 and 3D
+// L = 4..32 at T_c: for lattices of at most 64 words warp 0 and three (2D) or
+// seven (3D: more sites per row to draw) drawing warps; else 256 threads up
+// to 192 words, 512 up to 1024 words (two words per thread beyond 512: fewer
+// warps at the level barrier beat one word per thread), and the fewest that
+// hold two words each beyond that.
 int tiny_default_threads(int dim, int L) {
     const uint32_t nw = tiny_words_of(dim, L);
-    if (nw <= 64u) return 128;
+    if (nw <= 64u) return dim == 3 ? 256 : 128;
     if (nw <= 192u) return 256;
     if (nw <= 1024u) return 512;
     return (int)(((nw + 1u) / 2u + 31u) / 32u * 32u);

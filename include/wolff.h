@@ -84,13 +84,19 @@ enum { WOLFF_LAYOUT_INT8 = 0 };
  *               SM.  grid_blocks must be 0 or 1; block_threads from 32 to
  *               1024, at least half the lattice's words unless warp 0 runs
  *               alone (EINVAL otherwise);
- *   AUTO        the library's choice: TINY for Ising lattices of at most
- *               WOLFF_TINY_MAX_SITES sites (it was the fastest at every such
- *               size measured), else CLUSTER with the largest cluster the GPU
- *               launches (16 where non-portable sizes are allowed, else 8),
- *               512 threads, t_up = 128, t_down = 64, window mode on.  A new
- *               context starts on AUTO's choice; AUTO with grid_blocks > 1 or
- *               a block_threads TINY cannot use means CLUSTER. */
+ *               On lattices above 64 words TINY draws every site's bonds
+ *               each update: measured 3-11x faster than CLUSTER while the
+ *               clusters are large (equilibrated at or below T_c), up to 50x
+ *               slower on clusters of a few sites (random starts, above T_c),
+ *               where CLUSTER's window mode grows many updates at once;
+ *   AUTO        the library's choice: TINY for Ising lattices of at most 64
+ *               words (2D L <= 32, 3D L <= 8; 8-26x faster than CLUSTER in
+ *               every regime measured), else CLUSTER with the largest cluster
+ *               the GPU launches (16 where non-portable sizes are allowed,
+ *               else 8), 512 threads, t_up = 128, t_down = 64, window mode
+ *               on.  A new context starts on AUTO's choice; AUTO with
+ *               grid_blocks > 1 or a block_threads TINY cannot use means
+ *               CLUSTER. */
 enum {
     WOLFF_SCHED_AUTO = 0,
     WOLFF_SCHED_PERSISTENT = 1,

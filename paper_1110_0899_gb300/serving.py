@@ -5,12 +5,16 @@ back its per-update records (|C|, levels, E_bond, M) and final E, M.  The
 server keeps every admitted lattice resident on the device and works in
 epochs: at each epoch boundary it admits the requests that have arrived, as
 long as their memory (workspace + record buffer) fits the budget, then runs
-updates of every active request in shared batched launches (lattices of at
-most TINY_MAX_SITES sites one CTA each on the tiny engine, in two groups by
-size; the others one thread-block cluster each, large lattices with larger
-teams; each group on its own stream) -- each request's share sized from its
-measured cost per update and capped on the device by a time budget -- and
-retires the requests that are done.
+updates of every active request in shared batched launches -- each request's
+share sized from its measured cost per update and capped on the device by a
+time budget -- and retires the requests that are done.
+Engines: a lattice of at most 64 words runs on the tiny engine (one CTA,
+always the faster there); one of up to TINY_MAX_SITES sites runs on whichever
+of the tiny and the team engine its own measured cost per update favours
+(the team engine first: a fresh lattice's clusters are small; the other one
+is timed again every few epochs, since a lattice's clusters grow as it
+orders); the rest on the team engine, one thread-block cluster per lattice,
+large lattices with larger teams.  Each engine group has its own stream.
 Requests that arrive while others are on the GPU therefore join at the next
 epoch and their work overlaps on the device.  A request's chain does not
 depend on what it shares the GPU with: its records equal those of the same
@@ -29,9 +33,13 @@ def _tiny_words(dim, L):
     return L ** (dim - 1) * ((L + 31) // 32)
 
 
+TINY, TEAM = "tiny", "team"
+
+
 class Request:
     __slots__ = ("spec", "lattice", "records", "done", "admitted_s", "finished_s", "result",
-                 "ns_per_update", "quota", "updates_seen", "first_update_s")
+                 "ns_per_update", "quota", "updates_seen", "first_update_s", "engine", "ns_by",
+                 "same_engine_epochs")
 
     def __init__(self, spec):
         self.spec = spec
@@ -45,6 +53,9 @@ class Request:
         self.quota = 0
         self.updates_seen = 0
         self.first_update_s = None
+        self.engine = TEAM
+        self.ns_by = {TINY: None, TEAM: None}   # measured ns per update on each engine
+        self.same_engine_epochs = 0
 
     @property
     def remaining(self):
@@ -58,7 +69,7 @@ class Request:
 class WolffServer:
     def __init__(self, memory_budget=None, epoch_updates=1 << 20, big_sites=1 << 18,
                  small_team=(1, 256), big_team=(4, 256), max_active=4096, keep_records=True,
-                 epoch_seconds=0.02, first_quota=16, tiny=True):
+                 epoch_seconds=0.02, first_quota=16, tiny=True, reprobe_epochs=8):
         import torch
         if memory_budget is None:
             free, _ = torch.cuda.mem_get_info()
@@ -77,6 +88,8 @@ class WolffServer:
         # groups: tiny engine (<= 64 words), tiny engine (larger), small
         # teams, large teams -- each on its own stream
         self.tiny = bool(tiny)
+        self.reprobe_epochs = int(reprobe_epochs)
+        self.engine_epochs = {TINY: 0, TEAM: 0}
         self.streams = [torch.cuda.Stream() for _ in range(4)]
         self.batches = [WolffBatch(max_active, stream=s,
                                    schedule=SCHED_TINY if k < 2 else SCHED_CLUSTER)
@@ -89,6 +102,12 @@ class WolffServer:
         req.records = torch.empty(max(1, s["n_updates"]) * RECORD_BYTES, dtype=torch.uint8,
                                   device="cuda")
         req.admitted_s = now
+
+    def _engine(self, r):
+        """The engine for this epoch (see choose_engine)."""
+        s = r.spec
+        return choose_engine(s["dim"], s["L"], r.ns_by, r.engine, r.same_engine_epochs,
+                             self.tiny, self.reprobe_epochs)
 
     def _quota(self, r):
         if r.ns_per_update is None:
@@ -106,7 +125,12 @@ class WolffServer:
         groups = [[], [], [], []]
         for r in active:
             s = r.spec
-            if self.tiny and r.lattice.N <= TINY_MAX_SITES:
+            eng = self._engine(r)
+            r.same_engine_epochs = r.same_engine_epochs + 1 if eng == r.engine else 1
+            r.engine = eng
+            r.ns_per_update = r.ns_by[eng]
+            self.engine_epochs[eng] += 1
+            if eng == TINY:
                 groups[0 if _tiny_words(s["dim"], s["L"]) <= 64 else 1].append(r)
             else:
                 groups[3 if r.lattice.N >= self.big_sites else 2].append(r)
@@ -132,7 +156,9 @@ class WolffServer:
             dt = max(1, st["end_ns"] - st["start_ns"])
             if ran > 0:
                 per = dt / ran
-                r.ns_per_update = per if r.ns_per_update is None else 0.5 * (r.ns_per_update + per)
+                old = r.ns_by[r.engine]
+                r.ns_by[r.engine] = per if old is None else 0.5 * (old + per)
+                r.ns_per_update = r.ns_by[r.engine]
             r.quota = max(ran, 1)
             if ran > 0 and r.done == 0 and t0 is not None:
                 r.first_update_s = time.perf_counter() - t0
@@ -225,6 +251,7 @@ class WolffServer:
             "max_backlog": max_backlog,
             "offered_span_s": last_arrival,
             "saturated": wall > 1.5 * last_arrival + 1.0,
+            "engine_epochs": dict(self.engine_epochs),
         }
         for q in (50, 99):
             v, exact = censored_quantile(lat_all, q / 100.0)
@@ -235,6 +262,26 @@ class WolffServer:
     def close(self):
         for b in self.batches:
             b.close()
+
+
+def choose_engine(dim, L, ns_by, current, same_epochs, tiny=True, reprobe_epochs=8):
+    """Engine of a request's next epoch: TEAM above TINY_MAX_SITES sites (or
+    with the tiny engine off); TINY up to 64 words; otherwise TEAM until it
+    has been timed, then TINY once, then the faster by the measured ns per
+    update (ns_by), switching to the other for one epoch after
+    reprobe_epochs epochs in a row on the same one."""
+    if not tiny or L ** dim > TINY_MAX_SITES:
+        return TEAM
+    if _tiny_words(dim, L) <= 64:
+        return TINY
+    if ns_by[TEAM] is None:
+        return TEAM
+    if ns_by[TINY] is None:
+        return TINY
+    best = TINY if ns_by[TINY] < ns_by[TEAM] else TEAM
+    if current == best and same_epochs >= reprobe_epochs:
+        return TEAM if best == TINY else TINY
+    return best
 
 
 def censored_latencies(requests, wall, time_scale=1.0):

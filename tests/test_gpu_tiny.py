@@ -146,15 +146,15 @@ def test_chain_moves_between_schedules():
 
 def test_host_buffer_path_on_tiny():
     torch, w = require_cuda()
-    dim, L, T, seed = 3, 12, 4.5115, 12
-    s0 = oracle.init_lattice(dim, L, seed)
-    ref, s_ref = oracle_trajectory(dim, L, T, seed, 300, t0=40, s=s0)
-    lat = w.WolffLattice(dim, L, T, seed=seed)
-    assert lat.info()["schedule"] == w.SCHED_TINY
-    rec, spins = lat.run_host(300, spins_in=s0, t_in=40)
-    lat.close()
-    assert_records_equal(rec, ref, "run_host tiny")
-    assert np.array_equal(spins, s_ref)
+    for dim, L, T, seed in ((3, 8, 4.5115, 12), (3, 12, 4.5115, 13)):
+        s0 = oracle.init_lattice(dim, L, seed)
+        ref, s_ref = oracle_trajectory(dim, L, T, seed, 300, t0=40, s=s0)
+        lat = w.WolffLattice(dim, L, T, seed=seed)
+        lat.set_schedule(w.SCHED_TINY)
+        rec, spins = lat.run_host(300, spins_in=s0, t_in=40)
+        lat.close()
+        assert_records_equal(rec, ref, "run_host tiny %dD L=%d" % (dim, L))
+        assert np.array_equal(spins, s_ref)
 
 
 def test_schedule_choice_and_refusals():
@@ -165,14 +165,21 @@ def test_schedule_choice_and_refusals():
         big.set_schedule(w.SCHED_TINY)
     assert ei.value.status == w.WOLFF_EUNSUPPORTED
     big.close()
+    # AUTO: TINY up to 64 words (2D L <= 32, 3D L <= 8), CLUSTER above
+    for dim, L, sched in ((2, 32, w.SCHED_TINY), (2, 33, w.SCHED_CLUSTER),
+                          (3, 8, w.SCHED_TINY), (3, 9, w.SCHED_CLUSTER)):
+        x = w.WolffLattice(dim, L, TC2 if dim == 2 else 4.5115, seed=1)
+        assert x.info()["schedule"] == sched, (dim, L)
+        x.close()
     mid = w.WolffLattice(2, 65, TC2, seed=1)
-    assert mid.info()["schedule"] == w.SCHED_TINY
+    assert mid.info()["schedule"] == w.SCHED_CLUSTER
     mid.set_schedule(w.SCHED_TINY, 1, 1024)
     inf = mid.info()
     assert inf["schedule"] == w.SCHED_TINY and inf["block_threads"] == 1024
     mid.close()
     edge = w.WolffLattice(2, 181, TC2, seed=1)  # 1086 words: needs >= 543 threads
-    assert edge.info()["schedule"] == w.SCHED_TINY
+    assert edge.info()["schedule"] == w.SCHED_CLUSTER
+    edge.set_schedule(w.SCHED_TINY)
     assert edge.info()["block_threads"] == 544
     with pytest.raises(w.WolffError) as ei:
         edge.set_schedule(w.SCHED_TINY, 0, 512)

@@ -39,3 +39,24 @@ def test_censored_latencies_counts_unfinished_requests():
     lat = np.array([3.0, 1.0, 2.0, 5.0, 4.0])
     v, exact = censored_quantile([(x, True) for x in lat], 0.5)
     assert v == 3.0 and exact
+
+
+def test_engine_choice_follows_the_measured_cost():
+    from paper_1110_0899_gb300.serving import TEAM, TINY, choose_engine
+    none = {TINY: None, TEAM: None}
+    # above the tiny engine's limit, or with it off: the team engine
+    assert choose_engine(2, 182, none, TEAM, 0) == TEAM
+    assert choose_engine(3, 33, none, TEAM, 0) == TEAM
+    assert choose_engine(2, 16, none, TEAM, 0, tiny=False) == TEAM
+    # at most 64 words (2D L <= 32, 3D L <= 8): always the tiny engine
+    assert choose_engine(2, 32, none, TEAM, 0) == TINY
+    assert choose_engine(3, 8, {TINY: 9e9, TEAM: 1.0}, TINY, 100) == TINY
+    # larger: team first, then tiny once, then the faster
+    assert choose_engine(2, 64, none, TEAM, 1) == TEAM
+    assert choose_engine(2, 64, {TINY: None, TEAM: 5000.0}, TEAM, 1) == TINY
+    assert choose_engine(2, 64, {TINY: 800.0, TEAM: 5000.0}, TINY, 1) == TINY
+    assert choose_engine(3, 32, {TINY: 20000.0, TEAM: 900.0}, TINY, 1) == TEAM
+    # the other engine is timed again after reprobe_epochs on the same one
+    assert choose_engine(2, 64, {TINY: 800.0, TEAM: 5000.0}, TINY, 7) == TINY
+    assert choose_engine(2, 64, {TINY: 800.0, TEAM: 5000.0}, TINY, 8) == TEAM
+    assert choose_engine(2, 64, {TINY: 800.0, TEAM: 5000.0}, TEAM, 1) == TINY

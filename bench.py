@@ -118,7 +118,15 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="2d",
-                    choices=sorted(WORKLOADS) + ["batched", "served", "binder"])
+                    choices=sorted(WORKLOADS) + ["batched", "served", "binder", "small",
+                                                "tiny-sizes"])
+    ap.add_argument("--sizes", default=None,
+                    help="tiny-sizes: dim:L pairs, comma separated (default: 2D L 16..181, "
+                         "3D L 4..32)")
+    ap.add_argument("--temps", default="0.9,1.0,1.1",
+                    help="tiny-sizes: temperatures as fractions of T_c")
+    ap.add_argument("--regimes", default="random,equil",
+                    help="tiny-sizes: random (fresh lattice) and/or equil (after updates)")
     ap.add_argument("--updates-per-step", type=int, default=None,
                     help="updates per step (default: the workload's measured run, "
                          "10^4 for 2d and 3d, else 1000)")
@@ -954,6 +962,67 @@ def run_small(args):
                 info["schedule"], "schedule %d" % info["schedule"])}
 
 
+def run_tiny_sizes(args):
+    """The tiny schedule against the cluster schedule on the lattices it
+    takes, per update, at 0.9, 1.0 and 1.1 T_c, from a fresh random lattice
+    and after equilibration updates (random start seed 5; CUDA events; the
+    best of two runs of the same updates from the same state)."""
+    import torch
+
+    import paper_1110_0899_gb300 as w
+    torch.cuda.set_device(0)
+    if args.sizes:
+        cases = [tuple(int(v) for v in c.split(":")) for c in args.sizes.split(",")]
+    else:
+        cases = [(2, 16), (2, 32), (2, 48), (2, 64), (2, 96), (2, 128), (2, 181),
+                 (3, 4), (3, 8), (3, 12), (3, 16), (3, 20), (3, 24), (3, 32)]
+    temps = [float(v) for v in args.temps.split(",")]
+    regimes = args.regimes.split(",")
+    rows = []
+    for dim, L in cases:
+        N = L ** dim
+        for tf in temps:
+            T = (TC2 if dim == 2 else 4.5115) * tf
+            for regime in regimes:
+                pre = 0 if regime == "random" else (2000 if N <= 4096 else 600)
+                n = 2000 if N <= 4096 else 400
+                base = w.WolffLattice(dim, L, T, seed=5)
+                base.set_schedule(w.SCHED_TINY)
+                if pre:
+                    base.step(pre, records=False)
+                s0, t0 = base.get_state()
+                base.close()
+                row = {"dim": dim, "L": L, "T_over_Tc": tf, "regime": regime, "updates": n}
+                recs = {}
+                for name, sched in (("tiny", w.SCHED_TINY), ("cluster", w.SCHED_CLUSTER)):
+                    lat = w.WolffLattice(dim, L, T, seed=5)
+                    lat.set_schedule(sched)
+                    buf = lat.record_buffer(n)
+                    best = None
+                    for _ in range(2):
+                        lat.set_state(s0, t0)
+                        a = torch.cuda.Event(enable_timing=True)
+                        b = torch.cuda.Event(enable_timing=True)
+                        a.record()
+                        w.wolff_step(lat.handle, n, buf)
+                        b.record()
+                        b.synchronize()
+                        ms = a.elapsed_time(b)
+                        best = ms if best is None else min(best, ms)
+                    recs[name] = w.records_to_numpy(buf, n)
+                    row["%s_us_per_update" % name] = 1000.0 * best / n
+                    if name == "tiny":
+                        row["tiny_threads"] = lat.info()["block_threads"]
+                    lat.close()
+                row["mean_cluster"] = float(recs["tiny"]["C"].mean())
+                row["mean_levels"] = float(recs["tiny"]["levels"].mean())
+                row["records_equal"] = bool((recs["tiny"] == recs["cluster"]).all())
+                rows.append(row)
+                print(json.dumps(row), file=sys.stderr, flush=True)
+    print(json.dumps({"metric": "microseconds per update, tiny vs cluster schedule",
+                      "unit": "us", "higher_is_better": False, "tiny_sizes": rows}), flush=True)
+
+
 def add_l2_side(line, l2):
     """The L2 side of a line's roofline: the same algorithmic bytes against
     the probe's L2 read bandwidth, and the ncu L2 bytes when fresh."""
@@ -981,6 +1050,16 @@ def main():
         return run_served(args)
     if args.workload == "binder":
         return run_binder(args)
+    if args.workload == "small":
+        import torch
+        torch.cuda.set_device(0)
+        sm = run_small(args)
+        print(json.dumps({"metric": METRIC, "value": sm["gpu_flips_per_s"], "unit": UNIT,
+                          "n_gpus": 1, "higher_is_better": True,
+                          "config": {"workload": sm["workload"]}, "small": sm}), flush=True)
+        return
+    if args.workload == "tiny-sizes":
+        return run_tiny_sizes(args)
     import torch
 
     world, rank, local = dist_setup(args)

@@ -86,11 +86,11 @@ enum { WOLFF_LAYOUT_INT8 = 0 };
  *               alone (EINVAL otherwise);
  *               On lattices above 64 words TINY draws every site's bonds
  *               each update: measured 3-11x faster than CLUSTER while the
- *               clusters are large (equilibrated at or below T_c), up to 50x
+ *               clusters are large (equilibrated at or below T_c), up to 72x
  *               slower on clusters of a few sites (random starts, above T_c),
  *               where CLUSTER's window mode grows many updates at once;
  *   AUTO        the library's choice: TINY for Ising lattices of at most 64
- *               words (2D L <= 32, 3D L <= 8; 8-26x faster than CLUSTER in
+ *               words (2D L <= 32, 3D L <= 8; 9-29x faster than CLUSTER in
  *               every regime measured), else CLUSTER with the largest cluster
  *               the GPU launches (16 where non-portable sizes are allowed,
  *               else 8), 512 threads, t_up = 128, t_down = 64, window mode

@@ -97,11 +97,11 @@ uint32_t sites(int dim, int L) {
 }
 
 // AUTO's choice: the tiny schedule for Ising lattices of at most 64 words
-// (2D L <= 32, 3D L <= 8), where warp 0 grows from registers and it was 8-26x
+// (2D L <= 32, 3D L <= 8), where warp 0 grows from registers and it was 9-29x
 // faster than CLUSTER at 0.9-1.1 T_c from random and equilibrated starts;
 // else CLUSTER.  On larger lattices TINY draws every site's bonds each update:
 // 3-11x faster than CLUSTER while clusters are large (equilibrated at or
-// below T_c) but up to 50x slower on clusters of a few sites, which window
+// below T_c) but up to 72x slower on clusters of a few sites, which window
 // mode grows many at a time.
 int auto_schedule(const wolff_ctx *c) {
     return (!c->potts && !c->xy && c->N <= WOLFF_TINY_MAX_SITES &&

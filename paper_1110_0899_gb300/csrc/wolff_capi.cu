@@ -17,6 +17,7 @@
 
 #include "wolff.h"
 #include "wolff_internal.h"
+#include "wolff_tiny.h"
 
 using namespace wolff;
 

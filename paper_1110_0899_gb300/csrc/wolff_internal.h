@@ -211,21 +211,6 @@ cudaError_t launch_team(int dim, const StepParams &single, const StepParams *d_t
 // Clusters of this shape that can be resident at once (0 if the query fails).
 int team_max_active_clusters(int dim, int cluster_size, int threads, int window_slots);
 
-// Tiny schedule (wolff_tiny.cu): one CTA per job holds the whole lattice in
-// shared memory as bit planes (rows of ceil(L/32) 32-bit words); jobs from
-// d_table (njobs entries of side at most max_L) or the single job.
-constexpr uint32_t kTinyMaxSites = WOLFF_TINY_MAX_SITES;
-uint32_t tiny_words_of(int dim, int L);            // (N / L) ceil(L / 32)
-// warp 0 alone grows (64 or more threads, at most 64 words)
-bool tiny_warp_mode(int dim, int L, int threads);
-// a CTA of `threads` threads can run the lattice (each grower owns <= 2 words)
-bool tiny_shape_ok(int dim, int L, int threads);
-size_t tiny_smem_bytes(int dim, int L);
-// the CTA size the tiny schedule takes by default for this lattice
-int tiny_default_threads(int dim, int L);
-cudaError_t launch_tiny(int dim, const StepParams &single, const StepParams *d_table, int njobs,
-                        int max_L, int threads, cudaStream_t s);
-
 // q-state Potts (wolff_potts.cu).
 cudaError_t launch_potts_init(uint8_t *spins, Geometry g, uint32_t q, uint32_t k0, uint32_t k1,
                               cudaStream_t s);

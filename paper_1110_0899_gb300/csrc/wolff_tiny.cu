@@ -40,6 +40,7 @@
 
 #include "wolff_device.cuh"
 #include "wolff_internal.h"
+#include "wolff_tiny.h"
 
 namespace wolff {
 namespace {

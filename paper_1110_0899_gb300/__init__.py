@@ -399,14 +399,24 @@ class WolffLattice:
         _check(load_library().wolff_set_state_bits(self.handle, ctypes.c_void_p(bits.ctypes.data),
                                                    int(t)), self.handle)
 
-    def run_host_bits(self, n, bits_in=None, t_in=0, records=True, bits_out=True):
-        """As run_host with bit-packed lattices (see pack_spins)."""
+    def run_host_bits(self, n, bits_in=None, t_in=0, records=True, bits_out=True,
+                      records_out=None):
+        """As run_host with bit-packed lattices (see pack_spins).  records_out:
+        an optional C-contiguous RECORD_DTYPE array of at least n entries
+        (pinned memory for an asynchronous copy) that receives the records
+        directly; its first n entries are returned instead of a copy."""
         words = (self.N + 31) // 32
         bin_ = None if bits_in is None else np.ascontiguousarray(bits_in, dtype=np.uint32)
         if bin_ is not None and bin_.size != words:
             raise ValueError("need %d words" % words)
         rec = None
-        if records:
+        if records and records_out is not None:
+            if (records_out.dtype != RECORD_DTYPE or records_out.size < int(n)
+                    or not records_out.flags["C_CONTIGUOUS"]):
+                raise ValueError("records_out must be a C-contiguous RECORD_DTYPE array of "
+                                 "at least n entries")
+            rec = records_out[:int(n)]
+        elif records:
             torch = _torch()
             need = int(n) * RECORD_BYTES
             if getattr(self, "_h_records", None) is None or self._h_records.numel() < need:
@@ -417,7 +427,9 @@ class WolffLattice:
         ptr = lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data)  # noqa: E731
         _check(load_library().wolff_run_host_bits(self.handle, ptr(bin_), int(t_in), int(n),
                                                   ptr(rec), ptr(bout)), self.handle)
-        return (rec.copy() if rec is not None else None), bout
+        if rec is not None and records_out is None:
+            rec = rec.copy()
+        return rec, bout
 
     def selftest_wait_timeout(self, wait_ns):
         obs = ctypes.c_int()

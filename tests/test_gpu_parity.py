@@ -228,6 +228,15 @@ def test_bit_packed_transfers(dim, L):
     assert_records_equal(rec, ref, "run_host_bits")
     assert np.array_equal(w.unpack_bits(bout, L ** dim), s_ref)
     assert np.array_equal(lat.get_state()[0], s_ref)
+    # the records straight into a caller-owned pinned buffer (longer than n)
+    pinned = torch.empty(64 * w.RECORD_BYTES, dtype=torch.uint8, pin_memory=True)
+    out = pinned.numpy().view(w.RECORD_DTYPE)
+    rec2, _ = lat.run_host_bits(60, bits_in=w.pack_spins(s0), t_in=13, bits_out=False,
+                                records_out=out)
+    assert rec2.base is not None and len(rec2) == 60
+    assert_records_equal(out[:60], ref, "run_host_bits into records_out")
+    with pytest.raises(ValueError):
+        lat.run_host_bits(60, bits_in=w.pack_spins(s0), t_in=13, records_out=out[:59])
     lat.close()
 
 

@@ -61,16 +61,18 @@ TC2 = 2.0 / math.log(1.0 + math.sqrt(2.0))
 # cycles over its peak (4 per SM-cycle), on the SMs the launch kept active and
 # over the whole GPU, and its warp instructions per launch.
 TRAFFIC_CAPTURES = {
-    ("2d", 10000): {"src": "33841569bb9d", "bytes_per_launch": 13863680 + 3840,
-                    "l2_bytes_per_launch": 77944608,
-                    "imad": {"pipe_frac_active_sms": 11263374 / (4 * 59999668),
-                             "pipe_frac_gpu": 11263374 / (4 * 105378528),
-                             "warp_insts": 4664897}},
-    ("3d", 10000): {"src": "33841569bb9d", "bytes_per_launch": 26908160 + 73216,
-                    "l2_bytes_per_launch": 142192224,
-                    "imad": {"pipe_frac_active_sms": 13885302 / (4 * 83580008),
-                             "pipe_frac_gpu": 13885302 / (4 * 171567756),
-                             "warp_insts": 5771816}},
+    ("2d", 10000): {"src": "8f06b8d9d2d9", "bytes_per_launch": 13881088 + 2304,
+                    "l2_bytes_per_launch": 78064736,
+                    "imad": {"pipe_frac_active_sms": 11261724 / (4 * 59805320),
+                             "pipe_frac_gpu": 11261724 / (4 * 105197348),
+                             "warp_insts": 4664428}},
+    # 84 MB of the 3D launch's DRAM bytes are its first window's prefetch of
+    # the lattice and the cluster list into L2
+    ("3d", 10000): {"src": "8f06b8d9d2d9", "bytes_per_launch": 86614784 + 828416,
+                    "l2_bytes_per_launch": 254802688,
+                    "imad": {"pipe_frac_active_sms": 13794552 / (4 * 73513989),
+                             "pipe_frac_gpu": 13794552 / (4 * 157390900),
+                             "warp_insts": 5733166}},
 }
 
 

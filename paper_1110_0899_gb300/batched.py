@@ -202,32 +202,19 @@ def candidate_plans(specs):
 def refine_plans(best, specs):
     """Second stage, around the best first-stage plan: the window-mode queue
     (slots per CTA 32 or 128 instead of 64; 12 or 32 growth levels per round
-    instead of the default), larger teams for the large lattices beside the
-    best plan's shape for the rest, and the schedule of the large lattices
-    (one default launch each instead of a batched launch)."""
+    instead of the default) and the schedule of the large lattices (one
+    default launch each instead of a batched launch)."""
     out = []
-    big, small = _size_split(specs)
-    if big and small and len(best.groups) == 1 and best.groups[0].kind == BATCHED:
-        g0 = best.groups[0]
-        for cs in (2, 4, 8):
-            for th in (256, 512):
-                out.append(Plan([Group(big, cs, th, g0.slots, g0.levels),
-                                 Group(small, g0.cs, g0.th, g0.slots, g0.levels)],
-                                "split big cs=%d th=%d / small as %s" % (cs, th, best.label)))
     for slots in (32, 128):
         out.append(Plan([g.replace(slots=slots) for g in best.groups],
                         best.label + " / slots=%d" % slots))
     for levels in (12, 32):
         out.append(Plan([g.replace(levels=levels) for g in best.groups],
                         best.label + " / levels=%d" % levels))
+    big, small = _size_split(specs)
     if big and small:
         small_g = [g for g in best.groups if set(g.ix) == set(small)]
-        if small_g:
-            small_g = small_g[0]
-        elif len(best.groups) == 1 and best.groups[0].kind == BATCHED:
-            small_g = best.groups[0].replace(ix=small)
-        else:
-            small_g = Group(small, 1, 256)
+        small_g = small_g[0] if small_g else Group(small, 1, 256)
         out.append(Plan([Group(big, kind=LAUNCHES), small_g],
                         "big: one default launch each / small: %s" % (
                             "cs=%d th=%d" % (small_g.cs, small_g.th))))

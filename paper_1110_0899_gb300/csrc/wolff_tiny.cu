@@ -21,18 +21,22 @@
 // with population counts (D N - 2 x anti-parallel bonds, 2 x up spins - N).
 //
 // Two regimes, by the number of words NW = (N / L) W:
-//   - NW <= 64 (2D L <= 32, 3D L <= 8) with 64 or more threads: warp 0 alone
-//     runs the update, levels separated by __syncwarp; the other warps draw
-//     the next update's bond bits and seed meanwhile (a draw depends only on
-//     (seed, t, bond), never on the spins), so the Philox work is hidden;
+//   - NW <= 64 (2D L <= 32, 3D L <= 8, where a row is one word) with 64 or
+//     more threads: warp 0 alone runs the update with its rows in registers
+//     (one or two per lane), neighbour rows fetched by shuffles, a level
+//     ended by one vote; the other warps draw the next update's bond bits
+//     and seed meanwhile (a draw depends only on (seed, t, bond), never on
+//     the spins), so the Philox work is hidden;
 //   - otherwise every thread owns one or two words; the update's draws come
 //     first, then levels separated by __syncthreads_or, which also tells
 //     whether the wave front is empty.
 //
-// Shared memory (32-bit words): S[NW] spins (1 = +1) | B[2][DIM][NW] open
-// bonds by update parity and axis | F[2][NW] wave front, ping-pong | 8 words
-// of sums.  The lattice is read from the workspace at the start of a launch
-// and written back (bit 0 = bit 1 = spin) at its end.
+// Shared memory (32-bit words): S[NW] spins (1 = +1; in warp mode only at
+// the launch's start and end, warp 0 holds them meanwhile) | B[2][DIM][NW]
+// open bonds by update parity and axis | F[2][NW] wave front, ping-pong (the
+// all-thread regime) | 8 words of sums.  The lattice is read from the
+// workspace at the start of a launch and written back (bit 0 = bit 1 = spin)
+// at its end.
 #include <cuda_runtime.h>
 #include <stdint.h>
 

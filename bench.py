@@ -162,6 +162,8 @@ def parse():
     ap.add_argument("--no-served", action="store_true",
                     help="skip the serving run in the default line")
     ap.add_argument("--no-l2-probe", action="store_true")
+    ap.add_argument("--epoch-ms", type=float, default=20.0,
+                    help="served form: device time per epoch the server aims at")
     ap.add_argument("--no-tiny-engine", action="store_true",
                     help="served form: run every lattice on the team engine (no tiny engine)")
     ap.add_argument("--no-small", action="store_true",
@@ -531,7 +533,8 @@ def run_served(args, n_requests=200, embed=False):
     from paper_1110_0899_gb300 import serving, workloads
     torch.cuda.set_device(0)
     trace = workloads.serving_trace(n_requests)
-    srv = serving.WolffServer(keep_records=True, tiny=not getattr(args, "no_tiny_engine", False))
+    srv = serving.WolffServer(keep_records=True, tiny=not getattr(args, "no_tiny_engine", False),
+                              epoch_seconds=getattr(args, "epoch_ms", 20.0) / 1000.0)
     reqs, summary = srv.serve(trace, max_seconds=args.serve_seconds)
     srv.close()
     summary["workload"] = ("%d requests, Poisson 200 req/s, 70%% 2D L 32..2048, 30%% 3D L 16..128, "
@@ -1112,6 +1115,7 @@ def main():
         class _S:
             serve_seconds = args.embed_serve_seconds
             no_tiny_engine = args.no_tiny_engine
+            epoch_ms = args.epoch_ms
         line["served"] = run_served(_S, embed=True)
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -933,7 +933,9 @@ def run_small(args):
     """The small configuration, whole run on both sides: 2D L=16, J=1,
     T = T_c, Philox random start from seed 1, 10^4 updates with every record,
     timed on the GPU (one launch, CUDA events, after warm-up runs from the
-    same start) and by the oracle (one core); the records are compared."""
+    same start; the median of the timed runs, repeated for at least 0.6 s so
+    that the clock sampler sees them) and by the oracle (one core); the
+    records are compared."""
     import numpy as np
     import torch
 
@@ -945,15 +947,24 @@ def run_small(args):
     start, _ = lat.get_state()
     buf = lat.record_buffer(n)
     stream_times = []
-    for k in range(max(3, args.warmup) + max(3, args.steps)):
+    warm = max(3, args.warmup)
+    clocks = ClockSampler(torch.cuda.current_device())
+    k, t_first = 0, None
+    while len(stream_times) < max(3, args.steps) or time.perf_counter() - t_first < 0.6:
+        if k == warm:
+            clocks.start()
+            time.sleep(0.3)   # the sampler's start-up stays out of the timed runs
+            t_first = time.perf_counter()
         lat.set_state(start, 0)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         w.wolff_step(lat.handle, n, buf)
         b.record()
         b.synchronize()
-        if k >= max(3, args.warmup):
+        if k >= warm:
             stream_times.append(a.elapsed_time(b) / 1000.0)
+        k += 1
+    ck = clocks.stop()
     rec = w.records_to_numpy(buf, n)
     lat.close()
     thr = oracle.bond_threshold(1.0, T)
@@ -972,6 +983,14 @@ def run_small(args):
             "mean_cluster": flips / n,
             "mean_levels": float(rec["levels"].mean()),
             "gpu_us_per_update": 1e6 * t_gpu / n,
+            "timed_runs": len(stream_times),
+            "clocks": ck,
+            # what bounds it: one SM (1 of the GPU's SMs) running a dependent
+            # chain per breadth-first level; cycles per level at the sampled
+            # clock (the maximum clock when no sample came)
+            "cycles_per_level": (t_gpu / n) * 1e6 * float(ck.get("sm_mhz") or ck.get("sm_max_mhz")
+                                                         or 2070.0) / float(rec["levels"].mean()),
+            "sms_used": 1,
             "schedule": {w.SCHED_TINY: "tiny: one CTA of %d threads, the lattice in shared "
                                        "memory as bit planes" % info["block_threads"]}.get(
                 info["schedule"], "schedule %d" % info["schedule"])}

@@ -60,3 +60,16 @@ def test_engine_choice_follows_the_measured_cost():
     assert choose_engine(2, 64, {TINY: 800.0, TEAM: 5000.0}, TINY, 7) == TINY
     assert choose_engine(2, 64, {TINY: 800.0, TEAM: 5000.0}, TINY, 8) == TEAM
     assert choose_engine(2, 64, {TINY: 800.0, TEAM: 5000.0}, TEAM, 1) == TINY
+
+
+def test_tiny_split_of_the_batched_form():
+    from paper_1110_0899_gb300.batched import tiny_split, tiny_words
+    # words of the bit planes: (N / L) rows of ceil(L / 32) words
+    assert tiny_words(2, 16) == 16 and tiny_words(2, 33) == 66 and tiny_words(2, 181) == 1086
+    assert tiny_words(3, 8) == 64 and tiny_words(3, 32) == 1024
+    specs = [dict(dim=2, L=32), dict(dim=2, L=33), dict(dim=3, L=8), dict(dim=3, L=9),
+             dict(dim=2, L=181), dict(dim=2, L=182), dict(dim=3, L=32), dict(dim=3, L=33)]
+    small, large, rest = tiny_split(specs, range(len(specs)))
+    assert small == [0, 2]           # at most 64 words
+    assert large == [1, 3, 4, 6]     # up to 32768 sites
+    assert rest == [5, 7]            # beyond the tiny engine

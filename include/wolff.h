@@ -82,8 +82,8 @@ enum { WOLFF_LAYOUT_INT8 = 0 };
  *               level).  The paper's CPU/GPU hybrid (section 5) starts small
  *               clusters on the CPU; here a small lattice never leaves one
  *               SM.  grid_blocks must be 0 or 1; block_threads from 32 to
- *               1024, at least half the lattice's words unless warp 0 runs
- *               alone (EINVAL otherwise);
+ *               768 in 2D and 512 in 3D, at least half the lattice's words
+ *               unless warp 0 runs alone (EINVAL otherwise);
  *               On lattices above 64 words TINY draws every site's bonds
  *               each update: measured 3-11x faster than CLUSTER while the
  *               clusters are large (equilibrated at or below T_c), up to 72x
@@ -300,8 +300,8 @@ wolff_status wolff_run_host_bits(wolff_ctx *ctx, const uint32_t *h_bits_in, uint
  * CTAs (PERSISTENT caps it at what can be co-resident); for CLUSTER it is the
  * cluster size (1, 2, 4, 8 or 16; 16 needs a GPU that allows non-portable
  * cluster sizes); for TINY it must be 0 or 1.  block_threads: a multiple of
- * 32, at most 512 for PERSISTENT and CLUSTER, 1024 for GRAPH and TINY (see
- * TINY above for its lower bound).  TINY on a Potts or XY context, or on a
+ * 32, at most 512 for PERSISTENT and CLUSTER, 1024 for GRAPH (TINY: see
+ * above).  TINY on a Potts or XY context, or on a
  * lattice of more than WOLFF_TINY_MAX_SITES sites, is EUNSUPPORTED.  Results
  * do not depend on the choice. */
 wolff_status wolff_set_schedule(wolff_ctx *ctx, int schedule, int grid_blocks,

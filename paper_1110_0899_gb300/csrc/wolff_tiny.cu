@@ -112,7 +112,7 @@ __device__ __forceinline__ WordNb<DIM> word_nb(const TinyGeo &g, uint32_t k) {
 // and a ballot per axis packs the bits (bit set = r_d < thr).  Four words
 // per pass run their Philox chains interleaved.
 template <int DIM>
-__device__ __forceinline__ void draw_bonds(const StepParams &p, const TinyGeo &g,
+__device__ __forceinline__ void draw_words(const StepParams &p, const TinyGeo &g,
                                            unsigned long long t, uint32_t *B, uint32_t wi,
                                            uint32_t nw) {
     const uint32_t lane = threadIdx.x & 31u;
@@ -141,6 +141,61 @@ __device__ __forceinline__ void draw_bonds(const StepParams &p, const TinyGeo &g
             }
         }
     }
+}
+
+// The same for rows of at most 16 sites (one word each): R = 2^lr rows share
+// a warp's draw, 2^ls = 32 / R lanes a row (the power of two at or above L),
+// so short rows leave no lanes idle; row j's bits are bits [j 2^ls,
+// j 2^ls + L) of the ballot.  The warp handles units of R rows (wi, wi + nw,
+// ...), four units per pass.
+template <int DIM>
+__device__ __forceinline__ void draw_short_rows(const StepParams &p, const TinyGeo &g,
+                                                unsigned long long t, uint32_t *B, uint32_t wi,
+                                                uint32_t nw) {
+    uint32_t ls = 4u;   // the power of two at or above L (L <= 16)
+    while (ls > 0u && (1u << (ls - 1u)) >= g.L) --ls;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t lr = 5u - ls;
+    const uint32_t sub = lane >> ls, x = lane & ((1u << ls) - 1u);
+    const uint32_t rowmask = (1u << g.L) - 1u;
+    const uint32_t units = (g.NW + (1u << lr) - 1u) >> lr;
+    for (uint32_t u0 = wi; u0 < units; u0 += 4u * nw) {
+        uint32_t site[4];
+        bool valid[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t r = ((u0 + (uint32_t)q * nw) << lr) + sub;   // the row is the word
+            valid[q] = r < g.NW && x < g.L;
+            site[q] = valid[q] ? x + g.L * r : 0u;
+        }
+        Philox4 d[4];
+        philox4x32_10_lanes<4>(site, (uint32_t)t, (uint32_t)(t >> 32), kTagBond, p.key0, p.key1,
+                               d);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            // lane j < R writes row j of the unit
+            const uint32_t k = ((u0 + (uint32_t)q * nw) << lr) + lane;
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                const uint32_t bits = __ballot_sync(
+                    kFullMask, valid[q] && (unsigned long long)d[q].v[a] < p.thr);
+                if ((lane >> lr) == 0u && k < g.NW) B[a * g.NW + k] = (bits >> (lane << ls)) & rowmask;
+            }
+        }
+    }
+}
+
+// SHORT: a kernel instantiation for lattices whose rows are at most 16
+// sites (one word each); the others draw word by word.  Each instantiation
+// carries one of the two, so neither's registers weigh on the other's loops.
+template <int DIM, bool SHORT>
+__device__ __forceinline__ void draw_bonds(const StepParams &p, const TinyGeo &g,
+                                           unsigned long long t, uint32_t *B, uint32_t wi,
+                                           uint32_t nw) {
+    if (SHORT)
+        draw_short_rows<DIM>(p, g, t, B, wi, nw);
+    else
+        draw_words<DIM>(p, g, t, B, wi, nw);
 }
 
 __device__ __forceinline__ uint32_t seed_of(const StepParams &p, unsigned long long t,
@@ -296,11 +351,12 @@ __device__ __forceinline__ void warp_update(const TinyGeo &g, const WordNb<DIM> 
     up = __reduce_add_sync(kFullMask, u);
 }
 
-// two words per grower in 3D only occur in warp mode (3D lattices have at
-// most 1024 words): those CTAs are capped at 512 threads so that the two
-// words' state stays in registers
-template <int DIM, int J>
-__global__ void __launch_bounds__(DIM == 3 && J == 2 ? 512 : 1024, 1) k_tiny(StepParams single, const StepParams *table,
+// CTAs are capped at 768 threads in 2D (80 registers a thread) and 512 in 3D
+// (128): a 2D lattice has at most 1086 words and a 3D one 1024, two per
+// thread at those sizes, and more threads were never faster in the measured
+// sweeps (2D L=181: 544 and 1024 threads tie; 3D L=32: 512 beats 1024)
+template <int DIM, int J, bool SHORT>
+__global__ void __launch_bounds__(DIM == 3 ? 512 : 768, 1) k_tiny(StepParams single, const StepParams *table,
                                                   uint32_t warp_mode) {
     extern __shared__ __align__(16) uint32_t tiny_smem[];
     const StepParams p = table ? table[blockIdx.x] : single;
@@ -340,7 +396,7 @@ __global__ void __launch_bounds__(DIM == 3 && J == 2 ? 512 : 1024, 1) k_tiny(Ste
         if (lane == 0) S[k] = bits;
     }
     const unsigned long long t0 = p.t0;
-    draw_bonds<DIM>(p, g, t0, Bb, warp, nwarps);
+    draw_bonds<DIM, SHORT>(p, g, t0, Bb, warp, nwarps);
     unsigned long long total_C = 0, levels_sum = 0, start_ns = 0;
     uint32_t last_C = 0, last_levels = 0;
     long long E = 0, M = 0;
@@ -368,7 +424,7 @@ __global__ void __launch_bounds__(DIM == 3 && J == 2 ? 512 : 1024, 1) k_tiny(Ste
         if (!wm && u > 0) {
             // this update's bonds (the previous update's readers are past
             // the barrier that closed it)
-            draw_bonds<DIM>(p, g, t, Bb, warp, nwarps);
+            draw_bonds<DIM, SHORT>(p, g, t, Bb, warp, nwarps);
             if (tid == 0) s_seed[0] = seed_of(p, t, g.N);
             __syncthreads();
         }
@@ -432,7 +488,7 @@ __global__ void __launch_bounds__(DIM == 3 && J == 2 ? 512 : 1024, 1) k_tiny(Ste
             }
         } else {
             // warp mode helpers: the next update's bonds and seed
-            draw_bonds<DIM>(p, g, t + 1, Bb + (par ^ 1u) * bstride, warp - 1u, nwarps - 1u);
+            draw_bonds<DIM, SHORT>(p, g, t + 1, Bb + (par ^ 1u) * bstride, warp - 1u, nwarps - 1u);
             if (tid == 32u) s_seed[par ^ 1u] = seed_of(p, t + 1, g.N);
         }
         if (tid == 0 && p.budget_ns)
@@ -493,12 +549,15 @@ __global__ void __launch_bounds__(DIM == 3 && J == 2 ? 512 : 1024, 1) k_tiny(Ste
 constexpr int kAttrDevices = 64;
 std::atomic<size_t> g_tiny_smem_set[kAttrDevices][4];
 
+// (only the word-by-word kernels ever need more than the default 48 KB of
+// dynamic shared memory: a lattice with rows of at most 16 sites has at most
+// 4096 sites)
 const void *tiny_kernel(int dim, int J) {
     if (dim == 2)
-        return J == 1 ? reinterpret_cast<const void *>(&k_tiny<2, 1>)
-                      : reinterpret_cast<const void *>(&k_tiny<2, 2>);
-    return J == 1 ? reinterpret_cast<const void *>(&k_tiny<3, 1>)
-                  : reinterpret_cast<const void *>(&k_tiny<3, 2>);
+        return J == 1 ? reinterpret_cast<const void *>(&k_tiny<2, 1, false>)
+                      : reinterpret_cast<const void *>(&k_tiny<2, 2, false>);
+    return J == 1 ? reinterpret_cast<const void *>(&k_tiny<3, 1, false>)
+                  : reinterpret_cast<const void *>(&k_tiny<3, 2, false>);
 }
 
 cudaError_t ensure_tiny_smem(int dim, int J, size_t bytes) {
@@ -538,7 +597,7 @@ static int tiny_J(int dim, int L, int threads) {
     const uint32_t nw = tiny_words_of(dim, L);
     const uint32_t growers = tiny_warp_mode(dim, L, threads) ? 32u : (uint32_t)threads;
     const int J = nw <= growers ? 1 : (nw <= 2u * growers ? 2 : 0);
-    if (dim == 3 && J == 2 && threads > 512) return 0;
+    if (threads > (dim == 3 ? 512 : 768)) return 0;
     return J;
 }
 
@@ -578,12 +637,21 @@ cudaError_t launch_tiny(int dim, const StepParams &single, const StepParams *d_t
     cudaError_t e = ensure_tiny_smem(dim, J, smem);
     if (e != cudaSuccess) return e;
     const uint32_t flag = wm ? 1u : 0u;
+    // rows of at most 16 sites (every job's, as the largest's): packed draws
+    const bool shortrows = max_L <= 16;
     if (dim == 2) {
-        if (J == 1) k_tiny<2, 1><<<njobs, threads, smem, s>>>(single, d_table, flag);
-        else        k_tiny<2, 2><<<njobs, threads, smem, s>>>(single, d_table, flag);
+        if (shortrows)   k_tiny<2, 1, true><<<njobs, threads, smem, s>>>(single, d_table, flag);
+        else if (J == 1) k_tiny<2, 1, false><<<njobs, threads, smem, s>>>(single, d_table, flag);
+        else             k_tiny<2, 2, false><<<njobs, threads, smem, s>>>(single, d_table, flag);
     } else {
-        if (J == 1) k_tiny<3, 1><<<njobs, threads, smem, s>>>(single, d_table, flag);
-        else        k_tiny<3, 2><<<njobs, threads, smem, s>>>(single, d_table, flag);
+        if (shortrows && J == 1)
+            k_tiny<3, 1, true><<<njobs, threads, smem, s>>>(single, d_table, flag);
+        else if (shortrows)
+            k_tiny<3, 2, true><<<njobs, threads, smem, s>>>(single, d_table, flag);
+        else if (J == 1)
+            k_tiny<3, 1, false><<<njobs, threads, smem, s>>>(single, d_table, flag);
+        else
+            k_tiny<3, 2, false><<<njobs, threads, smem, s>>>(single, d_table, flag);
     }
     return cudaGetLastError();
 }

@@ -61,14 +61,16 @@ def test_3d_l8():
 
 # L=2 (double bonds), odd L, non powers of two, rows of one to six words
 # with full and one-bit last words (L=32, 33, 64, 65), one drawing warp (64
-# threads), a single warp on the all-thread path (32), 1024 threads, and the
+# threads), a single warp on the all-thread path (32), the most threads (768
+# in 2D, 512 in 3D), rows of 2 to 16 sites packed several to a warp's draw, and the
 # largest lattices the schedule takes (2D L=181: 32761 sites, 3D L=32: 32768)
 SHAPES = [
     (2, 2, 1.0, 300, 64), (2, 3, TC2, 300, 96), (3, 2, 4.5115, 300, 64),
     (3, 3, 3.0, 300, 128), (2, 37, TC2, 400, 96), (2, 100, 2.0, 300, 512),
-    (3, 13, 4.5115, 300, 256), (3, 17, 4.0, 200, 1024), (2, 64, 2.6, 400, 128),
+    (3, 13, 4.5115, 300, 256), (3, 17, 4.0, 200, 512), (2, 64, 2.6, 400, 128),
     (2, 32, TC2, 400, 32), (2, 33, TC2, 300, 0), (2, 65, 2.2, 200, 128),
-    (2, 181, TC2, 150, 1024), (3, 32, 4.5115, 60, 1024), (2, 181, 2.1, 40, 544),
+    (2, 181, TC2, 150, 768), (3, 32, 4.5115, 60, 512), (2, 181, 2.1, 40, 544),
+    (3, 16, 4.5115, 200, 128), (3, 5, 4.3, 300, 32), (2, 10, TC2, 300, 64),
 ]
 
 
@@ -86,8 +88,8 @@ def test_ragged_and_extreme_shapes(dim, L, T, n, threads):
 # 64 words) and the all-thread path, with one and two words per thread
 REGIMES = [
     (2, 32, TC2, 40, (32, 64, 512)), (3, 8, 4.5115, 40, (32, 64, 512)),
-    (2, 100, 2.1, 30, (224, 416)), (3, 24, 4.5115, 30, (288, 1024)),
-    (2, 181, TC2, 12, (544, 1024)), (2, 128, TC2, 30, (256, 512)),
+    (2, 100, 2.1, 30, (224, 416)), (3, 24, 4.5115, 30, (288, 512)),
+    (2, 181, TC2, 12, (544, 768)), (2, 128, TC2, 30, (256, 512)),
 ]
 
 
@@ -173,9 +175,12 @@ def test_schedule_choice_and_refusals():
         x.close()
     mid = w.WolffLattice(2, 65, TC2, seed=1)
     assert mid.info()["schedule"] == w.SCHED_CLUSTER
-    mid.set_schedule(w.SCHED_TINY, 1, 1024)
+    mid.set_schedule(w.SCHED_TINY, 1, 768)
     inf = mid.info()
-    assert inf["schedule"] == w.SCHED_TINY and inf["block_threads"] == 1024
+    assert inf["schedule"] == w.SCHED_TINY and inf["block_threads"] == 768
+    with pytest.raises(w.WolffError) as ei:          # 2D CTAs take at most 768 threads
+        mid.set_schedule(w.SCHED_TINY, 0, 800)
+    assert ei.value.status == w.WOLFF_EINVAL
     mid.close()
     edge = w.WolffLattice(2, 181, TC2, seed=1)  # 1086 words: needs >= 543 threads
     assert edge.info()["schedule"] == w.SCHED_CLUSTER
@@ -187,6 +192,11 @@ def test_schedule_choice_and_refusals():
     edge.set_schedule(w.SCHED_AUTO, 0, 512)     # a shape TINY cannot use: CLUSTER
     assert edge.info()["schedule"] == w.SCHED_CLUSTER
     edge.close()
+    cube = w.WolffLattice(3, 16, 4.5115, seed=1)   # 3D CTAs take at most 512 threads
+    with pytest.raises(w.WolffError) as ei:
+        cube.set_schedule(w.SCHED_TINY, 0, 1024)
+    assert ei.value.status == w.WOLFF_EINVAL
+    cube.close()
     lat = w.WolffLattice(2, 16, TC2, seed=1)
     for blocks, threads in ((2, 0), (0, 48)):
         with pytest.raises(w.WolffError) as ei:
